@@ -1,0 +1,440 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix
+(closed forms, invariants, printed values, brute force).  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_15532_b300 import workloads as W
+from conftest import golden
+
+FOURPI = 4.0 * math.pi
+ETA = np.diag([-1.0, 1, 1, 1])
+
+
+def one_cell(n_geo=4, **kw):
+    cfg = W.base_config(n_geo, (1, 1, 1), (0, 0, 0), (1, 1, 1), (("periodic",) * 2,) * 3, **kw)
+    return oracle.Oracle(cfg)
+
+
+# ------------------------------------------------------------------ grid (section 3.3)
+@pytest.mark.parametrize("gen,n,count", [tuple(int(v) for v in r) for r in golden("geodesic_counts.txt")][:5])
+def test_grid_counts_match_paper(gen, n, count):
+    o = one_cell(n)
+    g = o.grid()
+    assert o.nd == count
+    assert o.ne == 3 * count - 6
+    assert (g["nnb"] == 5).sum() == 12 and (g["nnb"] == 6).sum() == count - 12
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8])
+def test_grid_quadrature_moments(n):
+    g = one_cell(n).grid()
+    d, w = g["dir"], g["w"]
+    assert abs(w.sum() - FOURPI) < 1e-13
+    assert np.abs(d.T @ w).max() < 1e-14
+    M2 = np.einsum("s,si,sj->ij", w, d, d)
+    assert np.abs(M2 - FOURPI / 3 * np.eye(3)).max() < 1e-13
+    M3 = np.einsum("s,si,sj,sk->ijk", w, d, d, d)
+    assert np.abs(M3).max() < 1e-14
+    M4 = np.einsum("s,si,sj,sk,sl->ijkl", w, d, d, d, d)
+    I = np.eye(3)
+    iso = FOURPI / 15 * (np.einsum("ij,kl->ijkl", I, I) + np.einsum("ik,jl->ijkl", I, I) + np.einsum("il,jk->ijkl", I, I))
+    assert np.abs(M4 - iso).max() < 1e-13
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_grid_voronoi_geometry(n):
+    g = one_cell(n).grid()
+    d, w = g["dir"], g["w"]
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-15)
+    assert w.min() / w.max() > 0.75
+    # antipodal directions carry equal weights
+    for s in range(len(d)):
+        t = int(np.argmin(np.linalg.norm(d + d[s], axis=1)))
+        assert np.linalg.norm(d[t] + d[s]) < 1e-12 and abs(w[t] - w[s]) < 1e-14
+    # every edge midpoint is equidistant from its two directions; the edge
+    # normal is tangent there and points from s to s'
+    for e, (s, t) in enumerate(g["edge"]):
+        m = g["emid"][e]
+        assert abs(m @ d[s] - m @ d[t]) < 1e-14
+        assert abs(m @ g["eu"][e]) < 1e-14
+        assert g["eu"][e] @ (d[t] - d[s]) > 0
+    # brute force: neighbours are exactly the nearest ring of each direction
+    for s in range(len(d)):
+        k = g["nnb"][s]
+        dist = np.linalg.norm(d - d[s], axis=1)
+        assert set(np.argsort(dist)[1:k + 1].tolist()) == set(g["nbr"][s, :k].tolist())
+    # pole mirror (n1, -n2, -n3) is a permutation
+    assert sorted(g["mirror"].tolist()) == list(range(len(d)))
+
+
+def test_grid_voronoi_area_brute_force():
+    """Solid angle of a Voronoi cell against Monte-Carlo nearest-direction counting."""
+    g = one_cell(2).grid()
+    d, w = g["dir"], g["w"]
+    rng = np.random.default_rng(7)
+    p = rng.standard_normal((400000, 3))
+    p /= np.linalg.norm(p, axis=1)[:, None]
+    owner = np.argmax(p @ d.T, axis=1)
+    frac = np.bincount(owner, minlength=len(d)) / len(p) * FOURPI
+    assert np.abs(frac - w).max() < 4 * math.sqrt(w.max() / len(p) * FOURPI)
+
+
+# ------------------------------------------------------------------ geometry (section 2.1, App. A.2)
+def kerr_cell(a=0.9, M=1.0):
+    return oracle.Oracle(W.base_config(2, (1, 1, 1), (0, 0, 0), (1, 1, 1), (("periodic",) * 2,) * 3,
+                                       coords="kerr_schild", M=M, a=a))
+
+
+def ks_metric_independent(r, th, a, M=1.0):
+    """Kerr-Schild metric as eta + 2 H l l (spherical-like KS, textbook form),
+    then mapped to x1 = ln r."""
+    sig = r * r + a * a * math.cos(th) ** 2
+    H = M * r / sig
+    s2 = math.sin(th) ** 2
+    eta = np.zeros((4, 4))
+    eta[0, 0] = -1; eta[1, 1] = 1; eta[1, 3] = eta[3, 1] = -a * s2
+    eta[2, 2] = sig; eta[3, 3] = (r * r + a * a) * s2
+    l = np.array([1.0, 1.0, 0.0, -a * s2])
+    g = eta + 2 * H * np.outer(l, l)
+    J = np.diag([1.0, r, 1.0, 1.0])
+    return J @ g @ J
+
+
+@pytest.mark.parametrize("r,th", [(1.8, 0.7), (3.0, 1.2), (12.0, 2.5), (40.0, 0.2)])
+def test_kerr_metric_and_tetrad(r, th):
+    o = kerr_cell()
+    g, e, om, sg = o.geometry_at([math.log(r), th, 0.3])
+    assert np.abs(g - ks_metric_independent(r, th, 0.9)).max() < 1e-12 * max(1, r * r)
+    # orthonormality, eq. (tetrad_def)
+    assert np.abs(e @ g @ e.T - ETA).max() < 1e-13
+    # time leg normal to t = const, future pointing, eq. (tetrad_restriction)
+    for i in (1, 2, 3):
+        assert abs(e[0] @ g[:, i]) < 1e-13 * max(1, r)
+    assert e[0, 0] > 0
+    # spatial legs lie in t = const; phi-hat along d_phi; theta-hat along d_theta
+    assert np.abs(e[1:, 0]).max() == 0.0
+    assert e[3, 1] == 0 and e[3, 2] == 0 and e[2, 1] == 0 and e[2, 3] == 0
+    # legible entries of App. A.2: lapse alpha = 1/sqrt(1 + 2Mr/Sigma)
+    sig = r * r + 0.81 * math.cos(th) ** 2
+    assert abs(e[0, 0] - math.sqrt(1 + 2 * r / sig)) < 1e-13
+    # sqrt(-g) = r * Sigma * sin(theta) in (ln r, theta, phi)
+    assert abs(sg - r * sig * math.sin(th)) < 1e-12 * r * sig
+
+
+@pytest.mark.parametrize("r,th", [(1.8, 0.7), (6.0, 1.5), (25.0, 2.2)])
+def test_ricci_rotation_metric_compatible_and_fd(r, th):
+    o = kerr_cell()
+    x = np.array([math.log(r), th, 0.0])
+    g, e, om, sg = o.geometry_at(x)
+    # metric compatibility: omega_{a b c} antisymmetric in (a, c)
+    low = np.einsum("ad,dbc->abc", ETA, om)
+    assert np.abs(low + np.transpose(low, (2, 1, 0))).max() < 1e-12
+    # independent finite-difference connection from the metric and tetrad values
+    h = 1e-5
+    dg = np.zeros((4, 4, 4)); de = np.zeros((4, 4, 4))
+    for mu in (1, 2):
+        xp = x.copy(); xm = x.copy(); xp[mu - 1] += h; xm[mu - 1] -= h
+        gp, ep, _, _ = o.geometry_at(xp); gm, em, _, _ = o.geometry_at(xm)
+        dg[mu] = (gp - gm) / (2 * h); de[mu] = (ep - em) / (2 * h)
+    gi = np.linalg.inv(g)
+    Gam = 0.5 * (np.einsum("bl,mln->bmn", gi, dg) + np.einsum("bl,nlm->bmn", gi, dg) - np.einsum("bl,lmn->bmn", gi, dg))
+    ei = ETA @ e @ g        # ei[a, mu] = e^(a)_mu
+    cov = np.einsum("mcb->cmb", de) + np.einsum("bmn,cn->cmb", Gam, e)   # cov[c, mu, beta]
+    om_fd = np.einsum("ab,gm,cmb->agc", ei, e, cov)
+    assert np.abs(om_fd - om).max() < 1e-7 * max(1.0, np.abs(om).max())
+
+
+def test_ricci_rotation_flat_spherical_closed_form():
+    """M = 0: the spherical orthonormal frame of flat space."""
+    o = kerr_cell(a=0.0, M=0.0)
+    r, th = 2.5, 0.8
+    _, _, om, _ = o.geometry_at([math.log(r), th, 0.0])
+    ref = np.zeros((4, 4, 4))
+    R, T, P = 1, 2, 3
+    cot = math.cos(th) / math.sin(th)
+    ref[R, T, T] = -1 / r; ref[T, T, R] = 1 / r
+    ref[R, P, P] = -1 / r; ref[P, P, R] = 1 / r
+    ref[T, P, P] = -cot / r; ref[P, P, T] = cot / r
+    assert np.abs(om - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("row", golden("photon_orbits.txt"))
+def test_circular_photon_orbits(row):
+    """The tangent drift of eq. (angular_n_vectors) vanishes for the photon
+    direction that keeps r and theta fixed exactly at the circular photon
+    orbits of section 4.7 (printed radii for a = 0.5)."""
+    a, r1p, r2p, dec = row
+    radii = [2 * (1 + math.cos(2.0 / 3.0 * math.acos(-a))), 2 * (1 + math.cos(2.0 / 3.0 * math.acos(a)))]
+    assert round(radii[0], int(dec)) == pytest.approx(r1p, abs=0.011)
+    assert round(radii[1], int(dec)) == pytest.approx(r2p, abs=0.011)
+    o = kerr_cell(a=a)
+
+    def drift(r, prograde):
+        g, e, om, _ = o.geometry_at([math.log(r), math.pi / 2, 0.0])
+        f = lambda p: e[0, 1] + math.cos(p) * e[1, 1] + math.sin(p) * e[3, 1]
+        fphi = lambda p: e[0, 3] + math.cos(p) * e[1, 3] + math.sin(p) * e[3, 3]
+        ps = np.linspace(-math.pi, math.pi, 20001)
+        vals = np.array([abs(f(p)) if (fphi(p) > 0) == prograde else np.inf for p in ps])
+        p0 = ps[int(np.argmin(vals))]
+        lo, hi = p0 - 1e-3, p0 + 1e-3
+        for _ in range(100):
+            mid = 0.5 * (lo + hi)
+            if (f(lo) > 0) == (f(mid) > 0): lo = mid
+            else: hi = mid
+        psi = 0.5 * (lo + hi)
+        m = np.array([1.0, math.cos(psi), 0.0, math.sin(psi)])
+        q = np.einsum("abc,b,c->a", om, m, m)
+        return -(q[1:] - m[1:] * q[0])
+
+    for rad, pro in zip(radii, (True, False)):
+        assert np.abs(drift(rad, pro)).max() < 1e-9
+        assert np.abs(drift(1.15 * rad, pro)).max() > 1e-3
+
+
+# ------------------------------------------------------------------ spatial flux (section 3.5)
+def test_flux_vacuum_is_upwind():
+    for n in (0.7, -0.4):
+        assert oracle.face_flux(n, 2.0, 3.0, 1.5, 3.5, 0.0) == n * (2.0 if n > 0 else 3.0)
+
+
+def test_flux_small_tau_continuous():
+    for n in (0.7, -0.4):
+        F0 = oracle.face_flux(n, 2.0, 3.0, 1.5, 3.5, 0.0)
+        F1 = oracle.face_flux(n, 2.0, 3.0, 1.5, 3.5, 1e-6)
+        assert abs(F1 - F0) < 1e-5
+
+
+def test_flux_thick_limit_is_diffusive():
+    """App. B: at large tau only -|mu|/(2 tau) (I_{l+1} - I_l) remains."""
+    for n in (0.7, -0.4):
+        tau = 60.0
+        F = oracle.face_flux(n, 2.0, 3.0, 1.5, 3.5, tau)
+        assert abs(F - (-abs(n) / (2 * tau) * (3.5 - 1.5))) < 1e-15
+
+
+def test_flux_advective_term_thick():
+    F = oracle.face_flux(0.3, 2.0, 3.0, 2.0, 3.0, 80.0, 0.2, 0.2)
+    assert F == pytest.approx(-0.3 / 160 * 1.0 + 0.2 * 2.0, rel=1e-14)
+
+
+# ------------------------------------------------------------------ transport
+def periodic_box(N, n_geo=2, dims=3, **kw):
+    nx = tuple(N if a < dims else 1 for a in range(3))
+    return W.base_config(n_geo, nx, (0, 0, 0), tuple(1.0 / N if a < dims else 1.0 for a in range(3)),
+                         (("periodic", "periodic"),) * 3, **kw)
+
+
+def test_uniform_isotropic_field_stays_uniform():
+    o = oracle.Oracle(periodic_box(8, source=False))
+    nc = 8 ** 3
+    o.set_fluid(np.ones(nc), np.ones(nc), W.static_ucon(nc), np.full(nc, 0.5), np.full(nc, 0.3))
+    o.set_intensity(np.full((nc, o.nd), 0.7))
+    o.step(o.cfl_dt(0.4), 5)
+    assert np.abs(o.intensity() - 0.7).max() == 0.0
+
+
+def test_beam_straight_line():
+    dirs = one_cell(2).grid()["dir"]
+    cfg, f = W.beam2d(dirs)
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    o.set_intensity(f["I"])
+    o.step(o.cfl_dt(0.4), 100)
+    E = o.intensity().sum(1).reshape(32, 32)          # [j, i]
+    n = dirs[cfg["beam_dir"]]
+    slope = n[1] / n[0]
+    y = np.arange(32) + 0.5
+    checked = 0
+    for i in range(32):
+        col = E[:, i]
+        if col.sum() < 7.99:      # beam already leaving through the upper face
+            continue
+        yc = (col * y).sum() / col.sum()
+        assert abs(yc - (16.0 + slope * (i + 0.5))) < 0.1
+        checked += 1
+    assert checked >= 12
+    # the injected power (8 rows of I = 1) crosses every steady column
+    assert abs(E[:, :12].sum(0) - 8.0).max() < 1e-4
+    # nothing travels against the beam
+    assert E[:8, 20:].max() < 1e-12
+
+
+def advect_1d(N, steps_per_unit):
+    o = oracle.Oracle(periodic_box(N, n_geo=2, dims=1, source=False))
+    nd = o.nd
+    dirs = o.grid()["dir"]
+    x = (np.arange(N) + 0.5) / N
+    prof = lambda xx: np.exp(np.sin(2 * math.pi * xx))
+    I = np.repeat(prof(x)[:, None], nd, axis=1)
+    o.set_fluid(np.zeros(N), np.zeros(N), W.static_ucon(N), np.zeros(N), np.zeros(N))
+    o.set_intensity(I)
+    T = 0.5
+    nst = int(round(T * steps_per_unit * N))
+    o.step(T / nst, nst)
+    exact = np.stack([prof(x - dirs[s, 0] * T) for s in range(nd)], axis=1)
+    return np.abs(o.intensity() - exact).mean()
+
+
+def test_transport_second_order_convergence():
+    """Translation of a smooth profile at speed n^x: the predictor-corrector
+    PLI scheme converges at second order (error ratio ~4 per doubling)."""
+    e1, e2, e3 = advect_1d(32, 2), advect_1d(64, 2), advect_1d(128, 2)
+    assert e1 / e2 > 3.0 and e2 / e3 > 3.3
+
+
+def test_periodic_energy_conserved_with_coupling():
+    cfg, f = W.flat3d(N=8, n_geo=2, index=11)
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    o.set_intensity(f["I"])
+    _, E0, _ = o.moments()
+    tot0 = (E0 + o.ug()).sum()
+    assert o.step(o.cfl_dt(0.4), 10) == 0
+    _, E1, _ = o.moments()
+    tot1 = (E1 + o.ug()).sum()
+    assert abs(tot1 - tot0) / tot0 < 1e-13
+    assert np.abs(E1 - E0).max() > 1e-4 * E0.mean()
+
+
+# ------------------------------------------------------------------ MAPR (section 3.4)
+def test_mapr_exact_for_gnomonic_linear_fields():
+    o = one_cell(4)
+    g = o.grid()
+    d = g["dir"]
+    rng = np.random.default_rng(3)
+    for s in rng.choice(len(d), 12, replace=False):
+        ns = d[s]
+        h = rng.standard_normal(3); h -= (h @ ns) * ns
+        c0 = 1.3
+        with np.errstate(divide="ignore", invalid="ignore"):
+            # directions 90 degrees or more away have no gnomonic image; only
+            # the ring neighbours enter the reconstruction
+            x = d / (d @ ns)[:, None] - ns
+            field = np.where(d @ ns > 0.1, c0 + x @ h, 0.0)
+        rec = o.mapr(field)
+        for q in range(g["nnb"][s]):
+            t = g["nbr"][s, q]
+            e = [i for i in range(o.ne) if set(g["edge"][i]) == {s, t}][0]
+            m = g["emid"][e]
+            xm = m / (m @ ns) - ns
+            assert abs(rec[s, q] - (c0 + xm @ h)) < 1e-12
+
+
+def test_angular_flux_conserves_sum():
+    """One Kerr-Schild cell (no spatial flux): the angular update conserves
+    sum_s dOmega_s n^0 n_0 I_s (edge antisymmetry)."""
+    cfg = W.base_config(4, (1, 1, 1), (math.log(7.0), 1.1, 0.0), (0.05, 0.05, 0.05), (("periodic",) * 2,) * 3,
+                        coords="kerr_schild", a=0.9, source=False, order=1)
+    o = oracle.Oracle(cfg)
+    g = o.grid()
+    rng = np.random.default_rng(5)
+    I = 1.0 + 0.3 * rng.random((1, o.nd))
+    o.set_fluid([0.0], [0.0], [[1, 0, 0, 0]], [0.0], [0.0])
+    o.set_intensity(I)
+    gm, e, _, _ = o.geometry_at([math.log(7.0) + 0.025, 1.125, 0.025])
+    nup = e[0] + g["dir"] @ e[1:]
+    n0lo = nup @ gm[:, 0]
+    U0 = (g["w"] * nup[:, 0] * n0lo * I[0]).sum()
+    o.step(1e-2, 1)
+    I1 = o.intensity()[0]
+    U1 = (g["w"] * nup[:, 0] * n0lo * I1).sum()
+    assert abs(U1 - U0) < 1e-14 * abs(U0)
+    assert np.abs(I1 - I[0]).max() > 1e-5
+
+
+# ------------------------------------------------------------------ interaction (section 3.5.2)
+def test_pure_absorption_closed_form():
+    """eta = 0, alpha^s = 0, T-independent alpha: each step divides I by 1 + alpha dt."""
+    o = one_cell(2, transport=False, T_exp=0.0)
+    I0 = np.random.default_rng(1).random((1, o.nd))
+    o.set_fluid([1.0], [2.0], [[1, 0, 0, 0]], [0.7], [0.0], [0.0])
+    o.set_intensity(I0)
+    o.step(0.3, 5)
+    assert np.abs(o.intensity() - I0 * (1 + 0.7 * 0.3) ** -5).max() < 1e-15
+
+
+def test_pure_absorption_converges_first_order():
+    errs = []
+    for nst in (10, 20, 40):
+        o = one_cell(2, transport=False, T_exp=0.0)
+        o.set_fluid([1.0], [2.0], [[1, 0, 0, 0]], [0.7], [0.0], [0.0])
+        o.set_intensity(np.ones((1, o.nd)))
+        o.step(2.0 / nst, nst)
+        errs.append(abs(o.intensity()[0, 0] - math.exp(-1.4)))
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2
+
+
+@pytest.mark.parametrize("texp", [0.0, 3.5])
+def test_thermal_equilibrium_stationary(texp):
+    o = one_cell(4, transport=False, T_exp=texp)
+    T, rho = 1.7, 2.0
+    ug = rho * T / (2.0 / 3.0)
+    o.set_fluid([rho], [ug], [[1, 0, 0, 0]], [3.0], [0.4])
+    I = np.full((1, o.nd), T ** 4 / FOURPI)
+    o.set_intensity(I)
+    o.step(0.05, 10)
+    assert np.abs(o.intensity() / I - 1).max() < 2e-14
+    assert abs(o.ug()[0] / ug - 1) < 2e-14
+
+
+def test_equilibration_reaches_printed_temperature():
+    gam, rho, Tg, Tr, utot, Teq = golden("equilibration.txt")[0]
+    # the printed T_eq is the root of T^4 + rho T / (Gamma - 1) = u_total
+    assert abs(Teq ** 4 + rho * Teq / (gam - 1) - utot) < 1e-11
+    o = one_cell(4, transport=False, gam=gam)
+    o.set_fluid([rho], [rho * Tg / (gam - 1)], [[1, 0, 0, 0]], [1.0], [0.0])
+    o.set_intensity(np.full((1, o.nd), Tr ** 4 / FOURPI))
+    totals = []
+    for _ in range(60):
+        o.step(0.25, 1)
+        _, E, _ = o.moments()
+        totals.append(E[0] + o.ug()[0])
+    Tgas = (gam - 1) * o.ug()[0] / rho
+    assert abs(Tgas - Teq) < 1e-12
+    assert abs(E[0] ** 0.25 - Teq) < 1e-12
+    assert np.abs(np.array(totals) - utot).max() < 2e-15 * utot
+
+
+def test_constant_opacity_step_is_backward_euler():
+    """For T-independent opacity and an isotropic static field, one interaction
+    step is backward Euler of E' = alpha^a (a T^4 - E), Y T' = -E' (scattering
+    drops out); solved here independently by bisection."""
+    gam, rho, aa, cs, dt = 5.0 / 3.0, 1.5, 0.8, 0.6, 0.7
+    Y = rho / (gam - 1)
+    T0, E0 = 1.9, 0.6
+    o = one_cell(4, transport=False, T_exp=0.0)
+    o.set_fluid([rho], [Y * T0], [[1, 0, 0, 0]], [aa / rho], [cs / rho])
+    o.set_intensity(np.full((1, o.nd), E0 / FOURPI))
+    o.source_only(dt)
+    W_ = E0 + Y * T0
+    f = lambda T: (W_ - Y * T) * (1 + aa * dt) - E0 - dt * aa * T ** 4
+    lo, hi = 1e-6, W_ / Y
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0: lo = mid
+        else: hi = mid
+    T1 = 0.5 * (lo + hi)
+    assert abs((gam - 1) * o.ug()[0] / rho - T1) < 1e-13
+    _, E, _ = o.moments()
+    assert abs(E[0] - (W_ - Y * T1)) < 1e-13
+
+
+def test_comoving_energy_is_uRu_contraction():
+    """E-bar = u_a u_b R-hat^{ab} for a moving fluid (the boost factor D = -u.n)."""
+    o = one_cell(4, source=False, transport=False)
+    v = np.array([0.3, -0.2, 0.4])
+    gam = 1 / math.sqrt(1 - v @ v)
+    u = np.concatenate([[gam], gam * v])
+    o.set_fluid([1.0], [1.0], [u], [0.0], [0.0])
+    o.set_intensity(np.random.default_rng(9).random((1, o.nd)))
+    R, E, _ = o.moments()
+    Rm = np.zeros((4, 4))
+    q = 0
+    for m in range(4):
+        for n in range(m, 4):
+            Rm[m, n] = Rm[n, m] = R[0, q]; q += 1
+    ul = ETA @ u
+    assert abs(ul @ Rm @ ul - E[0]) < 1e-13 * E[0]
