@@ -1,0 +1,297 @@
+"""Benchmark of the radiation step on B300.
+
+Workload (one bench "step" = one rt_step time step = predictor + corrector
+stage over the whole grid): the flat 3D periodic opacity/coupling box,
+128^3 cells x 162 directions (n = 4), lognormal density, T ~ U[0.5, 2],
+alpha^a = 1e-2 rho T^-3.5, alpha^s = 0.4 rho; intensities stored in FP32 with
+the per-cell coupling (Newton solve, energy ledger) in FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--precision fp32|fp64|bf16] [--n-cells 128]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.  With N > 1 (under
+torchrun) every rank runs an independent replica of the workload (the step
+does not exchange data across GPUs in this build), so the job value is the sum
+over ranks with the time of the slowest rank.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-angle updates/s per rt_step, % of HBM roofline, at stated error vs FP64 oracle"
+UNIT = "cell-angle updates/s"
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "bf16": 2}
+# per-cell fluid traffic of one full step: read rho, u_g, u^mu, kappa, alpha_s, eta
+# (72 B) and write u_g and G (40 B), for each of the two stages
+FLUID_BYTES_PER_CELL_STEP = 224.0
+
+# DRAM traffic of one stage-kernel launch from an ncu capture (bytes per
+# cell-angle), valid only for the stage-kernel source it was measured on.
+NCU_TRAFFIC = {}   # {(sha1 of stage.cu, precision): bytes per cell-angle per launch}
+
+
+def stage_source_hash():
+    with open(os.path.join(ROOT, "paper_2508_15532_b300", "csrc", "stage.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows, self.proc, self.idx = [], None, gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def cpu_oracle_rate(n_cells, n_geo, steps):
+    """The FP64 oracle on a bounded periodic sample of the workload recipe."""
+    import oracle
+    from paper_2508_15532_b300 import workloads as W
+    cfg, f = W.flat3d(N=n_cells, n_geo=n_geo)
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    o.set_intensity(f["I"])
+    dt = o.cfl_dt(0.4)
+    t0 = time.perf_counter()
+    o.step(dt, steps)
+    el = time.perf_counter() - t0
+    nd = 10 * n_geo * n_geo + 2
+    return n_cells ** 3 * nd * steps / el, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    N = args.ref_cells
+    for _ in range(args.warmup):
+        cpu_oracle_rate(N, 4, 1)
+    rate, el = cpu_oracle_rate(N, 4, args.steps)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "flat3d-periodic-opacity-coupling", "cells": [128, 128, 128], "directions": 162,
+                   "reference_sample_cells": [N, N, N], "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d^3 periodic box of the same recipe, 162 directions, %d steps per timed step"
+                                   % (N, 1)},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--n-cells", type=int, default=128)
+    ap.add_argument("--ref-cells", type=int, default=32)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("gloo")
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import paper_2508_15532_b300 as rt
+    from paper_2508_15532_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    N = args.n_cells
+    prec = args.precision
+    tdt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[prec]
+    np_dt = np.float32 if prec != "fp64" else np.float64
+    cfg, f = W.flat3d(N=N, n_geo=4, intensity_dtype=np_dt)
+    nd = f["I"].shape[1]
+    ncell = N ** 3
+    grid = rt.Grid(4)
+    with torch.cuda.stream(stream):
+        st = rt.RadiationStep(grid, cfg, precision=prec, stream=stream.cuda_stream)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+        st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+        I_host = torch.from_numpy(f["I"]).to(tdt).pin_memory()
+        ug_host = torch.from_numpy(np.ascontiguousarray(f["ug"])).pin_memory()
+        st.set_intensity(I_host)
+        dt = st.cfl_dt(0.4)
+    del f
+    stream.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    # ---- device-resident timing (inputs already in HBM; larger than L2)
+    for _ in range(args.warmup):
+        st.step(dt, 1)
+    stream.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st.set_timing(True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st.step(dt, 1)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, launches = st.get_timing()
+    st.set_timing(False)
+    barrier()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    cell_angles = ncell * nd
+    value = world * cell_angles * args.steps / (ms * 1e-3)
+
+    # roofline of the stage kernel: algorithmic bytes per launch (two stage
+    # launches per step: 2 + 3 intensity passes plus the per-cell fluid I/O)
+    S = STORAGE_BYTES[prec]
+    alg_step = cell_angles * 5 * S + ncell * FLUID_BYTES_PER_CELL_STEP
+    alg_per_launch = alg_step / 2.0
+    avg_launch_s = stage_ms * 1e-3 / max(launches, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_per_launch / avg_launch_s / 1e9
+    traffic = NCU_TRAFFIC.get((stage_source_hash(), prec))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (traffic * cell_angles if traffic else None),
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_per_launch,
+                "avg_launch_ms": avg_launch_s * 1e3, "kernel": "k_stage (transport + interaction, fused)"}
+
+    # ---- end to end through the public API with pinned host buffers
+    out_I = torch.empty_like(I_host).pin_memory()
+    out_ug = torch.empty_like(ug_host).pin_memory()
+    for _ in range(1):
+        st.set_intensity(I_host); st.set_ugas(ug_host); st.step(dt, 1); st.get_intensity(out_I); st.get_ugas(out_ug)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        st.set_intensity(I_host)
+        st.set_ugas(ug_host)
+        st.step(dt, 1)
+        st.get_intensity(out_I)
+        st.get_ugas(out_ug)
+    stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * cell_angles * args.e2e_steps / e2e_s
+    h2d = I_host.numel() * I_host.element_size() + ug_host.numel() * 8
+    d2h = out_I.numel() * out_I.element_size() + out_ug.numel() * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_ref = args.ref_cells
+        rate, el = cpu_oracle_rate(n_ref, 4, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d^3 periodic box of the same recipe, 162 directions, 1 step (%.1f s)" % (n_ref, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32 (f64 coupling)", "fp64": "f64", "bf16": "bf16 storage, f32 math, f64 coupling"}[prec],
+            "data": "synthetic",
+            "config": {"workload": "flat3d-periodic-opacity-coupling", "cells": [N, N, N], "directions": nd,
+                       "precision": prec, "dt": dt, "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2 (%.2f GB per intensity array)" % (cell_angles * S / 1e9)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    del st
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

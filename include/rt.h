@@ -1,0 +1,145 @@
+/*
+ * rt.h — C ABI of the B300 radiation-step library (librt_b300.so).
+ *
+ * The library advances the gray, angle-resolved covariant radiative transfer
+ * equation of Wallace, Begue & Pe'er (cuHARM radiation module): the tetrad-
+ * frame intensity I-hat on every spatial cell x every direction of a geodesic
+ * (subdivided icosahedron) angular grid, eq. (covariant_radiative_transfer)
+ * in the finite-volume form eq. (radiative_transfer_discrete), with the
+ * implicit radiation-gas coupling of section 3.5.2 and the predictor-corrector
+ * update of section 3.6.
+ *
+ * Conventions (all entry points):
+ *  - Cell index: cell = (k*nx[1] + j)*nx[0] + i for logical indices (i, j, k)
+ *    along (x1, x2, x3).  Intensities are cell-major with the direction index
+ *    fastest: I[cell*n_dir + s], in the storage type of rt_config.precision
+ *    (double, float, or bfloat16 stored as uint16).
+ *  - Array arguments may be host or device pointers (the library copies with
+ *    cudaMemcpyDefault on the context's stream); they are caller-owned and
+ *    never freed or retained by the library.  rt_set_* copy into
+ *    library-owned device buffers.
+ *  - All work is ordered on the CUDA stream given to rt_create; calls that
+ *    return data to a host pointer synchronise that stream.
+ *  - Errors: every call returns an rt_status; rt_last_error() gives a message.
+ *    Calling out of order (e.g. rt_step before rt_set_fluid) is RT_ESTATE.
+ *    No call traps or hangs: temperature roots that fail to converge leave
+ *    the cell at its bracketed best estimate and are counted (RT_ENOCONV).
+ */
+#ifndef RT_B300_H
+#define RT_B300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RT_OK = 0, RT_EINVAL = 1, RT_ENOMEM = 2, RT_ECUDA = 3, RT_ENOCONV = 4,
+    RT_ESTATE = 5, RT_ETIMEOUT = 6
+} rt_status;
+
+typedef enum { RT_FP64 = 0, RT_FP32 = 1, RT_BF16 = 2 } rt_precision;
+typedef enum { RT_MINKOWSKI_CART = 0, RT_KERR_SCHILD = 1 } rt_metric_kind;
+typedef enum { RT_BC_PERIODIC = 0, RT_BC_OUTFLOW = 1, RT_BC_POLE = 2, RT_BC_BEAM = 3 } rt_bc;
+typedef enum { RT_LIM_MC = 0, RT_LIM_MINMOD = 1, RT_LIM_DONOR = 2 } rt_limiter;
+
+typedef struct rt_grid rt_grid;   /* opaque, library-owned */
+typedef struct rt_ctx rt_ctx;     /* opaque, library-owned */
+
+/* Problem description.  Units are scale-free (G = c = a_rad = k_B/(mu m_p) = 1
+ * by default), as in the paper's equilibration test (section 4.10). */
+typedef struct {
+    int nx[3];          /* cells per logical axis; an axis with one cell carries no flux */
+    double x0[3];       /* logical coordinate of the lower face of cell 0 */
+    double dx[3];       /* logical cell widths (Kerr-Schild: x1 = ln r, x2 = theta, x3 = phi) */
+    int bc[3][2];       /* rt_bc at the lower/upper face of each axis */
+    int beam_dir;       /* RT_BC_BEAM (x1-lower face only): injected direction */
+    int beam_lo, beam_hi;  /* ghost rows j in [beam_lo, beam_hi) carry the beam */
+    double beam_I;      /* injected intensity; every other ghost value is 0 */
+    int n_pole_zero;    /* theta cells zeroed next to each pole (section 5); 0 = none */
+    double gam;         /* adiabatic index Gamma */
+    double arad;        /* radiation constant */
+    double rho_exp;     /* absorption alpha^a = kappa rho^rho_exp T^-T_exp (comoving) */
+    double T_exp;       /* 0 <= T_exp < 4 */
+    double rho_floor;   /* rho below it: no interaction, vacuum fluxes (section 3.7) */
+    double abar;        /* signal-speed coefficient (eq. rad_speeds), 1 in the paper */
+    int tau_dt;         /* 0: tau = abar alpha dl (proper cell length); 1: abar alpha dt */
+    int order;          /* 2: predictor-corrector (section 3.6); 1: one Euler stage */
+    int limiter;        /* rt_limiter of the piecewise-linear reconstruction */
+    int ang_recon;      /* 0: minimum-angle plane reconstruction; 1: donor cell */
+    int transport;      /* 0 disables transport */
+    int source;         /* 0 disables the radiation-gas interaction */
+    double n0_cut;      /* intensities zeroed where |n_0| < n0_cut (section 3.5) */
+    int precision;      /* rt_precision of the stored intensities */
+} rt_config;
+
+/* Geodesic angular grid, section 3.3: icosahedron, log2(n) edge bisections
+ * with projection to the sphere, Voronoi cells of the Delaunay triangulation.
+ * n: edge subdivisions, a power of two in [1, 32]; n_dir = 10 n^2 + 2.
+ * Directions are in the canonical order (ascending -n_z rounded to 1e-9,
+ * then ascending atan2(n_y, n_x)).  Needs a CUDA device (the per-direction
+ * geometry is computed there).  RT_EINVAL for a bad n. */
+rt_status rt_create_geodesic_grid(int n, rt_grid **out);
+/* Sizes and (optionally, host pointers) directions [n_dir*3] and solid angles [n_dir]. */
+rt_status rt_grid_query(const rt_grid *g, int *n_dir, int *n_edge, double *dirs, double *weights);
+void rt_destroy_grid(rt_grid *g);
+/* Message of the last failed rt_create_geodesic_grid on this thread. */
+const char *rt_grid_last_error(void);
+
+/* Context for one problem on the current CUDA device.  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  The grid must outlive the
+ * context.  RT_EINVAL for inconsistent configs, RT_ENOMEM if device memory
+ * runs out. */
+rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cuda_stream, rt_ctx **out);
+void rt_destroy(rt_ctx *c);
+const char *rt_last_error(const rt_ctx *c);
+
+/* Metric and tetrad cache, sections 2.1 and App. A.2: kind = rt_metric_kind;
+ * params = {M, a} for Kerr-Schild (ignored for Minkowski).  Computes, in FP64
+ * on the device, the metric, the normal-observer tetrad (eq.
+ * tetrad_restriction), the Ricci rotation coefficients (eq.
+ * ricci_rotation_coefficients) with exact derivatives, and the per-direction
+ * and per-edge tables the step uses.  Must precede rt_set_fluid. */
+rt_status rt_set_metric(rt_ctx *c, int kind, const double *params);
+
+/* Fluid (sections 3.5.1-3.5.2), each [n_cell] except ucon [n_cell*4]
+ * (coordinate u^mu): density rho, gas internal energy u_g, absorption
+ * prefactor kappa, scattering coefficient alpha_s_coef (alpha^s = coef*rho),
+ * emission multiplier eta (NULL = 1).  Copied. */
+rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_gas, const double *ucon,
+                       const double *kappa, const double *alpha_s_coef, const double *eta);
+/* Tetrad-frame intensities [n_cell*n_dir] in the configured storage type. */
+rt_status rt_set_intensity(rt_ctx *c, const void *I);
+rt_status rt_get_intensity(rt_ctx *c, void *I);
+rt_status rt_set_ugas(rt_ctx *c, const double *u_gas);
+rt_status rt_get_ugas(rt_ctx *c, double *u_gas);
+
+/* Time-step bound of section 3.7: cfl times the shortest coordinate light
+ * crossing dx^a n^0/|n^a| over cells (pole-zeroed cells excluded), axes and
+ * directions.  Written to *dt. */
+rt_status rt_cfl_dt(rt_ctx *c, double cfl, double *dt);
+
+/* nsteps steps of size dt (dt <= 0: the cfl bound with cfl 0.4), section 3.6:
+ * predictor transport over dt/2 + interaction over dt/2, corrector transport
+ * over dt with the predictor fluxes + interaction over dt.  *n_fail (may be
+ * NULL) receives the number of unconverged temperature solves (then
+ * RT_ENOCONV).  Asynchronous unless n_fail is non-NULL. */
+rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *n_fail);
+
+/* Moments, eq. (R): R [n_cell*10] = coordinate R^{mu nu} (00,01,02,03,11,12,
+ * 13,22,23,33) = sum_s n^mu n^nu I_s dOmega_s; Ebar [n_cell] comoving energy
+ * density sum_s D_s^2 I_s dOmega_s; G [n_cell*4] coordinate force on the gas
+ * -Delta R^{0 mu}/dt of the last interaction (section 3.5.3).  Any may be NULL. */
+rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G);
+
+/* Launch timing of the stage kernel (no counterpart in the paper: a
+ * measurement hook).  rt_set_timing(c, 1) makes rt_step record a CUDA event
+ * pair around every stage launch on the context's stream; rt_get_timing
+ * synchronises the stream and returns the summed device time in ms and the
+ * number of launches since the last call, then clears them. */
+rt_status rt_set_timing(rt_ctx *c, int on);
+rt_status rt_get_timing(rt_ctx *c, double *ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

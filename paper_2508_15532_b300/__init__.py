@@ -1,0 +1,215 @@
+"""B300-native radiation step of the covariant gray radiative transfer method
+(Wallace, Begue & Pe'er; cuHARM radiation module).
+
+Thin ctypes binding over the C ABI of ``include/rt.h`` (librt_b300.so):
+argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of the library; there is no CPU fallback, and importing the binding
+fails loudly when the library has not been built.
+
+Arrays may be torch tensors (device or host) or numpy arrays (host); the
+library copies with cudaMemcpyDefault on the context's stream.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt_b300.so")
+
+RT_STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOCONV", 5: "RT_ESTATE",
+             6: "RT_ETIMEOUT"}
+BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3}
+METRIC = {"minkowski": 0, "kerr_schild": 1}
+LIMITER = {"mc": 0, "minmod": 1, "donor": 2}
+ANG = {"mapr": 0, "donor": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
+
+
+class RTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (RT_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class rt_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int * 3), ("x0", C.c_double * 3), ("dx", C.c_double * 3), ("bc", (C.c_int * 2) * 3),
+        ("beam_dir", C.c_int), ("beam_lo", C.c_int), ("beam_hi", C.c_int), ("beam_I", C.c_double),
+        ("n_pole_zero", C.c_int), ("gam", C.c_double), ("arad", C.c_double), ("rho_exp", C.c_double),
+        ("T_exp", C.c_double), ("rho_floor", C.c_double), ("abar", C.c_double), ("tau_dt", C.c_int),
+        ("order", C.c_int), ("limiter", C.c_int), ("ang_recon", C.c_int), ("transport", C.c_int),
+        ("source", C.c_int), ("n0_cut", C.c_double), ("precision", C.c_int),
+    ]
+
+
+_lib = None
+EXPORTS = ["rt_create_geodesic_grid", "rt_grid_query", "rt_destroy_grid", "rt_create", "rt_destroy",
+           "rt_last_error", "rt_set_metric", "rt_set_fluid", "rt_set_intensity", "rt_get_intensity",
+           "rt_set_ugas", "rt_get_ugas", "rt_cfl_dt", "rt_step", "rt_moments", "rt_grid_last_error",
+           "rt_set_timing", "rt_get_timing"]
+
+
+def lib():
+    """Load librt_b300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("librt_b300.so is not built; run python -m paper_2508_15532_b300._build")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.rt_create_geodesic_grid.argtypes = [i, C.POINTER(vp)]
+        L.rt_grid_query.argtypes = [vp, C.POINTER(i), C.POINTER(i), vp, vp]
+        L.rt_destroy_grid.argtypes = [vp]
+        L.rt_destroy_grid.restype = None
+        L.rt_create.argtypes = [vp, C.POINTER(rt_config), vp, C.POINTER(vp)]
+        L.rt_destroy.argtypes = [vp]
+        L.rt_destroy.restype = None
+        L.rt_last_error.argtypes = [vp]
+        L.rt_last_error.restype = C.c_char_p
+        L.rt_set_metric.argtypes = [vp, i, vp]
+        L.rt_set_fluid.argtypes = [vp] * 7
+        L.rt_set_intensity.argtypes = [vp, vp]
+        L.rt_get_intensity.argtypes = [vp, vp]
+        L.rt_set_ugas.argtypes = [vp, vp]
+        L.rt_get_ugas.argtypes = [vp, vp]
+        L.rt_cfl_dt.argtypes = [vp, d, C.POINTER(d)]
+        L.rt_step.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_longlong)]
+        L.rt_moments.argtypes = [vp, vp, vp, vp]
+        L.rt_grid_last_error.restype = C.c_char_p
+        L.rt_set_timing.argtypes = [vp, i]
+        L.rt_get_timing.argtypes = [vp, C.POINTER(d), C.POINTER(C.c_longlong)]
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or a C-contiguous numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+class Grid:
+    """Geodesic angular grid (rt_create_geodesic_grid)."""
+
+    def __init__(self, n):
+        h = C.c_void_p()
+        st = lib().rt_create_geodesic_grid(int(n), C.byref(h))
+        if st:
+            raise RTError(st, lib().rt_grid_last_error().decode())
+        self.h = h
+        nd, ne = C.c_int(), C.c_int()
+        lib().rt_grid_query(h, C.byref(nd), C.byref(ne), None, None)
+        self.nd, self.ne = nd.value, ne.value
+
+    def query(self):
+        d = np.zeros((self.nd, 3)); w = np.zeros(self.nd)
+        lib().rt_grid_query(self.h, None, None, d.ctypes.data, w.ctypes.data)
+        return d, w
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().rt_destroy_grid(self.h)
+            self.h = None
+
+
+def make_config(cfg: dict, precision="fp64") -> rt_config:
+    c = rt_config()
+    for a in range(3):
+        c.nx[a] = int(cfg["nx"][a]); c.x0[a] = float(cfg["x0"][a]); c.dx[a] = float(cfg["dx"][a])
+        for s in range(2):
+            c.bc[a][s] = BC[cfg["bc"][a][s]]
+    c.beam_dir = int(cfg.get("beam_dir", -1)); c.beam_lo = int(cfg.get("beam_lo", 0))
+    c.beam_hi = int(cfg.get("beam_hi", 0)); c.beam_I = float(cfg.get("beam_I", 0.0))
+    c.n_pole_zero = int(cfg.get("n_pole_zero", 0))
+    c.gam = float(cfg.get("gam", 5.0 / 3.0)); c.arad = float(cfg.get("arad", 1.0))
+    c.rho_exp = float(cfg.get("rho_exp", 1.0)); c.T_exp = float(cfg.get("T_exp", 3.5))
+    c.rho_floor = float(cfg.get("rho_floor", 5e-4)); c.abar = float(cfg.get("abar", 1.0))
+    c.tau_dt = int(bool(cfg.get("tau_dt", False))); c.order = int(cfg.get("order", 2))
+    c.limiter = LIMITER[cfg.get("limiter", "mc")]; c.ang_recon = ANG[cfg.get("ang_recon", "mapr")]
+    c.transport = int(bool(cfg.get("transport", True))); c.source = int(bool(cfg.get("source", True)))
+    c.n0_cut = float(cfg.get("n0_cut", 0.1)); c.precision = PRECISION[precision]
+    return c
+
+
+class RadiationStep:
+    """One problem on the current CUDA device (rt_create ... rt_destroy)."""
+
+    def __init__(self, grid: Grid, cfg: dict, precision="fp64", stream=None):
+        self.grid = grid
+        self.cfg = dict(cfg)
+        self.precision = precision
+        self._c = make_config(cfg, precision)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib().rt_create(grid.h, C.byref(self._c), C.c_void_p(stream), C.byref(h))
+        if st:
+            raise RTError(st, lib().rt_last_error(None).decode())
+        self.h = h
+        self.nd = grid.nd
+        self.ncell = int(np.prod(cfg["nx"]))
+        self._check(lib().rt_set_metric(h, METRIC[cfg.get("coords", "minkowski")],
+                                        np.array([cfg.get("M", 1.0), cfg.get("a", 0.0)]).ctypes.data))
+
+    def _check(self, st):
+        if st:
+            raise RTError(st, lib().rt_last_error(self.h).decode())
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().rt_destroy(self.h)
+            self.h = None
+
+    def set_fluid(self, rho, ug, ucon, kappa, alpha_s, eta=None):
+        self._keep = (rho, ug, ucon, kappa, alpha_s, eta)
+        self._check(lib().rt_set_fluid(self.h, _ptr(rho), _ptr(ug), _ptr(ucon), _ptr(kappa), _ptr(alpha_s), _ptr(eta)))
+
+    def set_intensity(self, I):
+        self._check(lib().rt_set_intensity(self.h, _ptr(I)))
+
+    def get_intensity(self, out):
+        self._check(lib().rt_get_intensity(self.h, _ptr(out)))
+        return out
+
+    def set_ugas(self, ug):
+        self._check(lib().rt_set_ugas(self.h, _ptr(ug)))
+
+    def get_ugas(self, out):
+        self._check(lib().rt_get_ugas(self.h, _ptr(out)))
+        return out
+
+    def cfl_dt(self, cfl=0.4):
+        d = C.c_double()
+        self._check(lib().rt_cfl_dt(self.h, float(cfl), C.byref(d)))
+        return d.value
+
+    def step(self, dt, nsteps=1, check=False):
+        used = C.c_double()
+        nf = C.c_longlong()
+        self._check(lib().rt_step(self.h, float(dt), int(nsteps), C.byref(used), C.byref(nf) if check else None))
+        return used.value, (nf.value if check else None)
+
+    def set_timing(self, on=True):
+        self._check(lib().rt_set_timing(self.h, int(bool(on))))
+
+    def get_timing(self):
+        """(summed stage-kernel device time in ms, launches) since the last call."""
+        ms, n = C.c_double(), C.c_longlong()
+        self._check(lib().rt_get_timing(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def moments(self, R=None, Ebar=None, G=None):
+        self._check(lib().rt_moments(self.h, _ptr(R), _ptr(Ebar), _ptr(G)))
+        return R, Ebar, G

@@ -1,0 +1,260 @@
+// api.cu — the C ABI of librt_b300 (see include/rt.h for the contract).
+#include "rt_internal.cuh"
+#include <cstring>
+#include <utility>
+
+static std::string g_create_err;
+
+static rt_status fail(rt_ctx *c, rt_status st, const char *msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+static void free_ctx(rt_ctx *c) {
+    if (!c) return;
+    for (auto &pr : c->ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    void *ptrs[] = {c->I[0], c->I[1], c->I[2], c->ug[0], c->ug[1], c->ug[2], c->alpha[0], c->alpha[1], c->rho,
+                    c->kap, c->cs, c->eta, c->ucon, c->vel, c->uhat, c->G, c->fail, c->pt_e, c->pt_ei, c->pt_V,
+                    c->pt_n0, c->pt_len, c->pt_om, c->cenU_d, c->cenU_f, c->mask, c->fn_d, c->fn_f, c->fP_d,
+                    c->fP_f, c->ew_d, c->ew_f};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    delete c;
+}
+
+extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cuda_stream, rt_ctx **out) {
+    if (!g || !cfg || !out) return RT_EINVAL;
+    *out = nullptr;
+    const rt_config &f = *cfg;
+    for (int a = 0; a < 3; ++a) {
+        if (f.nx[a] < 1 || !(f.dx[a] > 0.0)) { g_create_err = "nx must be >= 1 and dx > 0"; return RT_EINVAL; }
+        for (int s = 0; s < 2; ++s)
+            if (f.bc[a][s] < 0 || f.bc[a][s] > 3) { g_create_err = "unknown boundary kind"; return RT_EINVAL; }
+        if (f.nx[a] > 1 && f.nx[a] < 2) { g_create_err = "active axes need at least 2 cells"; return RT_EINVAL; }
+    }
+    if (f.precision < 0 || f.precision > 2 || f.order < 1 || f.order > 2 || !(f.gam > 1.0) ||
+        f.T_exp < 0.0 || f.T_exp >= 4.0 || f.limiter < 0 || f.limiter > 2) {
+        g_create_err = "invalid precision, order, gamma, T_exp or limiter";
+        return RT_EINVAL;
+    }
+    if (f.bc[1][0] == RT_BC_POLE && f.nx[2] > 1 && (f.nx[2] % 2)) {
+        g_create_err = "the pole boundary needs an even number of x3 cells";
+        return RT_EINVAL;
+    }
+    rt_ctx *c = new rt_ctx();
+    c->cfg = f;
+    c->g = g;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->nd = g->nd; c->ne = g->ne;
+    c->ncell = f.nx[0] * f.nx[1] * f.nx[2];
+    for (int a = 0; a < 3; ++a) c->active[a] = f.nx[a] > 1;
+    c->esize = f.precision == RT_FP64 ? 8 : (f.precision == RT_FP32 ? 4 : 2);
+    size_t ni = (size_t)c->ncell * c->nd * c->esize, nc = (size_t)c->ncell;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMalloc(&c->I[q], ni);
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMalloc(&c->ug[q], nc * 8);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaMalloc(&c->alpha[q], nc * 8);
+    double **fl[] = {&c->rho, &c->kap, &c->cs, &c->eta};
+    for (auto p : fl) if (e == cudaSuccess) e = cudaMalloc(p, nc * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ucon, nc * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&c->vel, nc * 24);
+    if (e == cudaSuccess) e = cudaMalloc(&c->uhat, nc * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&c->G, nc * 32);
+    if (e == cudaSuccess) e = cudaMalloc(&c->fail, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->G, 0, nc * 32);
+    if (e != cudaSuccess) {
+        g_create_err = std::string("allocation: ") + cudaGetErrorString(e);
+        free_ctx(c);
+        return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+    }
+    *out = c;
+    return RT_OK;
+}
+
+extern "C" void rt_destroy(rt_ctx *c) {
+    if (c && c->stream) cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+extern "C" const char *rt_last_error(const rt_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+extern "C" rt_status rt_set_metric(rt_ctx *c, int kind, const double *params) {
+    if (!c) return RT_EINVAL;
+    if (kind != RT_MINKOWSKI_CART && kind != RT_KERR_SCHILD) return fail(c, RT_EINVAL, "unknown metric kind");
+    if (c->metric >= 0) return fail(c, RT_ESTATE, "the metric is already set");
+    c->metric = kind;
+    if (kind == RT_KERR_SCHILD) {
+        if (!params) return fail(c, RT_EINVAL, "Kerr-Schild needs {M, a}");
+        c->M = params[0]; c->a = params[1];
+        if (!(c->M >= 0.0) || !(std::fabs(c->a) <= c->M || c->M == 0.0)) return fail(c, RT_EINVAL, "need M >= 0, |a| <= M");
+        return rt_build_geometry(c);
+    }
+    c->gn[0] = c->cfg.nx[0] + (c->active[0] ? 4 : 0);
+    c->gn[1] = c->cfg.nx[1] + (c->active[1] ? 4 : 0);
+    return RT_OK;
+}
+
+extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_gas, const double *ucon,
+                                  const double *kappa, const double *alpha_s_coef, const double *eta) {
+    if (!c) return RT_EINVAL;
+    if (c->metric < 0) return fail(c, RT_ESTATE, "rt_set_metric must precede rt_set_fluid");
+    if (!rho || !u_gas || !ucon || !kappa || !alpha_s_coef) return fail(c, RT_EINVAL, "null fluid array");
+    size_t n = (size_t)c->ncell * 8;
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->rho, rho, n, cudaMemcpyDefault, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->ug[0], u_gas, n, cudaMemcpyDefault, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->ucon, ucon, 4 * n, cudaMemcpyDefault, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->kap, kappa, n, cudaMemcpyDefault, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->cs, alpha_s_coef, n, cudaMemcpyDefault, c->stream));
+    if (eta) RT_CUDA_TRY(c, cudaMemcpyAsync(c->eta, eta, n, cudaMemcpyDefault, c->stream));
+    else {
+        std::vector<double> ones(c->ncell, 1.0);
+        RT_CUDA_TRY(c, cudaMemcpyAsync(c->eta, ones.data(), n, cudaMemcpyHostToDevice, c->stream));
+        RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    rt_status st = rt_compute_uhat(c);
+    if (st != RT_OK) return st;
+    st = rt_launch_alpha(c, c->ug[0], c->alpha[0]);
+    if (st != RT_OK) return st;
+    c->have_fluid = true;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_set_intensity(rt_ctx *c, const void *I) {
+    if (!c || !I) return RT_EINVAL;
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->I[0], I, (size_t)c->ncell * c->nd * c->esize, cudaMemcpyDefault, c->stream));
+    c->have_I = true;
+    return RT_OK;
+}
+
+static bool is_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return true; }
+    return at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged;
+}
+
+extern "C" rt_status rt_get_intensity(rt_ctx *c, void *I) {
+    if (!c || !I) return RT_EINVAL;
+    if (!c->have_I) return fail(c, RT_ESTATE, "no intensity set");
+    RT_CUDA_TRY(c, cudaMemcpyAsync(I, c->I[0], (size_t)c->ncell * c->nd * c->esize, cudaMemcpyDefault, c->stream));
+    if (is_host(I)) RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RT_OK;
+}
+
+extern "C" rt_status rt_set_ugas(rt_ctx *c, const double *u_gas) {
+    if (!c || !u_gas) return RT_EINVAL;
+    if (!c->have_fluid) return fail(c, RT_ESTATE, "rt_set_fluid must precede rt_set_ugas");
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->ug[0], u_gas, (size_t)c->ncell * 8, cudaMemcpyDefault, c->stream));
+    return rt_launch_alpha(c, c->ug[0], c->alpha[0]);
+}
+
+extern "C" rt_status rt_get_ugas(rt_ctx *c, double *u_gas) {
+    if (!c || !u_gas) return RT_EINVAL;
+    if (!c->have_fluid) return fail(c, RT_ESTATE, "no fluid set");
+    RT_CUDA_TRY(c, cudaMemcpyAsync(u_gas, c->ug[0], (size_t)c->ncell * 8, cudaMemcpyDefault, c->stream));
+    if (is_host(u_gas)) RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return RT_OK;
+}
+
+extern "C" rt_status rt_cfl_dt(rt_ctx *c, double cfl, double *dt) {
+    if (!c || !dt || !(cfl > 0.0)) return RT_EINVAL;
+    if (c->metric < 0) return fail(c, RT_ESTATE, "rt_set_metric must precede rt_cfl_dt");
+    double m;
+    rt_status st = rt_launch_cfl(c, &m);
+    if (st != RT_OK) return st;
+    *dt = cfl * m;
+    return RT_OK;
+}
+
+// stage launch, bracketed by an event pair when timing is on
+static rt_status timed_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout, const double *ug_in,
+                             double *ug_out, const double *a_in, double *a_out, double dtk, double *G) {
+    if (!c->timing) return rt_launch_stage(c, Isrc, Ibase, Iout, ug_in, ug_out, a_in, a_out, dtk, G);
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t a, b;
+        RT_CUDA_TRY(c, cudaEventCreate(&a));
+        RT_CUDA_TRY(c, cudaEventCreate(&b));
+        c->ev.push_back({a, b});
+    }
+    auto &pr = c->ev[c->ev_used++];
+    RT_CUDA_TRY(c, cudaEventRecord(pr.first, c->stream));
+    rt_status st = rt_launch_stage(c, Isrc, Ibase, Iout, ug_in, ug_out, a_in, a_out, dtk, G);
+    RT_CUDA_TRY(c, cudaEventRecord(pr.second, c->stream));
+    return st;
+}
+
+extern "C" rt_status rt_set_timing(rt_ctx *c, int on) {
+    if (!c) return RT_EINVAL;
+    c->timing = on != 0;
+    c->ev_used = 0;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_get_timing(rt_ctx *c, double *ms, long long *launches) {
+    if (!c) return RT_EINVAL;
+    RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    for (size_t q = 0; q < c->ev_used; ++q) {
+        float m = 0.0f;
+        RT_CUDA_TRY(c, cudaEventElapsedTime(&m, c->ev[q].first, c->ev[q].second));
+        tot += m;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = (long long)c->ev_used;
+    c->ev_used = 0;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *n_fail) {
+    if (!c || nsteps < 0) return RT_EINVAL;
+    if (c->metric < 0 || !c->have_fluid || !c->have_I) return fail(c, RT_ESTATE, "metric, fluid and intensity must be set");
+    if (!(dt > 0.0)) {
+        if (c->dt_cfl <= 0.0) {
+            rt_status st = rt_cfl_dt(c, 0.4, &c->dt_cfl);
+            if (st != RT_OK) return st;
+        }
+        dt = c->dt_cfl;
+    }
+    if (dt_used) *dt_used = dt;
+    if (n_fail) RT_CUDA_TRY(c, cudaMemsetAsync(c->fail, 0, sizeof(unsigned long long), c->stream));
+    for (int n = 0; n < nsteps; ++n) {
+        rt_status st;
+        if (c->cfg.order == 1) {
+            st = timed_stage(c, c->I[0], c->I[0], c->I[2], c->ug[0], c->ug[2], c->alpha[0], c->alpha[1], dt, c->G);
+            if (st != RT_OK) return st;
+            std::swap(c->alpha[0], c->alpha[1]);
+        } else {
+            st = timed_stage(c, c->I[0], c->I[0], c->I[1], c->ug[0], c->ug[1], c->alpha[0], c->alpha[1], 0.5 * dt,
+                             nullptr);
+            if (st != RT_OK) return st;
+            st = timed_stage(c, c->I[1], c->I[0], c->I[2], c->ug[0], c->ug[2], c->alpha[1], c->alpha[0], dt, c->G);
+            if (st != RT_OK) return st;
+        }
+        std::swap(c->I[0], c->I[2]);
+        std::swap(c->ug[0], c->ug[2]);
+    }
+    if (n_fail) {
+        unsigned long long h = 0;
+        RT_CUDA_TRY(c, cudaMemcpyAsync(&h, c->fail, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        *n_fail = (long long)h;
+        if (h) return fail(c, RT_ENOCONV, "temperature solve did not converge in some cells");
+    }
+    return RT_OK;
+}
+
+extern "C" rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G) {
+    if (!c) return RT_EINVAL;
+    if (!c->have_fluid || !c->have_I) return fail(c, RT_ESTATE, "fluid and intensity must be set");
+    size_t nc = (size_t)c->ncell;
+    bool hostR = R && is_host(R), hostE = Ebar && is_host(Ebar);
+    double *dR = R, *dE = Ebar;
+    if (hostR) RT_CUDA_TRY(c, cudaMalloc(&dR, nc * 80));
+    if (hostE) RT_CUDA_TRY(c, cudaMalloc(&dE, nc * 8));
+    rt_status st = rt_launch_moments(c, dR, dE);
+    if (st == RT_OK && hostR) RT_CUDA_TRY(c, cudaMemcpyAsync(R, dR, nc * 80, cudaMemcpyDeviceToHost, c->stream));
+    if (st == RT_OK && hostE) RT_CUDA_TRY(c, cudaMemcpyAsync(Ebar, dE, nc * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (G) RT_CUDA_TRY(c, cudaMemcpyAsync(G, c->G, nc * 32, cudaMemcpyDefault, c->stream));
+    if (hostR || hostE || (G && is_host(G))) RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (hostR) cudaFree(dR);
+    if (hostE) cudaFree(dE);
+    return st;
+}

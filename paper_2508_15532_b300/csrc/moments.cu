@@ -1,0 +1,126 @@
+// moments.cu — radiation moments (eq. R) and the light-crossing time-step bound.
+#include "rt_internal.cuh"
+
+namespace {
+
+template <typename TS> __device__ __forceinline__ double ldd(const void *p, size_t i);
+template <> __device__ __forceinline__ double ldd<double>(const void *p, size_t i) { return ((const double *)p)[i]; }
+template <> __device__ __forceinline__ double ldd<float>(const void *p, size_t i) { return ((const float *)p)[i]; }
+template <> __device__ __forceinline__ double ldd<__nv_bfloat16>(const void *p, size_t i) {
+    return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
+}
+
+// one warp per cell: R^{mu nu} = sum_s n^mu n^nu I_s dOmega_s (coordinate
+// components, n^mu = e^mu_(a) nhat^(a)) and E-bar = sum_s D_s^2 I_s dOmega_s
+template <typename TS>
+__global__ void k_moments(int ncell, int nd, int nx0, int nx1, int gn0, int ng0, int ng1, int flat,
+                          const void *__restrict__ I, const double *__restrict__ dir, const double *__restrict__ w,
+                          const double *__restrict__ pe, const double *__restrict__ uhat, double *__restrict__ R,
+                          double *__restrict__ Ebar) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= ncell) return;
+    const int c = warp;
+    double E[16];
+    if (flat) {
+        for (int q = 0; q < 16; ++q) E[q] = (q % 5 == 0) ? 1.0 : 0.0;
+    } else {
+        int i = c % nx0, j = (c / nx0) % nx1;
+        const double *p = pe + 16 * (size_t)((j + ng1) * gn0 + (i + ng0));
+        for (int q = 0; q < 16; ++q) E[q] = p[q];
+    }
+    const double *u = uhat + 4 * (size_t)c;
+    double acc[11] = {0};
+    for (int s = lane; s < nd; s += 32) {
+        double nh[4] = {1.0, dir[3 * s], dir[3 * s + 1], dir[3 * s + 2]};
+        double n[4];
+        for (int m = 0; m < 4; ++m) n[m] = E[m] * nh[0] + E[4 + m] * nh[1] + E[8 + m] * nh[2] + E[12 + m] * nh[3];
+        double Iw = ldd<TS>(I, (size_t)c * nd + s) * w[s];
+        int q = 0;
+        for (int m = 0; m < 4; ++m)
+            for (int k = m; k < 4; ++k) acc[q++] += n[m] * n[k] * Iw;
+        double D = u[0] - (u[1] * nh[1] + u[2] * nh[2] + u[3] * nh[3]);
+        acc[10] += D * D * Iw;
+    }
+    for (int q = 0; q < 11; ++q)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0) {
+        if (R) for (int q = 0; q < 10; ++q) R[10 * (size_t)c + q] = acc[q];
+        if (Ebar) Ebar[c] = acc[10];
+    }
+}
+
+// minimum over cells (pole-zeroed rows excluded), active axes and directions
+// of dx^a n^0 / |n^a|; positive doubles order like their bit patterns
+__global__ void k_cfl(int nx0, int nx1, int nd, int gn0, int ng0, int ng1, int flat, int npole, int a0, int a1,
+                      int a2, double dx0, double dx1, double dx2, const double *__restrict__ dir,
+                      const double *__restrict__ pe, unsigned long long *__restrict__ out) {
+    size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t npts = flat ? 1 : (size_t)nx0 * nx1;
+    if (idx >= npts * nd) return;
+    int s = (int)(idx % nd);
+    int p = (int)(idx / nd);
+    int i = p % nx0, j = p / nx0;
+    if (!flat && npole > 0 && (j < npole || j >= nx1 - npole)) return;
+    double E[16];
+    if (flat) for (int q = 0; q < 16; ++q) E[q] = (q % 5 == 0) ? 1.0 : 0.0;
+    else {
+        const double *pp = pe + 16 * (size_t)((j + ng1) * gn0 + (i + ng0));
+        for (int q = 0; q < 16; ++q) E[q] = pp[q];
+    }
+    double nh[4] = {1.0, dir[3 * s], dir[3 * s + 1], dir[3 * s + 2]};
+    double n[4];
+    for (int m = 0; m < 4; ++m) n[m] = E[m] * nh[0] + E[4 + m] * nh[1] + E[8 + m] * nh[2] + E[12 + m] * nh[3];
+    double best = 1e300;
+    double dxs[3] = {dx0, dx1, dx2};
+    int act[3] = {a0, a1, a2};
+    for (int a = 0; a < 3; ++a) {
+        if (!act[a] || n[a + 1] == 0.0) continue;
+        double t = dxs[a] * n[0] / fabs(n[a + 1]);
+        best = fmin(best, t);
+    }
+    atomicMin(out, (unsigned long long)__double_as_longlong(best));
+}
+
+}  // namespace
+
+rt_status rt_launch_moments(rt_ctx *c, double *R, double *Ebar) {
+    int ng0 = c->active[0] ? 2 : 0, ng1 = c->active[1] ? 2 : 0;
+    int flat = c->metric == RT_MINKOWSKI_CART;
+    unsigned blocks = (unsigned)(((size_t)c->ncell * 32 + 255) / 256);
+    auto P = c->cfg.precision;
+    if (P == RT_FP64)
+        k_moments<double><<<blocks, 256, 0, c->stream>>>(c->ncell, c->nd, c->cfg.nx[0], c->cfg.nx[1], c->gn[0], ng0, ng1,
+                                                         flat, c->I[0], c->g->dir, c->g->w, c->pt_e, c->uhat, R, Ebar);
+    else if (P == RT_FP32)
+        k_moments<float><<<blocks, 256, 0, c->stream>>>(c->ncell, c->nd, c->cfg.nx[0], c->cfg.nx[1], c->gn[0], ng0, ng1,
+                                                        flat, c->I[0], c->g->dir, c->g->w, c->pt_e, c->uhat, R, Ebar);
+    else
+        k_moments<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>(c->ncell, c->nd, c->cfg.nx[0], c->cfg.nx[1], c->gn[0],
+                                                                ng0, ng1, flat, c->I[0], c->g->dir, c->g->w, c->pt_e,
+                                                                c->uhat, R, Ebar);
+    RT_CUDA_TRY(c, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status rt_launch_cfl(rt_ctx *c, double *dt_min_host) {
+    unsigned long long *d = nullptr;
+    RT_CUDA_TRY(c, cudaMalloc(&d, sizeof(unsigned long long)));
+    double big = 1e300;
+    unsigned long long bits;
+    memcpy(&bits, &big, sizeof(bits));
+    cudaMemcpyAsync(d, &bits, sizeof(bits), cudaMemcpyHostToDevice, c->stream);
+    int flat = c->metric == RT_MINKOWSKI_CART;
+    size_t n = (flat ? 1 : (size_t)c->cfg.nx[0] * c->cfg.nx[1]) * c->nd;
+    int ng0 = c->active[0] ? 2 : 0, ng1 = c->active[1] ? 2 : 0;
+    k_cfl<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->cfg.nx[0], c->cfg.nx[1], c->nd, c->gn[0], ng0, ng1, flat,
+                                                              c->cfg.n_pole_zero, c->active[0], c->active[1],
+                                                              c->active[2], c->cfg.dx[0], c->cfg.dx[1], c->cfg.dx[2],
+                                                              c->g->dir, c->pt_e, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) { c->err = std::string("cfl: ") + cudaGetErrorString(e); return RT_ECUDA; }
+    memcpy(dt_min_host, &bits, sizeof(bits));
+    return RT_OK;
+}

@@ -1,0 +1,102 @@
+// rt_internal.cuh — private structures of librt_b300 (the CUDA radiation step).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "../../include/rt.h"
+
+#define RT_MAXNB 6
+
+// Geodesic grid: host topology + device geometry (all FP64 on the device,
+// FP32 copies for the mixed path).
+struct rt_grid {
+    int n = 0, nd = 0, ne = 0;
+    std::vector<double> h_dir, h_w;        // host copies for rt_grid_query
+    std::vector<int> h_nnb, h_nbr, h_mirror, h_ring_edge, h_ring_back, h_edge;
+    // device, per direction s
+    double *dir = nullptr;       // [nd*3]
+    double *w = nullptr;         // [nd] solid angle
+    int *nnb = nullptr;          // [nd]
+    int *nbr = nullptr;          // [nd*6] ccw ring, smallest index first
+    int *ring_edge = nullptr;    // [nd*6]
+    int *ring_back = nullptr;    // [nd*6] slot of s in nbr's ring
+    int *mirror = nullptr;       // [nd] (n1,-n2,-n3)
+    int *edge = nullptr;         // [ne*2] s < s'
+    double *emid = nullptr;      // [ne*3]
+    double *eu = nullptr;        // [ne*3] unit normal from s to s'
+    double *dlam = nullptr;      // [ne]
+    // minimum-angle plane reconstruction tables, per (s, ring slot q)
+    double *mx = nullptr;        // [nd*6*3] gnomonic image of neighbour q in the tangent plane of s
+    double *mg = nullptr;        // [nd*6*3] inverse Gram matrix (a, b, c) of the pair (q, q+1)
+    double *mm = nullptr;        // [nd*6*3] gnomonic image of the midpoint of edge q
+    float *dirf = nullptr, *wf = nullptr, *mxf = nullptr, *mgf = nullptr, *mmf = nullptr;
+};
+
+// Per-context device state.
+struct rt_ctx {
+    rt_config cfg{};
+    const rt_grid *g = nullptr;
+    cudaStream_t stream = nullptr;
+    int ncell = 0, nd = 0, ne = 0;
+    int active[3] = {0, 0, 0};
+    int gn[2] = {0, 0};          // ghosted extents of the (x1, x2) geometry table
+    int metric = -1;             // rt_metric_kind once set
+    double M = 1.0, a = 0.0;
+    bool have_fluid = false, have_I = false;
+    size_t esize = 8;            // bytes per stored intensity
+    std::string err;
+
+    // intensity state: current, predictor, next (rotated after each step)
+    void *I[3] = {nullptr, nullptr, nullptr};
+    double *ug[3] = {nullptr, nullptr, nullptr};
+    double *alpha[2] = {nullptr, nullptr};   // comoving opacity of the flux stage
+    // fluid
+    double *rho = nullptr, *kap = nullptr, *cs = nullptr, *eta = nullptr, *ucon = nullptr;
+    double *vel = nullptr;       // [ncell*3] coordinate velocity u^a/u^0
+    double *uhat = nullptr;      // [ncell*4] tetrad-frame fluid velocity
+    double *G = nullptr;         // [ncell*4]
+    unsigned long long *fail = nullptr;   // device counter of unconverged solves
+
+    // geometry tables over ghosted (i, j) points (Kerr-Schild); flat: unused
+    double *pt_e = nullptr;      // [npt*16] e^mu_(a) at cell centres
+    double *pt_ei = nullptr;     // [npt*16] e^(a)_mu
+    double *pt_V = nullptr;      // [npt] sqrt(-g) dx1 dx2 dx3
+    double *pt_n0 = nullptr;     // [npt] n^0 (direction independent for normal observers)
+    double *pt_len = nullptr;    // [3*npt] proper length sqrt(g_aa) dx_a at the lower face
+    double *pt_om = nullptr;     // [npt*64] Ricci rotation coefficients
+    double *cenU_d = nullptr; float *cenU_f = nullptr;     // [npt*nd] n^0 n_0
+    uint8_t *mask = nullptr;     // [npt*nd] bit0: |n_0| < cut, bit1: n_0 > 0
+    double *fn_d = nullptr; float *fn_f = nullptr;         // [3*npt*nd] n^a at the lower face
+    double *fP_d = nullptr; float *fP_f = nullptr;         // [3*npt*nd] dA_a n_0 at the lower face
+    double *ew_d = nullptr; float *ew_f = nullptr;         // [npt*ne] dlam_e n_0(m) v(m).u_e
+    double dt_cfl = 0.0;
+    // optional per-launch timing of the stage kernel
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t ev_used = 0;
+};
+
+#define RT_CUDA_TRY(c, call)                                                          \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            if (c) (c)->err = std::string(#call) + ": " + cudaGetErrorString(e_);   \
+            return e_ == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;           \
+        }                                                                             \
+    } while (0)
+
+// geometry (geometry.cu)
+rt_status rt_build_geometry(rt_ctx *c);
+rt_status rt_compute_uhat(rt_ctx *c);
+// grid device geometry (grid.cu)
+rt_status rt_grid_device_geometry(rt_grid *g, std::string &err);
+// stage launcher (stage.cu)
+rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout,
+                          const double *ug_in, double *ug_out, const double *alpha_in, double *alpha_out,
+                          double dtk, double *G);
+rt_status rt_launch_alpha(rt_ctx *c, const double *ug, double *alpha);
+// moments (moments.cu)
+rt_status rt_launch_moments(rt_ctx *c, double *R, double *Ebar);
+rt_status rt_launch_cfl(rt_ctx *c, double *dt_min_host);

@@ -1,0 +1,50 @@
+"""Shared helpers of the parity tests: run one workload on the CUDA library
+and on the FP64 oracle from the same seeded inputs."""
+import numpy as np
+
+import oracle
+
+
+def rel_err(x, ref, floor_frac=1e-6):
+    """|x - ref| / max(|ref|, floor_frac * max|ref|), elementwise."""
+    ref = np.asarray(ref, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    floor = floor_frac * max(np.abs(ref).max(), 1e-300)
+    return np.abs(x - ref) / np.maximum(np.abs(ref), floor)
+
+
+def run_oracle(cfg, f, dt, nsteps):
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    o.set_intensity(f["I"])
+    fails = o.step(dt, nsteps)
+    R, E, G = o.moments()
+    return dict(I=o.intensity(), ug=o.ug(), R=R, E=E, G=G, fails=fails)
+
+
+def run_gpu(cfg, f, dt, nsteps, precision="fp64", grid=None):
+    import torch
+    import paper_2508_15532_b300 as rt
+    g = grid or rt.Grid(cfg["n_geo"])
+    st = rt.RadiationStep(g, cfg, precision=precision)
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+    tdt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[precision]
+    I0 = torch.as_tensor(np.asarray(f["I"], dtype=np.float64), device=dev).to(tdt).contiguous()
+    st.set_intensity(I0)
+    _, nfail = st.step(dt, nsteps, check=True)
+    nc, nd = I0.shape
+    I = torch.empty_like(I0)
+    st.get_intensity(I)
+    ug = torch.empty(nc, dtype=torch.float64, device=dev)
+    st.get_ugas(ug)
+    R = torch.empty(nc, 10, dtype=torch.float64, device=dev)
+    E = torch.empty(nc, dtype=torch.float64, device=dev)
+    G = torch.empty(nc, 4, dtype=torch.float64, device=dev)
+    st.moments(R, E, G)
+    torch.cuda.synchronize()
+    out = dict(I=I.double().cpu().numpy(), ug=ug.cpu().numpy(), R=R.cpu().numpy(), E=E.cpu().numpy(),
+               G=G.cpu().numpy(), fails=nfail)
+    del st
+    return out

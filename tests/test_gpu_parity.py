@@ -1,0 +1,143 @@
+"""Parity of the CUDA radiation step (through the C ABI) with the FP64 oracle
+on the same seeded inputs.
+
+Tolerances (from the accuracy targets of the FP64 / mixed paths):
+  FP64 path: |dI| / max(|I_ref|, 1e-6 max|I_ref|) <= 1e-11 per intensity.
+  FP32 path: <= 1e-4 per intensity (floor 1e-3 max|I_ref|), <= 2e-5 on the
+             radiation energy density.
+  BF16 storage: every stage stores the intensity with 8 mantissa bits, a
+             relative rounding of at most 2^-9; after K steps (2K stores) the
+             worst case is 2K 2^-9 per intensity (energy density: 5e-3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle
+import paper_2508_15532_b300 as rt
+from paper_2508_15532_b300 import workloads as W
+from helpers import rel_err, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def small_flat(nx=(20, 12, 10), n_geo=2, index=21):
+    """flat3d recipe on a non-cubic periodic box (ragged x1 tile tail)."""
+    rng = np.random.Generator(np.random.PCG64(W.SEED0 + index))
+    N0, N1, N2 = nx
+    cfg = W.base_config(n_geo, nx, (0, 0, 0), (1.0 / N0, 1.0 / N1, 1.0 / N2), (("periodic", "periodic"),) * 3)
+    nc = N0 * N1 * N2
+    nd = 10 * n_geo * n_geo + 2
+    g = W.gaussian_field(rng, (N2, N1, N0))
+    rho = np.exp(g - 0.5).ravel()
+    T = rng.uniform(0.5, 2.0, nc)
+    ug = rho * T / (W.GAMMA - 1.0)
+    I = W.planck(T)[:, None] * (1.0 + 0.1 * rng.uniform(-1, 1, (nc, nd)))
+    f = dict(rho=rho, ug=ug, ucon=W.static_ucon(nc), kappa=np.full(nc, 1e-2), alpha_s=np.full(nc, 0.4),
+             eta=np.ones(nc), I=I)
+    return cfg, f
+
+
+def test_grid_matches_oracle():
+    for n in (1, 2, 4, 8):
+        g = rt.Grid(n)
+        d, w = g.query()
+        o = oracle.Oracle(W.base_config(n, (1, 1, 1), (0, 0, 0), (1, 1, 1), (("periodic",) * 2,) * 3))
+        og = o.grid()
+        assert g.nd == o.nd and g.ne == o.ne
+        assert np.abs(d - og["dir"]).max() < 1e-15
+        assert np.abs(w - og["w"]).max() < 1e-14
+        assert abs(w.sum() - 4 * math.pi) < 1e-13
+
+
+def test_beam2d_fp64_full_config():
+    """The 2D beam workload at its full size (32x32, 42 directions, 100 steps)."""
+    dirs = rt.Grid(2).query()[0]
+    cfg, f = W.beam2d(dirs)
+    o = oracle.Oracle(cfg)
+    dt = o.cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 100)
+    out = run_gpu(cfg, f, dt, 100, "fp64")
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert np.abs(out["I"]).max() > 0.5
+
+
+def test_flat_fp64_ragged_box():
+    cfg, f = small_flat()
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 4)
+    out = run_gpu(cfg, f, dt, 4, "fp64")
+    assert out["fails"] == 0 and ref["fails"] == 0
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert rel_err(out["ug"], ref["ug"]).max() < 1e-11
+    assert rel_err(out["E"], ref["E"]).max() < 1e-11
+    assert rel_err(out["R"], ref["R"], 1e-6).max() < 1e-10
+    assert np.abs(out["G"] - ref["G"]).max() < 1e-9 * np.abs(ref["G"]).max()
+
+
+def test_flat_fp64_order1_minmod_and_source_off():
+    cfg, f = small_flat(nx=(17, 9, 6), index=22)
+    cfg.update(order=1, limiter="minmod")
+    dt = oracle.Oracle(cfg).cfl_dt(0.3)
+    assert rel_err(run_gpu(cfg, f, dt, 3)["I"], run_oracle(cfg, f, dt, 3)["I"]).max() < 1e-11
+    cfg.update(order=2, limiter="mc", source=False)
+    assert rel_err(run_gpu(cfg, f, dt, 3)["I"], run_oracle(cfg, f, dt, 3)["I"]).max() < 1e-11
+
+
+def test_flat_fp32_and_bf16_against_fp64_oracle():
+    cfg, f = small_flat(nx=(24, 16, 8), n_geo=4, index=23)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 10)
+    out = run_gpu(cfg, f, dt, 10, "fp32")
+    assert rel_err(out["I"], ref["I"], 1e-3).max() < 1e-4
+    assert rel_err(out["E"], ref["E"]).max() < 2e-5
+    b = run_gpu(cfg, f, dt, 10, "bf16")
+    assert rel_err(b["I"], ref["I"], 1e-3).max() < 2 * 10 * 2.0 ** -9
+    assert rel_err(b["E"], ref["E"]).max() < 5e-3
+
+
+def test_flat_periodic_energy_conserved_fp64_gpu():
+    cfg, f = small_flat(nx=(16, 8, 8), index=24)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    out0 = run_gpu(cfg, f, dt, 0, "fp64")
+    out = run_gpu(cfg, f, dt, 8, "fp64")
+    tot0 = (out0["E"] + out0["ug"]).sum()
+    tot1 = (out["E"] + out["ug"]).sum()
+    assert abs(tot1 - tot0) / tot0 < 1e-13
+
+
+def test_equilibration_single_cell_gpu():
+    cfg = W.base_config(4, (1, 1, 1), (0, 0, 0), (1, 1, 1), (("periodic",) * 2,) * 3, transport=False)
+    f = dict(rho=np.array([1.0]), ug=np.array([3.0]), ucon=W.static_ucon(1), kappa=np.array([1.0]),
+             alpha_s=np.array([0.0]), eta=np.array([1.0]), I=np.full((1, 162), 1 / (4 * math.pi)))
+    out = run_gpu(cfg, f, 0.25, 60, "fp64")
+    assert abs(out["ug"][0] * 2 / 3 - 1.2147993409938) < 1e-12
+    assert abs(out["E"][0] + out["ug"][0] - 4.0) < 1e-13
+
+
+@pytest.mark.parametrize("nph", [1, 8])
+def test_kerr_fp64_parity(nph):
+    cfg, f = W.kerr(nr=24, nth=16, nph=nph, n_geo=2, index=31 + nph)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 3)
+    out = run_gpu(cfg, f, dt, 3, "fp64")
+    assert out["fails"] == 0
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert rel_err(out["ug"], ref["ug"]).max() < 1e-11
+    assert rel_err(out["R"], ref["R"], 1e-6).max() < 1e-10
+
+
+def test_kerr_fp32_against_fp64_oracle():
+    cfg, f = W.kerr(nr=32, nth=16, nph=1, n_geo=4, index=40)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 5)
+    out = run_gpu(cfg, f, dt, 5, "fp32")
+    assert rel_err(out["I"], ref["I"], 1e-3).max() < 1e-4
