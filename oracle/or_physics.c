@@ -109,8 +109,9 @@ static void fill_ghosts(const or_ctx *c, const double *I, double *Ig) {
 /* minimum-angle plane reconstruction on the geodesic grid (section 3.4).
    Reading: in the gnomonic tangent plane of direction s, the planes through s
    and each pair of consecutive ring neighbours are formed; the one whose
-   gradient has the smallest norm (smallest tilt; the first in ring order on
-   ties) is evaluated at the edge midpoints.  out[q] is the value at the
+   gradient has the smallest norm (smallest tilt; norms within a relative 1e-6
+   of the smallest tie, and the first in ring order wins) is evaluated at the
+   edge midpoints.  out[q] is the value at the
    midpoint of the edge to ring slot q. */
 static void mapr_dir(const or_ctx *c, const double *Ic, int s, double out[6]) {
     const or_grid *G = &c->G;
@@ -125,18 +126,23 @@ static void mapr_dir(const or_ctx *c, const double *Ic, int s, double out[6]) {
         for (int m = 0; m < 3; ++m) x[q][m] = nt[m] / d - ns[m];
         dI[q] = Ic[t] - Ic[s];
     }
-    int best = -1; double bn = 0.0, ba = 0.0, bb = 0.0;
+    double al[6] = {0}, be[6] = {0}, nrm[6] = {0}, mn = 0.0;
     for (int q = 0; q < k; ++q) {
         int q1 = (q + 1) % k;
         double g00 = x[q][0]*x[q][0] + x[q][1]*x[q][1] + x[q][2]*x[q][2];
         double g01 = x[q][0]*x[q1][0] + x[q][1]*x[q1][1] + x[q][2]*x[q1][2];
         double g11 = x[q1][0]*x[q1][0] + x[q1][1]*x[q1][1] + x[q1][2]*x[q1][2];
         double det = g00 * g11 - g01 * g01;
-        double al = (g11 * dI[q] - g01 * dI[q1]) / det;
-        double be = (g00 * dI[q1] - g01 * dI[q]) / det;
-        double nrm = al * dI[q] + be * dI[q1];
-        if (best < 0 || nrm < bn) { best = q; bn = nrm; ba = al; bb = be; }
+        al[q] = (g11 * dI[q] - g01 * dI[q1]) / det;
+        be[q] = (g00 * dI[q1] - g01 * dI[q]) / det;
+        nrm[q] = al[q] * dI[q] + be[q] * dI[q1];
+        if (q == 0 || nrm[q] < mn) mn = nrm[q];
     }
+    /* planes within a relative 1e-6 of the smallest norm count as equal (mirror
+       symmetric neighbourhoods tie exactly); the first in ring order wins */
+    int best = 0;
+    while (!(nrm[best] <= mn + 1e-6 * fabs(mn))) ++best;
+    double ba = al[best], bb = be[best];
     int b1 = (best + 1) % k;
     for (int q = 0; q < k; ++q) {
         int e = G->ring_edge[6 * s + q];
@@ -294,33 +300,35 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
     free(Ig); free(alg); free(vg);
 }
 
-/* h(T) of the temperature equation, method 3 (eq. T_almost_fully_implicit)
-   divided by T^(T_exp): with A'_1 = B1, A'_2 = B2 taken without the
-   1/(alpha_+ dt) prefactor (the only reading under which eq.
+/* Method 3 (eq. T_almost_fully_implicit) with A'_1 = B1, A'_2 = B2 taken
+   without the 1/(alpha_+ dt) prefactor (the only reading under which eq.
    T_almost_fully_implicit follows from eqs. ideal_gas_difference and
-   energy_integral), and the emission multiplier eta. */
-typedef struct { double B1, B2, W, Y, au, as, eta, arad, dt, p; } teq;
-static double teq_h(const teq *q, double T) {
+   energy_integral), and the emission multiplier eta.  Divided by T^p it reads
+     (alpha(T) dt - B2 alpha^s) E* - B1 - B2 eta alpha^a(T) a T^4 = 0,
+   with E* = W - Y T the radiation energy after the interaction (eq.
+   ideal_gas_difference).  It is solved for E* (T = T_- + (E-bar_- - E*)/Y):
+   where the gas holds far more energy than the radiation, W - Y T cancels
+   catastrophically, while E* itself is well conditioned.  h increases
+   strictly with E* on [0, W), so the root is unique. */
+typedef struct { double B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p; } teq;
+static double teq_T(const teq *q, double X) { return q->Tm + (q->Em - X) / q->Y; }
+static double teq_h(const teq *q, double X) {
+    double T = teq_T(q, X);
+    if (!(T > 0.0)) return INFINITY;
     double aa = q->au * pow(T, -q->p);
-    return ((aa + q->as) * q->dt - q->B2 * q->as) * (q->W - q->Y * T) - q->B1 - q->B2 * q->eta * aa * q->arad * T * T * T * T;
+    return ((aa + q->as) * q->dt - q->B2 * q->as) * X - q->B1 - q->B2 * q->eta * aa * q->arad * T * T * T * T;
 }
 
-/* root of h on (0, W/Y] by bisection to adjacent doubles; h is strictly
-   decreasing there (each term decreases), so the root is unique */
-static int solve_T(const teq *q, double *T) {
-    double hi = q->W / q->Y;
-    double hh = teq_h(q, hi);
-    if (hh >= 0.0) { *T = hi; return 1; }
-    double lo = hi;
-    int it = 0;
-    do { hi = lo; lo *= 0.5; ++it; } while (!(teq_h(q, lo) > 0.0) && it < 3000);
-    if (!(teq_h(q, lo) > 0.0)) { *T = lo; return 0; }
-    for (int n = 0; n < 400; ++n) {
+/* root of h(E*) on [0, W) by bisection to adjacent doubles */
+static int solve_E(const teq *q, double *X) {
+    double lo = 0.0, hi = q->W;
+    if (!(teq_h(q, lo) < 0.0)) { *X = 0.0; return teq_h(q, lo) == 0.0; }
+    for (int n = 0; n < 2000; ++n) {
         double mid = 0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (teq_h(q, mid) > 0.0) lo = mid; else hi = mid;
+        if (teq_h(q, mid) > 0.0) hi = mid; else lo = mid;
     }
-    *T = fabs(teq_h(q, lo)) <= fabs(teq_h(q, hi)) ? lo : hi;
+    *X = fabs(teq_h(q, lo)) <= fabs(teq_h(q, hi)) ? lo : hi;
     return 1;
 }
 
@@ -374,10 +382,10 @@ long or_source_step(or_ctx *c, double *I, const double *ug_in, double *ug_out, d
                     B2 += Dd[s] * K * wb;
                 }
                 B2 *= dtk / fourpi;
-                teq q = {B1, B2, Em + Y * Tm, Y, au, as, eta, c->c.arad, dtk, c->c.T_exp};
-                double Tp;
-                if (!solve_T(&q, &Tp)) ++fails;
-                double Estar = q.W - Y * Tp;
+                teq q = {B1, B2, Em + Y * Tm, Y, Tm, Em, au, as, eta, c->c.arad, dtk, c->c.T_exp};
+                double Estar;
+                if (!solve_E(&q, &Estar)) ++fails;
+                double Tp = teq_T(&q, Estar);
                 double aap = au * pow(Tp, -c->c.T_exp), atp = aap + as;
                 double em = eta * aap * c->c.arad * Tp * Tp * Tp * Tp + as * Estar;
                 double Ep = 0.0, dR[4] = {0, 0, 0, 0};
