@@ -16,7 +16,7 @@ static void free_ctx(rt_ctx *c) {
     void *ptrs[] = {c->I[0], c->I[1], c->I[2], c->ug[0], c->ug[1], c->ug[2], c->alpha[0], c->alpha[1], c->rho,
                     c->kap, c->cs, c->eta, c->ucon, c->vel, c->uhat, c->G, c->fail, c->pt_e, c->pt_ei, c->pt_V,
                     c->pt_n0, c->pt_len, c->pt_om, c->cenU_d, c->cenU_f, c->mask, c->fn_d, c->fn_f, c->fP_d,
-                    c->fP_f, c->ew_d, c->ew_f};
+                    c->fP_f, c->ew_d, c->ew_f, c->cc_au, c->cc_as, c->cc_Y, c->cc_on};
     for (void *p : ptrs) if (p) cudaFree(p);
     delete c;
 }
@@ -60,6 +60,11 @@ extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cud
     if (e == cudaSuccess) e = cudaMalloc(&c->uhat, nc * 32);
     if (e == cudaSuccess) e = cudaMalloc(&c->G, nc * 32);
     if (e == cudaSuccess) e = cudaMalloc(&c->fail, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->cc_au, nc * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->cc_as, nc * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->cc_Y, nc * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->cc_on, nc);
+    for (double w : g->h_w) c->sumw += w;
     if (e == cudaSuccess) e = cudaMemset(c->G, 0, nc * 32);
     if (e != cudaSuccess) {
         g_create_err = std::string("allocation: ") + cudaGetErrorString(e);
@@ -111,6 +116,8 @@ extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_
         RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     }
     rt_status st = rt_compute_uhat(c);
+    if (st != RT_OK) return st;
+    st = rt_launch_cellconst(c);
     if (st != RT_OK) return st;
     st = rt_launch_alpha(c, c->ug[0], c->alpha[0]);
     if (st != RT_OK) return st;
@@ -166,8 +173,9 @@ extern "C" rt_status rt_cfl_dt(rt_ctx *c, double cfl, double *dt) {
 
 // stage launch, bracketed by an event pair when timing is on
 static rt_status timed_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout, const double *ug_in,
-                             double *ug_out, const double *a_in, double *a_out, double dtk, double *G) {
-    if (!c->timing) return rt_launch_stage(c, Isrc, Ibase, Iout, ug_in, ug_out, a_in, a_out, dtk, G);
+                             double *ug_out, const double *a_in, const double *a_int, double *a_out, double dtk,
+                             double *G) {
+    if (!c->timing) return rt_launch_stage(c, Isrc, Ibase, Iout, ug_in, ug_out, a_in, a_int, a_out, dtk, G);
     if (c->ev_used == c->ev.size()) {
         cudaEvent_t a, b;
         RT_CUDA_TRY(c, cudaEventCreate(&a));
@@ -176,7 +184,7 @@ static rt_status timed_stage(rt_ctx *c, const void *Isrc, const void *Ibase, voi
     }
     auto &pr = c->ev[c->ev_used++];
     RT_CUDA_TRY(c, cudaEventRecord(pr.first, c->stream));
-    rt_status st = rt_launch_stage(c, Isrc, Ibase, Iout, ug_in, ug_out, a_in, a_out, dtk, G);
+    rt_status st = rt_launch_stage(c, Isrc, Ibase, Iout, ug_in, ug_out, a_in, a_int, a_out, dtk, G);
     RT_CUDA_TRY(c, cudaEventRecord(pr.second, c->stream));
     return st;
 }
@@ -218,14 +226,19 @@ extern "C" rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, 
     for (int n = 0; n < nsteps; ++n) {
         rt_status st;
         if (c->cfg.order == 1) {
-            st = timed_stage(c, c->I[0], c->I[0], c->I[2], c->ug[0], c->ug[2], c->alpha[0], c->alpha[1], dt, c->G);
+            st = timed_stage(c, c->I[0], c->I[0], c->I[2], c->ug[0], c->ug[2], c->alpha[0], c->alpha[0], c->alpha[1],
+                             dt, c->G);
             if (st != RT_OK) return st;
             std::swap(c->alpha[0], c->alpha[1]);
         } else {
-            st = timed_stage(c, c->I[0], c->I[0], c->I[1], c->ug[0], c->ug[1], c->alpha[0], c->alpha[1], 0.5 * dt,
-                             nullptr);
+            // predictor: fluxes and interaction from (I^n, u_g^n)
+            st = timed_stage(c, c->I[0], c->I[0], c->I[1], c->ug[0], c->ug[1], c->alpha[0], c->alpha[0], c->alpha[1],
+                             0.5 * dt, nullptr);
             if (st != RT_OK) return st;
-            st = timed_stage(c, c->I[1], c->I[0], c->I[2], c->ug[0], c->ug[2], c->alpha[1], c->alpha[0], dt, c->G);
+            // corrector: fluxes from (I*, u_g*), base I^n, interaction from u_g^n;
+            // alpha(u_g^n) is read and overwritten cell by cell by the same CTA
+            st = timed_stage(c, c->I[1], c->I[0], c->I[2], c->ug[0], c->ug[2], c->alpha[1], c->alpha[0], c->alpha[0],
+                             dt, c->G);
             if (st != RT_OK) return st;
         }
         std::swap(c->I[0], c->I[2]);

@@ -57,6 +57,10 @@ struct rt_ctx {
     double *vel = nullptr;       // [ncell*3] coordinate velocity u^a/u^0
     double *uhat = nullptr;      // [ncell*4] tetrad-frame fluid velocity
     double *G = nullptr;         // [ncell*4]
+    // per-cell constants of the fluid: kappa rho^m, alpha_s rho, rho/(Gamma-1), floor switch
+    double *cc_au = nullptr, *cc_as = nullptr, *cc_Y = nullptr;
+    uint8_t *cc_on = nullptr;
+    double sumw = 0.0;           // sum of the solid angles (4 pi to rounding)
     unsigned long long *fail = nullptr;   // device counter of unconverged solves
 
     // geometry tables over ghosted (i, j) points (Kerr-Schild); flat: unused
@@ -94,9 +98,10 @@ rt_status rt_compute_uhat(rt_ctx *c);
 rt_status rt_grid_device_geometry(rt_grid *g, std::string &err);
 // stage launcher (stage.cu)
 rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout,
-                          const double *ug_in, double *ug_out, const double *alpha_in, double *alpha_out,
-                          double dtk, double *G);
+                          const double *ug_in, double *ug_out, const double *alpha_in, const double *alpha_int,
+                          double *alpha_out, double dtk, double *G);
 rt_status rt_launch_alpha(rt_ctx *c, const double *ug, double *alpha);
+rt_status rt_launch_cellconst(rt_ctx *c);
 // moments (moments.cu)
 rt_status rt_launch_moments(rt_ctx *c, double *R, double *Ebar);
 rt_status rt_launch_cfl(rt_ctx *c, double *dt_min_host);

@@ -1,30 +1,41 @@
 // stage.cu — one fused stage of the radiation step on sm_103a.
 //
-// A stage (section 3.6) is: explicit transport of the conserved n^0 n_0 I-hat
+// A stage (section 3.6) is the explicit transport of the conserved n^0 n_0 I
 // over dtk with fluxes from I_src (eq. radiative_transfer_discrete: spatial
 // flux eqs. spatial_fluxes_vacuum / rad_speeds / flux_Jiang on a piecewise-
 // linear reconstruction, angular flux eq. angular_fluxes on a minimum-angle
 // plane reconstruction), followed in the same kernel by the implicit
 // radiation-gas interaction of section 3.5.2 on every cell of the tile.
 //
-// Work decomposition: one CTA = one run of TX consecutive cells along x1 with
-// all directions; thread s owns direction s (the warp reads 32 consecutive
-// directions of a cell: coalesced).  The direction-independent face
-// coefficients (optical depth cut-offs, signal-speed factors, fluid advection)
-// are computed once per face into shared memory.  The transported intensities
-// of the tile stay in shared memory for the interaction, so each stage reads
-// I_src (stencil, L2-resident neighbours), I_base, and writes I_out once.
-// Interaction: per-cell angular sums by groups of 8 threads (shuffle
-// reduction), one FP64 temperature solve per cell (one lane per cell), then
-// the per-direction update and the exchange ledger.
+// Work decomposition (HBM-bound design):
+//  - one CTA owns a brick of 32 cells: TXC consecutive cells along x1 times
+//    BY x BZ rows (x2, x3), with all directions; thread s owns direction s, so
+//    every warp-wide load or store touches 32 consecutive directions of one
+//    cell (coalesced, cell-major layout);
+//  - each thread marches along x1 with a sliding register window (one new
+//    value, one slope and one face flux per cell); the x2/x3 stencils of the
+//    BY x BZ rows are register columns, so every slope and face flux of the
+//    brick is evaluated once; boundary conditions are resolved per CTA into
+//    row/column descriptors in shared memory (no ghost arrays);
+//  - the direction-independent face coefficients (optical-depth cut-offs,
+//    signal-speed factors, fluid advection) are computed once per face;
+//  - the transported brick stays in shared memory for the interaction: each
+//    stage reads I_src (neighbours mostly from L2), I_base, and writes I_out
+//    exactly once;
+//  - interaction: per-cell angular sums in direction chunks (lane = cell, no
+//    shuffles), one warp (lane = cell) solves the 32 temperature equations —
+//    FP32 Newton iterations finished by an FP64 Newton step in the mixed
+//    path, FP64 throughout in the FP64 path — then the per-direction update
+//    and the FP64 energy ledger.
 #include "rt_internal.cuh"
 #include <cmath>
 
 namespace {
 
-constexpr int TX = 16;       // cells per tile along x1
-constexpr int GS = 8;        // threads per cell in the angular sums
+constexpr int NCELL = 32;    // cells per CTA
+constexpr int MAXNT = 256;
 constexpr double FOURPI = 12.566370614359172953850573533118;
+constexpr int F_MIR = 1 << 29, F_FIX = 1 << 30, F_MASK = (1 << 29) - 1;
 
 struct StageArgs {
     int nx0, nx1, nx2, nd, ne;
@@ -34,27 +45,26 @@ struct StageArgs {
     double beam_I;
     int n_pole_zero;
     double dx0, dx1, dx2;
-    double gam, arad, rho_exp, T_exp, rho_floor, abar;
+    double gam, arad, T_exp, abar, sumw;
     int tau_dt, limiter, ang_recon, transport, source;
     double dtk;
     const void *Isrc; const void *Ibase; void *Iout;
-    const double *ug_in; double *ug_out; const double *alpha_in; double *alpha_out;
-    const double *rho, *kap, *cs, *eta, *vel, *uhat;
+    const double *ug_in; double *ug_out;
+    const double *alpha_in;    // opacity of the flux stage (neighbours)
+    const double *alpha_int;   // opacity at the interaction's initial gas state
+    double *alpha_out;         // opacity after the interaction
+    const double *cc_au, *cc_as, *cc_Y, *eta, *vel, *uhat;
+    const uint8_t *cc_on;
     double *G;
     unsigned long long *fail;
-    // grid
     const int *mirror, *nnb, *nbr, *ring_edge, *ring_back, *edge;
-    const void *dirT, *wT, *mxT, *mgT, *mmT;   // math-type copies
-    // geometry (curved)
+    const void *dirT, *wT, *mxT, *mgT, *mmT;   // math-type copies of the grid tables
     int gn0, ng0, ng1;
-    const void *cenU, *fn, *fP, *ew;           // math-type tables
+    const void *cenU, *fn, *fP, *ew;           // math-type geometry tables (curved)
     const uint8_t *mask;
-    const double *pt_V, *pt_n0, *pt_len, *pt_e;
+    const double *pt_V, *pt_n0, *pt_e;
+    const double *pt_len;
 };
-
-template <typename T> __device__ __forceinline__ float tof(T v);
-template <> __device__ __forceinline__ float tof<float>(float v) { return v; }
-template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename TS, typename TM> struct IO;
 template <> struct IO<double, double> {
@@ -63,10 +73,12 @@ template <> struct IO<double, double> {
 };
 template <> struct IO<float, float> {
     __device__ static float ld(const void *p, size_t i) { return __ldg((const float *)p + i); }
-    __device__ static float st(void *p, size_t i, float v) { ((float *)p)[i] = v; return v; }
+    __device__ static float st(void *p, size_t i, float v) { __stcs((float *)p + i, v); return v; }
 };
 template <> struct IO<__nv_bfloat16, float> {
-    __device__ static float ld(const void *p, size_t i) { return __bfloat162float(((const __nv_bfloat16 *)p)[i]); }
+    __device__ static float ld(const void *p, size_t i) {
+        return __bfloat162float(__ldg((const __nv_bfloat16 *)p + i));
+    }
     __device__ static float st(void *p, size_t i, float v) {
         __nv_bfloat16 b = __float2bfloat16_rn(v);
         ((__nv_bfloat16 *)p)[i] = b;
@@ -76,103 +88,21 @@ template <> struct IO<__nv_bfloat16, float> {
 
 template <typename TM> __device__ __forceinline__ TM ldT(const void *p, size_t i) { return __ldg((const TM *)p + i); }
 
+template <typename TM> __device__ __forceinline__ TM dv(TM a, TM b);
+template <> __device__ __forceinline__ float dv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double dv<double>(double a, double b) { return a / b; }
+
 template <typename TM> __device__ __forceinline__ TM limiter(int kind, TM dl, TM dr) {
     if (kind == RT_LIM_DONOR) return TM(0);
     if (dl * dr <= TM(0)) return TM(0);
-    TM s = dl > TM(0) ? TM(1) : TM(-1);
     TM al = fabs(dl), ar = fabs(dr);
-    if (kind == RT_LIM_MINMOD) return s * fmin(al, ar);
-    TM m = fmin(TM(2) * al, TM(2) * ar);
-    m = fmin(m, TM(0.5) * fabs(dl + dr));
-    return s * m;
+    TM m = (kind == RT_LIM_MINMOD) ? fmin(al, ar) : fmin(fmin(TM(2) * al, TM(2) * ar), TM(0.5) * fabs(dl + dr));
+    return dl > TM(0) ? m : -m;
 }
 
-// comoving total opacity with the density floor (sections 3.5.2 and 3.7)
-__device__ __forceinline__ double cell_alpha(const StageArgs &A, double rho, double ug, double kap, double cs) {
-    if (!(rho >= A.rho_floor) || rho <= 0.0) return 0.0;
-    double T = (A.gam - 1.0) * ug / rho;
-    return kap * pow(rho, A.rho_exp) * pow(T, -A.T_exp) + cs * rho;
-}
-
-// Boundary mapping of a cell index that may lie up to two cells outside the
-// domain along one axis.  Returns the interior cell; *mir toggles the pole
-// direction mirror; *beam is set for the fixed-inflow face.
-__device__ __forceinline__ int map_cell(const StageArgs &A, int i, int j, int k, bool *mir, bool *beam) {
-    *mir = false; *beam = false;
-    if (i < 0 || i >= A.nx0) {
-        int side = i < 0 ? 0 : 1, bc = A.bc[0][side];
-        if (bc == RT_BC_PERIODIC) i = (i + A.nx0) % A.nx0;
-        else if (bc == RT_BC_POLE) { i = side ? 2 * A.nx0 - 1 - i : -1 - i; *mir = true; }
-        else { if (bc == RT_BC_BEAM) *beam = true; i = side ? A.nx0 - 1 : 0; }
-    }
-    if (j < 0 || j >= A.nx1) {
-        int side = j < 0 ? 0 : 1, bc = A.bc[1][side];
-        if (bc == RT_BC_PERIODIC) j = (j + A.nx1) % A.nx1;
-        else if (bc == RT_BC_POLE) {
-            j = side ? 2 * A.nx1 - 1 - j : -1 - j; *mir = !*mir;
-            if (A.nx2 > 1) k = (k + A.nx2 / 2) % A.nx2;
-        } else { if (bc == RT_BC_BEAM) *beam = true; j = side ? A.nx1 - 1 : 0; }
-    }
-    if (k < 0 || k >= A.nx2) {
-        int side = k < 0 ? 0 : 1, bc = A.bc[2][side];
-        if (bc == RT_BC_PERIODIC) k = (k + A.nx2) % A.nx2;
-        else if (bc == RT_BC_POLE) { k = side ? 2 * A.nx2 - 1 - k : -1 - k; *mir = !*mir; }
-        else { if (bc == RT_BC_BEAM) *beam = true; k = side ? A.nx2 - 1 : 0; }
-    }
-    return (k * A.nx1 + j) * A.nx0 + i;
-}
-
-template <typename TS, typename TM>
-__device__ __forceinline__ TM load_I(const StageArgs &A, const void *I, int i, int j, int k, int s) {
-    bool mir, beam;
-    int c = map_cell(A, i, j, k, &mir, &beam);
-    if (beam) {
-        // fixed inflow through the x1-lower face (only that face carries a beam)
-        if (i < 0 && j >= A.beam_lo && j < A.beam_hi && s == A.beam_dir) return TM(A.beam_I);
-        return TM(0);
-    }
-    int d = mir ? __ldg(A.mirror + s) : s;
-    return IO<TS, TM>::ld(I, (size_t)c * A.nd + d);
-}
-
-struct FaceRec {
-    double c1, c2, c3, kL, kR;
-};
-
-// direction-independent coefficients of the spatial flux across the face
-// between cells l = (il, jl, kl) and r = l + e_ax (eqs. rad_speeds, flux_Jiang
-// per unit n^a; the tau -> 0 limits f = 1, g = 0 give the vacuum flux)
-__device__ FaceRec face_coeffs(const StageArgs &A, bool flat, int ax, int il, int jl, int kl) {
-    int ir = il + (ax == 0), jr = jl + (ax == 1), kr = kl + (ax == 2);
-    bool m1, b1;
-    int cl = map_cell(A, il, jl, kl, &m1, &b1), cr = map_cell(A, ir, jr, kr, &m1, &b1);
-    double al = A.alpha_in[cl], ar = A.alpha_in[cr];
-    double len;
-    if (A.tau_dt) len = A.dtk;
-    else if (flat) len = ax == 0 ? A.dx0 : (ax == 1 ? A.dx1 : A.dx2);
-    else {
-        int gn1 = 0; (void)gn1;
-        int p = (jr + A.ng1) * A.gn0 + (ir + A.ng0);
-        if (ax == 2) p = (jl + A.ng1) * A.gn0 + (il + A.ng0);
-        int npt_stride = A.gn0 * (A.nx1 + 2 * A.ng1);
-        len = A.pt_len[(size_t)ax * npt_stride + p];
-    }
-    double tau = A.abar * 0.5 * (al + ar) * len;
-    FaceRec R;
-    if (tau > 0.0) {
-        double f = sqrt(-expm1(-tau * tau)) / tau;
-        double g = sqrt(-expm1(-tau * tau * tau * tau)) / tau;
-        double e = exp(-tau), fg = f + g;
-        R.c1 = f * e / fg; R.c2 = g * e / fg; R.c3 = f * g / fg;
-        double cadv = -expm1(-tau);
-        double vl = A.vel[3 * (size_t)cl + ax], vr = A.vel[3 * (size_t)cr + ax];
-        R.kL = cadv * fmax(vl, 0.0); R.kR = cadv * fmin(vr, 0.0);
-    } else {
-        R.c1 = 1.0; R.c2 = 0.0; R.c3 = 0.0; R.kL = 0.0; R.kR = 0.0;
-    }
-    return R;
-}
-
+// per-unit-n_0 flux through one face for one direction: the exponentially cut
+// HLL form (eqs. rad_speeds, flux_Jiang; see the oracle for the orientation
+// reading); rec = (c1, c2, c3, kL, kR) of the face
 template <typename TM>
 __device__ __forceinline__ TM face_phi(TM n, const TM *rec, TM IL, TM IR, TM Il, TM Ir) {
     TM cL = n > TM(0) ? rec[0] : rec[1];
@@ -180,423 +110,656 @@ __device__ __forceinline__ TM face_phi(TM n, const TM *rec, TM IL, TM IR, TM Il,
     return n * (cL * IL + cR * IR) - fabs(n) * rec[2] * (Ir - Il) + rec[3] * IL + rec[4] * IR;
 }
 
-// ------------------------------------------------------------ temperature
-// h(T) of method 3 (eq. T_almost_fully_implicit divided by T^p), with the
-// reading A'_1 = B1, A'_2 = B2 (no 1/(alpha_+ dt) prefactor); see the oracle.
-struct TeqArgs { double B1, B2, W, Y, au, as, eta, arad, dt, p; };
+// boundary resolution of one index along one axis (setup only)
+__device__ int map_axis(const StageArgs &A, int ax, int q, int *flags, int *kshift) {
+    int n = ax == 0 ? A.nx0 : (ax == 1 ? A.nx1 : A.nx2);
+    if (q >= 0 && q < n) return q;
+    int side = q < 0 ? 0 : 1, bc = A.bc[ax][side];
+    if (bc == RT_BC_PERIODIC) return (q + n) % n;
+    if (bc == RT_BC_POLE) {
+        *flags ^= F_MIR;
+        if (ax == 1 && A.nx2 > 1 && kshift) *kshift = A.nx2 / 2;
+        return side ? 2 * n - 1 - q : -1 - q;
+    }
+    if (bc == RT_BC_BEAM) *flags |= F_FIX;
+    return side ? n - 1 : 0;
+}
 
-__device__ __forceinline__ double tpow_neg(double T, double p) {
-    if (p == 3.5) { double r = sqrt(T); return 1.0 / (T * T * T * r); }
-    if (p == 0.0) return 1.0;
+// row descriptor: base cell index of row (j, k) at x1 = 0, with flags
+__device__ int row_desc(const StageArgs &A, int j, int k) {
+    int fl = 0, ks = 0;
+    int jm = map_axis(A, 1, j, &fl, &ks);
+    int km = map_axis(A, 2, k, &fl, nullptr);
+    if (ks) km = (km + ks) % A.nx2;
+    return ((km * A.nx1 + jm) * A.nx0) | fl;
+}
+
+// ------------------------------------------------------------ temperature
+// Method 3 solved for the post-interaction radiation energy X = E* (see the
+// oracle): h(X) = (alpha(T) dt - B2 alpha^s) X - B1 - B2 eta alpha^a(T) a T^4,
+// T = T_- + (E-bar_- - X)/Y; h increases strictly on [0, W).
+template <typename R> struct Teq { R B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p; };
+
+template <typename R> __device__ __forceinline__ R tpow_neg(R T, R p) {
+    if (p == R(3.5)) { R r = sqrt(T); return R(1) / (T * T * T * r); }
+    if (p == R(0)) return R(1);
     return pow(T, -p);
 }
 
-__device__ __forceinline__ void teq_eval(const TeqArgs &q, double T, double *h, double *dh) {
-    double tp = tpow_neg(T, q.p);            // T^-p
-    double aa = q.au * tp;
-    double T3 = T * T * T, T4 = T3 * T;
-    double em = q.B2 * q.eta * q.arad * aa * T4;  // B2 eta au a T^(4-p)
-    double lin = (aa + q.as) * q.dt - q.B2 * q.as;
-    double gap = q.W - q.Y * T;
-    *h = lin * gap - q.B1 - em;
-    *dh = (-q.p * aa / T) * q.dt * gap - lin * q.Y - em * (4.0 - q.p) / T;
+template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, R X, R *h, R *dh) {
+    R T = q.Tm + (q.Em - X) / q.Y;
+    if (!(T > R(0))) { *h = R(1e30); *dh = R(1); return; }
+    R tp = tpow_neg(T, q.p);
+    R aa = q.au * tp;
+    R T4 = T * T * T * T;
+    R em = q.B2 * q.eta * q.arad * aa * T4;
+    R lin = (aa + q.as) * q.dt - q.B2 * q.as;
+    *h = lin * X - q.B1 - em;
+    // dh/dX with dT/dX = -1/Y
+    *dh = lin + (q.p * aa / T) * q.dt * X / q.Y + em * (R(4) - q.p) / (T * q.Y);
 }
 
-// safeguarded Newton on the bracket (lo, hi], h(lo) > 0 >= h(hi); h decreases
-__device__ bool solve_T(const TeqArgs &q, double T0, double *Tout) {
-    double hi = q.W / q.Y, lo;
-    double h, dh;
-    teq_eval(q, hi, &h, &dh);
-    if (h >= 0.0) { *Tout = hi; return true; }
-    double T = fmin(fmax(T0, 1e-300), hi);
-    teq_eval(q, T, &h, &dh);
-    if (h > 0.0) lo = T;
-    else {
-        hi = T; lo = T;
-        int it = 0;
-        do { lo *= 0.5; teq_eval(q, lo, &h, &dh); } while (!(h > 0.0) && ++it < 2200);
-        if (!(h > 0.0)) { *Tout = lo; return false; }
-        T = lo;
+// safeguarded Newton on [lo, hi] with h(lo) <= 0 < h(hi); returns converged flag
+template <typename R> __device__ bool newton_E(const Teq<R> &q, R X, R &lo, R &hi, int maxit, R tol, R *Xout) {
+    R h, dh;
+    for (int it = 0; it < maxit; ++it) {
+        teq_eval(q, X, &h, &dh);
+        if (h > R(0)) hi = fmin(hi, X); else lo = fmax(lo, X);
+        R Xn = X - h / dh;
+        if (!(Xn > lo && Xn < hi)) Xn = R(0.5) * (lo + hi);
+        R step = fabs(Xn - X);
+        X = Xn;
+        if (h == R(0) || step <= tol * X || hi - lo <= tol * hi) { *Xout = X; return true; }
     }
-    for (int it = 0; it < 200; ++it) {
-        double Tn = T - h / dh;
-        if (!(Tn > lo && Tn < hi)) Tn = (hi > 4.0 * lo) ? sqrt(lo * hi) : 0.5 * (lo + hi);
-        double step = fabs(Tn - T);
-        T = Tn;
-        teq_eval(q, T, &h, &dh);
-        if (h > 0.0) lo = T; else hi = T;
-        if (h == 0.0 || step <= 4.0 * 2.220446049250313e-16 * T || hi - lo <= 4.0 * 2.220446049250313e-16 * hi) {
-            *Tout = T;
-            return true;
-        }
-    }
-    *Tout = T;
+    *Xout = X;
     return false;
 }
 
-// ------------------------------------------------------------ the kernel
-template <typename TS, typename TM, bool FLAT>
-__global__ void __launch_bounds__(256) k_stage(const StageArgs A) {
+template <typename TS, typename TM, bool FLAT, int BY, int BZ>
+__global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
+    constexpr int TXC = NCELL / (BY * BZ);
+    constexpr int NOWN = BY * BZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nd = A.nd;
+    const int nd = A.nd, ndp = nd + 1;
     const int NT = blockDim.x;
     const int s = threadIdx.x;
     const bool act = s < nd;
-    const int nseg = (A.nx0 + TX - 1) / TX;
+    const int nseg = (A.nx0 + TXC - 1) / TXC;
     const int seg = blockIdx.x % nseg;
-    const int row = blockIdx.x / nseg;
-    const int j = row % A.nx1, k = row / A.nx1;
-    const int i0 = seg * TX;
-    const int nc = min(TX, A.nx0 - i0);
-    const int nfx = nc + 1;
-    const int nface = nfx + 4 * nc;
+    const int rest = blockIdx.x / nseg;
+    const int nyb = A.nx1 / BY;
+    const int j0 = (rest % nyb) * BY, k0 = (rest / nyb) * BZ;
+    const int i0 = seg * TXC;
+    const int nc = min(TXC, A.nx0 - i0);
 
-    // shared layout
-    TM *It = (TM *)smem_raw;                       // [TX][nd] transported
-    TM *Ip = It + TX * nd;                         // [TX][nd] after the interaction
-    TM *Rec = Ip + TX * nd;                        // [(5 TX + 1)][5] face coefficients
-    TM *Icell = Rec + (5 * TX + 1) * 5;            // [nd] (curved: angular stencil)
-    TM *Arec = Icell + nd;                         // [nd][6] reconstructed edge values
-    double *cs_ = (double *)(((uintptr_t)(Arec + 6 * nd) + 15) & ~(uintptr_t)15);   // per-cell scalars
-    double *sEm = cs_, *sB1 = cs_ + TX, *sB2 = cs_ + 2 * TX, *sEp = cs_ + 3 * TX, *sR = cs_ + 4 * TX;  // sR [TX][4]
-    TM *sN0 = (TM *)(cs_ + 8 * TX), *sEm2 = sN0 + TX, *sAd = sEm2 + TX;
-    int *sFlag = (int *)(sAd + TX);
+    // ---- shared layout
+    TM *It = (TM *)smem_raw;                                  // [NCELL][ndp]
+    TM *Ip = It + NCELL * ndp;                                // [NCELL][ndp]
+    TM *recX = Ip + NCELL * ndp;                              // [NOWN][TXC+1][5]
+    TM *recY = recX + NOWN * (TXC + 1) * 5;                   // [BZ][BY+1][TXC][5]
+    TM *recZ = recY + BZ * (BY + 1) * TXC * 5;                // [BY][BZ+1][TXC][5]
+    TM *scU = recZ + BY * (BZ + 1) * TXC * 5;                 // [NCELL][4] tetrad-frame fluid velocity
+    TM *scN0 = scU + 4 * NCELL, *scK = scN0 + NCELL, *scEm = scK + NCELL, *scA = scEm + NCELL;
+    TM *Icell = scA + NCELL;                                  // [NOWN][nd]   (curved only)
+    TM *Arec = Icell + (FLAT ? 0 : NOWN * nd);                // [NOWN][nd][6] (curved only)
+    double *part = (double *)(((uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)) + 15) & ~(uintptr_t)15);  // [8][NCELL][6]
+    double *sc64 = part + 8 * NCELL * 6;                      // [NCELL]: E-bar_-
+    int *xmap = (int *)(sc64 + NCELL);                        // [TXC+4]
+    int *rowY = xmap + TXC + 4;                               // [BZ][BY+4]
+    int *rowZ = rowY + BZ * (BY + 4);                         // [BY][BZ+4]
+    int *scOn = rowZ + BY * (BZ + 4);                         // [NCELL]
 
-    // --- face coefficients
+    // ---- boundary descriptors
+    for (int t = s; t < TXC + 4; t += NT) {
+        int fl = 0;
+        int im = map_axis(A, 0, i0 - 2 + t, &fl, nullptr);
+        xmap[t] = im | fl;
+    }
+    for (int t = s; t < BZ * (BY + 4); t += NT) {
+        int r = t / (BY + 4), q = t % (BY + 4);
+        rowY[t] = row_desc(A, j0 - 2 + q, k0 + r);
+    }
+    for (int t = s; t < BY * (BZ + 4); t += NT) {
+        int q = t / (BZ + 4), r = t % (BZ + 4);
+        rowZ[t] = row_desc(A, j0 + q, k0 - 2 + r);
+    }
+    __syncthreads();
+
+    // ---- face coefficients (direction independent)
+    auto coeffs = [&](int ax, int cl, int cr, double len, TM *rec) {
+        double al = A.alpha_in[cl], ar = A.alpha_in[cr];
+        double tau = A.abar * 0.5 * (al + ar) * (A.tau_dt ? A.dtk : len);
+        if (tau > 0.0) {
+            TM t = (TM)tau;
+            TM f = sqrt(-expm1(-t * t)) / t;
+            TM g = sqrt(-expm1(-t * t * t * t)) / t;
+            TM e = exp(-t), fg = f + g;
+            TM cadv = -expm1(-t);
+            rec[0] = f * e / fg; rec[1] = g * e / fg; rec[2] = f * g / fg;
+            rec[3] = cadv * (TM)fmax(A.vel[3 * (size_t)cl + ax], 0.0);
+            rec[4] = cadv * (TM)fmin(A.vel[3 * (size_t)cr + ax], 0.0);
+        } else {
+            rec[0] = TM(1); rec[1] = TM(0); rec[2] = TM(0); rec[3] = TM(0); rec[4] = TM(0);
+        }
+    };
+    auto plen = [&](int ax, int i, int j) -> double {
+        if (FLAT) return ax == 0 ? A.dx0 : (ax == 1 ? A.dx1 : A.dx2);
+        int npt = A.gn0 * (A.nx1 + 2 * A.ng1);
+        return A.pt_len[(size_t)ax * npt + (j + A.ng1) * A.gn0 + (i + A.ng0)];
+    };
     if (A.transport) {
-        for (int f = s; f < nface; f += NT) {
-            FaceRec R;
-            if (f < nfx) {
-                if (!A.act0) continue;
-                R = face_coeffs(A, FLAT, 0, i0 + f - 1, j, k);
+        const int nX = A.act0 ? NOWN * (nc + 1) : 0, nY = A.act1 ? BZ * (BY + 1) * nc : 0;
+        const int nZ = A.act2 ? BY * (BZ + 1) * nc : 0;
+        for (int t = s; t < nX + nY + nZ; t += NT) {
+            if (t < nX) {
+                int o = t / (nc + 1), f = t % (nc + 1);
+                int q = o % BY, r = o / BY;
+                int rb = rowY[r * (BY + 4) + q + 2] & F_MASK;
+                coeffs(0, rb + (xmap[f + 1] & F_MASK), rb + (xmap[f + 2] & F_MASK), plen(0, i0 + f, j0 + q),
+                       recX + (o * (TXC + 1) + f) * 5);
+            } else if (t < nX + nY) {
+                int u = t - nX, ii = u % nc, v = u / nc, f = v % (BY + 1), r = v / (BY + 1);
+                int rl = rowY[r * (BY + 4) + f + 1] & F_MASK, rr = rowY[r * (BY + 4) + f + 2] & F_MASK;
+                coeffs(1, rl + i0 + ii, rr + i0 + ii, plen(1, i0 + ii, j0 + f), recY + ((r * (BY + 1) + f) * TXC + ii) * 5);
+            } else {
+                int u = t - nX - nY, ii = u % nc, v = u / nc, f = v % (BZ + 1), q = v / (BZ + 1);
+                int rl = rowZ[q * (BZ + 4) + f + 1] & F_MASK, rr = rowZ[q * (BZ + 4) + f + 2] & F_MASK;
+                coeffs(2, rl + i0 + ii, rr + i0 + ii, plen(2, i0 + ii, j0 + q), recZ + ((q * (BZ + 1) + f) * TXC + ii) * 5);
             }
-            else {
-                int q = f - nfx, ii = q % nc, t = q / nc;   // t: 0 y-lower, 1 y-upper, 2 z-lower, 3 z-upper
-                int ax = 1 + t / 2, up = t & 1;
-                int jl = j, kl = k;
-                if (ax == 1) { if (!A.act1) continue; jl = up ? j : j - 1; }
-                else { if (!A.act2) continue; kl = up ? k : k - 1; }
-                R = face_coeffs(A, FLAT, ax, i0 + ii, jl, kl);
-            }
-            TM *r = Rec + 5 * f;
-            r[0] = (TM)R.c1; r[1] = (TM)R.c2; r[2] = (TM)R.c3; r[3] = (TM)R.kL; r[4] = (TM)R.kR;
         }
     }
     __syncthreads();
 
-    const int npt_stride = A.gn0 * (A.nx1 + 2 * A.ng1);
-    const size_t pd = (size_t)npt_stride * nd;
+    // ---- transport
+    const int npt = FLAT ? 1 : A.gn0 * (A.nx1 + 2 * A.ng1);
+    const size_t pd = (size_t)npt * nd;
+    const int smir = act ? __ldg(A.mirror + s) : 0;
+    TM nh[3] = {TM(0), TM(0), TM(0)};
+    if (act) for (int m = 0; m < 3; ++m) nh[m] = ldT<TM>(A.dirT, 3 * s + m);
+    const TM dtk = (TM)A.dtk;
+    const TM cdx[3] = {dtk / (TM)A.dx0, dtk / (TM)A.dx1, dtk / (TM)A.dx2};
+    const bool same_base = A.Isrc == A.Ibase;
 
-    // --- transport
-    for (int ii = 0; ii < nc; ++ii) {
-        const int i = i0 + ii;
-        const size_t cidx = ((size_t)k * A.nx1 + j) * A.nx0 + i;
-        const int pt = FLAT ? 0 : (j + A.ng1) * A.gn0 + (i + A.ng0);
-        TM Ic = TM(0), Ib = TM(0);
-        if (act) {
-            Ic = IO<TS, TM>::ld(A.Isrc, cidx * nd + s);
-            Ib = IO<TS, TM>::ld(A.Ibase, cidx * nd + s);
-        }
-        TM out = Ib;
-        if (A.transport) {
-            TM acc = TM(0);
-            TM nh[3] = {TM(0), TM(0), TM(0)};
-            if (act) for (int m = 0; m < 3; ++m) nh[m] = ldT<TM>(A.dirT, 3 * s + m);
-            for (int ax = 0; ax < 3; ++ax) {
-                int on = ax == 0 ? A.act0 : (ax == 1 ? A.act1 : A.act2);
-                if (!on || !act) continue;
-                int di = ax == 0, dj = ax == 1, dk = ax == 2;
-                TM v0 = load_I<TS, TM>(A, A.Isrc, i - 2 * di, j - 2 * dj, k - 2 * dk, s);
-                TM v1 = load_I<TS, TM>(A, A.Isrc, i - di, j - dj, k - dk, s);
-                TM v3 = load_I<TS, TM>(A, A.Isrc, i + di, j + dj, k + dk, s);
-                TM v4 = load_I<TS, TM>(A, A.Isrc, i + 2 * di, j + 2 * dj, k + 2 * dk, s);
-                TM sm = limiter<TM>(A.limiter, Ic - v1, v1 - v0);
-                TM s0 = limiter<TM>(A.limiter, v3 - Ic, Ic - v1);
-                TM sp = limiter<TM>(A.limiter, v4 - v3, v3 - Ic);
-                const TM *rlo, *rhi;
-                if (ax == 0) { rlo = Rec + 5 * ii; rhi = Rec + 5 * (ii + 1); }
+    auto ld_row = [&](int desc, int i) -> TM {      // direction s in row desc at interior x1 index i
+        if (desc & F_FIX) return TM(0);
+        int d = (desc & F_MIR) ? smir : s;
+        return IO<TS, TM>::ld(A.Isrc, (size_t)((desc & F_MASK) + i) * nd + d);
+    };
+    auto ld_x = [&](int rowbase, int xd, int jrow) -> TM {   // own row, x1 index from the descriptor
+        if (xd & F_FIX) return (s == A.beam_dir && jrow >= A.beam_lo && jrow < A.beam_hi) ? TM(A.beam_I) : TM(0);
+        int d = (xd & F_MIR) ? smir : s;
+        return IO<TS, TM>::ld(A.Isrc, (size_t)(rowbase + (xd & F_MASK)) * nd + d);
+    };
+    // curved-geometry face: flux = P phi with n^a and dA n_0 from the tables;
+    // no flux across a sign change of n_0 between the two cells (mask bit 1)
+    auto geo_face = [&](int ax, int pt_face, int pt_l, int pt_r, TM &n, TM &P) {
+        uint8_t ml = A.mask[(size_t)pt_l * nd + s], mr = A.mask[(size_t)pt_r * nd + s];
+        size_t o = (size_t)ax * pd + (size_t)pt_face * nd + s;
+        n = ldT<TM>(A.fn, o);
+        P = ((ml ^ mr) & 2) ? TM(0) : ldT<TM>(A.fP, o);
+    };
+
+    if (A.transport) {
+        // x1 sliding window per own row: value at i, i+1, slope at i, flux at i - 1/2
+        TM W0[NOWN], W1[NOWN], S0[NOWN], Flo[NOWN];
+#pragma unroll
+        for (int o = 0; o < NOWN; ++o) { W0[o] = W1[o] = S0[o] = Flo[o] = TM(0); }
+        if (act && A.act0) {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                const int q = o % BY, r = o / BY, jr = j0 + q;
+                const int rb = rowY[r * (BY + 4) + q + 2] & F_MASK;
+                TM Im2 = ld_x(rb, xmap[0], jr), Im1 = ld_x(rb, xmap[1], jr);
+                TM I0 = ld_x(rb, xmap[2], jr), I1 = ld_x(rb, xmap[3], jr);
+                TM sm1 = limiter<TM>(A.limiter, I0 - Im1, Im1 - Im2);
+                TM s0 = limiter<TM>(A.limiter, I1 - I0, I0 - Im1);
+                const TM *rc = recX + (o * (TXC + 1)) * 5;
+                TM IL = Im1 + TM(0.5) * sm1, IR = I0 - TM(0.5) * s0;
+                TM phi;
+                if (FLAT) phi = face_phi<TM>(nh[0], rc, IL, IR, Im1, I0);
                 else {
-                    int base = nfx + (ax == 1 ? 0 : 2 * nc);
-                    rlo = Rec + 5 * (base + ii); rhi = Rec + 5 * (base + nc + ii);
+                    TM n, P;
+                    int p0 = (jr + A.ng1) * A.gn0 + (i0 + A.ng0);
+                    geo_face(0, p0, p0 - 1, p0, n, P);
+                    phi = P * face_phi<TM>(n, rc, IL, IR, Im1, I0);
                 }
-                TM ILlo = v1 + TM(0.5) * sm, IRlo = Ic - TM(0.5) * s0;
-                TM ILhi = Ic + TM(0.5) * s0, IRhi = v3 - TM(0.5) * sp;
-                if (FLAT) {
-                    TM n = nh[ax];
-                    TM Flo = face_phi<TM>(n, rlo, ILlo, IRlo, v1, Ic);
-                    TM Fhi = face_phi<TM>(n, rhi, ILhi, IRhi, Ic, v3);
-                    TM dxa = TM(ax == 0 ? A.dx0 : (ax == 1 ? A.dx1 : A.dx2));
-                    acc += (Fhi - Flo) / dxa;
-                } else {
-                    // face points: lower face of this cell and of the next cell along ax
-                    int ptn = ax == 0 ? pt + 1 : (ax == 1 ? pt + A.gn0 : pt);
-                    int ptp = ax == 0 ? pt - 1 : (ax == 1 ? pt - A.gn0 : pt);
-                    size_t o = (size_t)ax * pd;
-                    uint8_t mc = A.mask[(size_t)pt * nd + s];
-                    uint8_t mlo = A.mask[(size_t)ptp * nd + s], mhi = A.mask[(size_t)ptn * nd + s];
-                    TM Flo = TM(0), Fhi = TM(0);
-                    if (((mlo ^ mc) & 2) == 0) {
-                        TM n = ldT<TM>(A.fn, o + (size_t)pt * nd + s), P = ldT<TM>(A.fP, o + (size_t)pt * nd + s);
-                        if (P != TM(0)) Flo = P * face_phi<TM>(n, rlo, ILlo, IRlo, v1, Ic);
+                W0[o] = I0; W1[o] = I1; S0[o] = s0; Flo[o] = phi;
+            }
+        }
+        for (int ii = 0; ii < nc; ++ii) {
+            const int i = i0 + ii;
+            TM acc[NOWN], Ic[NOWN];
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) { acc[o] = TM(0); Ic[o] = TM(0); }
+            if (act) {
+#pragma unroll
+                for (int o = 0; o < NOWN; ++o) {
+                    const int q = o % BY, r = o / BY;
+                    Ic[o] = A.act0 ? W0[o] : ld_row(rowY[r * (BY + 4) + q + 2], i);
+                }
+                if (A.act0) {
+#pragma unroll
+                    for (int o = 0; o < NOWN; ++o) {
+                        const int q = o % BY, r = o / BY, jr = j0 + q;
+                        const int rb = rowY[r * (BY + 4) + q + 2] & F_MASK;
+                        TM I2 = ld_x(rb, xmap[ii + 4], jr);
+                        TM s1 = limiter<TM>(A.limiter, I2 - W1[o], W1[o] - W0[o]);
+                        const TM *rc = recX + (o * (TXC + 1) + ii + 1) * 5;
+                        TM IL = W0[o] + TM(0.5) * S0[o], IR = W1[o] - TM(0.5) * s1;
+                        TM phi;
+                        if (FLAT) phi = face_phi<TM>(nh[0], rc, IL, IR, W0[o], W1[o]);
+                        else {
+                            TM n, P;
+                            int p1 = (jr + A.ng1) * A.gn0 + (i + 1 + A.ng0);
+                            geo_face(0, p1, p1 - 1, p1, n, P);
+                            phi = P * face_phi<TM>(n, rc, IL, IR, W0[o], W1[o]);
+                        }
+                        acc[o] += FLAT ? cdx[0] * (phi - Flo[o]) : (phi - Flo[o]);
+                        Flo[o] = phi; W0[o] = W1[o]; W1[o] = I2; S0[o] = s1;
                     }
-                    if (((mhi ^ mc) & 2) == 0) {
-                        TM n = ldT<TM>(A.fn, o + (size_t)ptn * nd + s), P = ldT<TM>(A.fP, o + (size_t)ptn * nd + s);
-                        if (P != TM(0)) Fhi = P * face_phi<TM>(n, rhi, ILhi, IRhi, Ic, v3);
+                }
+                if (A.act1) {
+#pragma unroll
+                    for (int r = 0; r < BZ; ++r) {
+                        TM Y[BY + 4], sy[BY + 4], F[BY + 1];
+#pragma unroll
+                        for (int q = 0; q < BY + 4; ++q)
+                            Y[q] = (q >= 2 && q < BY + 2) ? Ic[r * BY + q - 2] : ld_row(rowY[r * (BY + 4) + q], i);
+                        sy[0] = sy[BY + 3] = TM(0);
+#pragma unroll
+                        for (int q = 1; q < BY + 3; ++q) sy[q] = limiter<TM>(A.limiter, Y[q + 1] - Y[q], Y[q] - Y[q - 1]);
+#pragma unroll
+                        for (int f = 0; f <= BY; ++f) {
+                            const TM *rc = recY + ((r * (BY + 1) + f) * TXC + ii) * 5;
+                            TM IL = Y[f + 1] + TM(0.5) * sy[f + 1], IR = Y[f + 2] - TM(0.5) * sy[f + 2];
+                            if (FLAT) F[f] = face_phi<TM>(nh[1], rc, IL, IR, Y[f + 1], Y[f + 2]);
+                            else {
+                                TM n, P;
+                                int pu = (j0 + f + A.ng1) * A.gn0 + (i + A.ng0);
+                                geo_face(1, pu, pu - A.gn0, pu, n, P);
+                                F[f] = P * face_phi<TM>(n, rc, IL, IR, Y[f + 1], Y[f + 2]);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < BY; ++q) acc[r * BY + q] += FLAT ? cdx[1] * (F[q + 1] - F[q]) : (F[q + 1] - F[q]);
                     }
-                    acc += Fhi - Flo;
+                }
+                if (A.act2) {
+#pragma unroll
+                    for (int q = 0; q < BY; ++q) {
+                        TM Z[BZ + 4], sz[BZ + 4], F[BZ + 1];
+#pragma unroll
+                        for (int r = 0; r < BZ + 4; ++r)
+                            Z[r] = (r >= 2 && r < BZ + 2) ? Ic[(r - 2) * BY + q] : ld_row(rowZ[q * (BZ + 4) + r], i);
+                        sz[0] = sz[BZ + 3] = TM(0);
+#pragma unroll
+                        for (int r = 1; r < BZ + 3; ++r) sz[r] = limiter<TM>(A.limiter, Z[r + 1] - Z[r], Z[r] - Z[r - 1]);
+#pragma unroll
+                        for (int f = 0; f <= BZ; ++f) {
+                            const TM *rc = recZ + ((q * (BZ + 1) + f) * TXC + ii) * 5;
+                            TM IL = Z[f + 1] + TM(0.5) * sz[f + 1], IR = Z[f + 2] - TM(0.5) * sz[f + 2];
+                            if (FLAT) F[f] = face_phi<TM>(nh[2], rc, IL, IR, Z[f + 1], Z[f + 2]);
+                            else {
+                                TM n, P;
+                                int pc = (j0 + q + A.ng1) * A.gn0 + (i + A.ng0);
+                                geo_face(2, pc, pc, pc, n, P);
+                                F[f] = P * face_phi<TM>(n, rc, IL, IR, Z[f + 1], Z[f + 2]);
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < BZ; ++r) acc[r * BY + q] += FLAT ? cdx[2] * (F[r + 1] - F[r]) : (F[r + 1] - F[r]);
+                    }
                 }
             }
-            if (FLAT) {
-                out = Ib - TM(A.dtk) * acc;
-            } else {
-                TM ang = TM(0);
-                // angular flux across the Voronoi edges of direction s
-                if (act) Icell[s] = Ic;
+            // angular flux (curved geometry): minimum-angle plane reconstruction
+            // of every direction at the edge midpoints, edge fluxes with the
+            // upwind side of n_0(m) v(m).u_e (eq. angular_fluxes)
+            TM ang[NOWN];
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) ang[o] = TM(0);
+            if (!FLAT) {
+                if (act)
+                    for (int o = 0; o < NOWN; ++o) Icell[o * nd + s] = Ic[o];
                 __syncthreads();
                 int kk = act ? __ldg(A.nnb + s) : 0;
                 if (act) {
-                    TM rec[RT_MAXNB];
-                    if (A.ang_recon == 1) {
-                        for (int q = 0; q < kk; ++q) rec[q] = Ic;
-                    } else {
-                        TM dI[RT_MAXNB];
-                        for (int q = 0; q < kk; ++q) dI[q] = Icell[__ldg(A.nbr + 6 * s + q)] - Ic;
-                        int best = -1; TM bn = TM(0), ba = TM(0), bb = TM(0);
-                        for (int q = 0; q < kk; ++q) {
-                            int q1 = q + 1 == kk ? 0 : q + 1;
-                            const size_t o = (size_t)(6 * s + q) * 3;
-                            TM ga = ldT<TM>(A.mgT, o), gb = ldT<TM>(A.mgT, o + 1), gc = ldT<TM>(A.mgT, o + 2);
-                            TM al = ga * dI[q] + gb * dI[q1];
-                            TM be = gb * dI[q] + gc * dI[q1];
-                            TM nr = al * dI[q] + be * dI[q1];
-                            if (best < 0 || nr < bn) { best = q; bn = nr; ba = al; bb = be; }
+                    for (int o = 0; o < NOWN; ++o) {
+                        TM rec[RT_MAXNB];
+                        if (A.ang_recon == 1) {
+                            for (int q = 0; q < kk; ++q) rec[q] = Ic[o];
+                        } else {
+                            TM dI[RT_MAXNB], al[RT_MAXNB], be[RT_MAXNB], nr[RT_MAXNB];
+                            for (int q = 0; q < kk; ++q) dI[q] = Icell[o * nd + __ldg(A.nbr + 6 * s + q)] - Ic[o];
+                            TM mn = TM(0);
+                            for (int q = 0; q < kk; ++q) {
+                                int q1 = q + 1 == kk ? 0 : q + 1;
+                                const size_t og = (size_t)(6 * s + q) * 3;
+                                TM ga = ldT<TM>(A.mgT, og), gb = ldT<TM>(A.mgT, og + 1), gc = ldT<TM>(A.mgT, og + 2);
+                                al[q] = ga * dI[q] + gb * dI[q1];
+                                be[q] = gb * dI[q] + gc * dI[q1];
+                                nr[q] = al[q] * dI[q] + be[q] * dI[q1];
+                                if (q == 0 || nr[q] < mn) mn = nr[q];
+                            }
+                            // near-equal norms tie (mirror-symmetric neighbourhoods); first in ring order wins
+                            int best = 0;
+                            while (best + 1 < kk && !(nr[best] <= mn + TM(1e-6) * fabs(mn))) ++best;
+                            int b1 = best + 1 == kk ? 0 : best + 1;
+                            const size_t ox0 = (size_t)(6 * s + best) * 3, ox1 = (size_t)(6 * s + b1) * 3;
+                            TM x0[3], x1[3];
+                            for (int m = 0; m < 3; ++m) { x0[m] = ldT<TM>(A.mxT, ox0 + m); x1[m] = ldT<TM>(A.mxT, ox1 + m); }
+                            for (int q = 0; q < kk; ++q) {
+                                const size_t om = (size_t)(6 * s + q) * 3;
+                                TM xm0 = ldT<TM>(A.mmT, om), xm1 = ldT<TM>(A.mmT, om + 1), xm2 = ldT<TM>(A.mmT, om + 2);
+                                rec[q] = Ic[o] + al[best] * (x0[0] * xm0 + x0[1] * xm1 + x0[2] * xm2) +
+                                         be[best] * (x1[0] * xm0 + x1[1] * xm1 + x1[2] * xm2);
+                            }
                         }
-                        int b1 = best + 1 == kk ? 0 : best + 1;
-                        const size_t ox0 = (size_t)(6 * s + best) * 3, ox1 = (size_t)(6 * s + b1) * 3;
-                        TM x0[3], x1[3];
-                        for (int m = 0; m < 3; ++m) { x0[m] = ldT<TM>(A.mxT, ox0 + m); x1[m] = ldT<TM>(A.mxT, ox1 + m); }
-                        for (int q = 0; q < kk; ++q) {
-                            const size_t om = (size_t)(6 * s + q) * 3;
-                            TM xm0 = ldT<TM>(A.mmT, om), xm1 = ldT<TM>(A.mmT, om + 1), xm2 = ldT<TM>(A.mmT, om + 2);
-                            TM p0 = x0[0] * xm0 + x0[1] * xm1 + x0[2] * xm2;
-                            TM p1 = x1[0] * xm0 + x1[1] * xm1 + x1[2] * xm2;
-                            rec[q] = Ic + ba * p0 + bb * p1;
-                        }
+                        for (int q = 0; q < kk; ++q) Arec[(o * nd + s) * 6 + q] = rec[q];
                     }
-                    for (int q = 0; q < kk; ++q) Arec[6 * s + q] = rec[q];
                 }
                 __syncthreads();
                 if (act) {
-                    for (int q = 0; q < kk; ++q) {
-                        int e = __ldg(A.ring_edge + 6 * s + q), t = __ldg(A.nbr + 6 * s + q);
-                        int back = __ldg(A.ring_back + 6 * s + q);
-                        bool own = __ldg(A.edge + 2 * e) == s;
-                        TM w = ldT<TM>(A.ew, (size_t)pt * A.ne + e);
-                        TM Io = Arec[6 * s + q], It2 = Arec[6 * t + back];
-                        TM IL = own ? Io : It2, IR = own ? It2 : Io;
-                        TM F = w * (w > TM(0) ? IL : IR);
-                        ang += own ? F : -F;
+                    TM winv = TM(1) / ldT<TM>(A.wT, s);
+                    for (int o = 0; o < NOWN; ++o) {
+                        const int pc = (j0 + o % BY + A.ng1) * A.gn0 + (i + A.ng0);
+                        TM a = TM(0);
+                        for (int q = 0; q < kk; ++q) {
+                            int e = __ldg(A.ring_edge + 6 * s + q), t = __ldg(A.nbr + 6 * s + q);
+                            int back = __ldg(A.ring_back + 6 * s + q);
+                            bool own = __ldg(A.edge + 2 * e) == s;
+                            TM w = ldT<TM>(A.ew, (size_t)pc * A.ne + e);
+                            TM Io = Arec[(o * nd + s) * 6 + q], It2 = Arec[(o * nd + t) * 6 + back];
+                            TM IL = own ? Io : It2, IR = own ? It2 : Io;
+                            TM F = w * (w > TM(0) ? IL : IR);
+                            a += own ? F : -F;
+                        }
+                        ang[o] = a * winv;
                     }
-                    ang /= ldT<TM>(A.wT, s);
                 }
                 __syncthreads();
-                if (act) {
-                    TM U = ldT<TM>(A.cenU, (size_t)pt * nd + s);
-                    TM V = TM(A.pt_V[pt]);
-                    TM Un = U * Ib - TM(A.dtk) * (acc / V + ang);
-                    out = Un / U;
+            }
+            if (act) {
+#pragma unroll
+                for (int o = 0; o < NOWN; ++o) {
+                    const int q = o % BY, r = o / BY, j = j0 + q, k = k0 + r;
+                    const size_t cidx = ((size_t)k * A.nx1 + j) * A.nx0 + i;
+                    TM Ib = same_base ? Ic[o] : IO<TS, TM>::ld(A.Ibase, cidx * nd + s);
+                    TM out;
+                    bool zero = A.n_pole_zero > 0 && (j < A.n_pole_zero || j >= A.nx1 - A.n_pole_zero);
+                    if (FLAT) out = Ib - acc[o];
+                    else {
+                        const int pc = (j + A.ng1) * A.gn0 + (i + A.ng0);
+                        TM U = ldT<TM>(A.cenU, (size_t)pc * nd + s);
+                        TM V = (TM)A.pt_V[pc];
+                        out = (U * Ib - dtk * (acc[o] / V + ang[o])) / U;
+                        zero = zero || (A.mask[(size_t)pc * nd + s] & 1);
+                    }
+                    It[((r * BY + q) * TXC + ii) * ndp + s] = zero ? TM(0) : out;
                 }
             }
         }
-        if (act) {
-            bool zero = false;
-            if (A.transport) {
-                if (!FLAT) zero = (A.mask[(size_t)pt * nd + s] & 1) != 0;
-                if (A.n_pole_zero > 0 && (j < A.n_pole_zero || j >= A.nx1 - A.n_pole_zero)) zero = true;
+    } else if (act) {
+        for (int o = 0; o < NOWN; ++o)
+            for (int ii = 0; ii < nc; ++ii) {
+                const int q = o % BY, r = o / BY;
+                const size_t cidx = ((size_t)(k0 + r) * A.nx1 + j0 + q) * A.nx0 + i0 + ii;
+                It[(o * TXC + ii) * ndp + s] = IO<TS, TM>::ld(A.Ibase, cidx * nd + s);
             }
-            It[ii * nd + s] = zero ? TM(0) : out;
-        }
     }
-    __syncthreads();
 
-    // --- interaction (section 3.5.2)
-    const int lane8 = threadIdx.x & (GS - 1);
-    const int cpp = NT / GS;      // cells per pass
-    for (int c0 = 0; c0 < nc; c0 += cpp) {
-        int ci = c0 + threadIdx.x / GS;
-        TM Em = 0, B1 = 0, B2 = 0, cEm = 0;
-        bool on = false;
-        if (ci < nc) {
-            const int i = i0 + ci;
-            const size_t cidx = ((size_t)k * A.nx1 + j) * A.nx0 + i;
-            const int pt = FLAT ? 0 : (j + A.ng1) * A.gn0 + (i + A.ng0);
-            double rho = A.rho[cidx], ug = A.ug_in[cidx];
-            double Y = rho / (A.gam - 1.0), Tm = ug / Y;
-            double au = A.kap[cidx] * pow(rho, A.rho_exp), as = A.cs[cidx] * rho;
-            double atm = (Tm > 0.0) ? au * tpow_neg(Tm, A.T_exp) + as : 0.0;
-            on = A.source && rho >= A.rho_floor && rho > 0.0 && atm > 0.0;
-            TM u0 = TM(A.uhat[4 * cidx]), u1 = TM(A.uhat[4 * cidx + 1]), u2 = TM(A.uhat[4 * cidx + 2]),
-               u3 = TM(A.uhat[4 * cidx + 3]);
-            TM n0 = FLAT ? TM(1) : TM(A.pt_n0[pt]);
-            TM adt = TM(atm * A.dtk);
-            if (on) {
-                for (int d = lane8; d < nd; d += GS) {
-                    TM x = ldT<TM>(A.dirT, 3 * d), y = ldT<TM>(A.dirT, 3 * d + 1), z = ldT<TM>(A.dirT, 3 * d + 2);
-                    TM D = u0 - (u1 * x + u2 * y + u3 * z);
-                    TM w = ldT<TM>(A.wT, d);
-                    TM t = D * D * It[ci * nd + d] * w;
-                    // compensated sum of the comoving energy
-                    TM yk = t - cEm, tk = Em + yk;
-                    cEm = (tk - Em) - yk; Em = tk;
-                    TM K = adt / (n0 + D * adt);
+    // ---- interaction (section 3.5.2); local cell lc = (r BY + q) TXC + ii
+    auto gcell = [&](int lc, int &ii, int &j) -> size_t {
+        ii = lc % TXC;
+        int o = lc / TXC;
+        j = j0 + o % BY;
+        int k = k0 + o / BY;
+        return ((size_t)k * A.nx1 + j) * A.nx0 + i0 + ii;
+    };
+    int all_static = 1;
+    if (s < NCELL) {
+        int ii, j;
+        size_t cidx = gcell(s, ii, j);
+        int on = 0;
+        if (ii < nc) {
+            double Y = A.cc_Y[cidx], ug = A.ug_in[cidx], am = A.alpha_int[cidx];
+            double Tm = Y > 0.0 ? ug / Y : 0.0;
+            on = A.source && A.cc_on[cidx] && am > 0.0 && Tm > 0.0;
+            const int pc = FLAT ? 0 : (j + A.ng1) * A.gn0 + (i0 + ii + A.ng0);
+            double n0 = FLAT ? 1.0 : A.pt_n0[pc];
+            for (int m = 0; m < 4; ++m) scU[4 * s + m] = (TM)A.uhat[4 * cidx + m];
+            scN0[s] = (TM)n0;
+            scK[s] = (TM)(am * A.dtk);
+            if (on && !(A.uhat[4 * cidx + 1] == 0.0 && A.uhat[4 * cidx + 2] == 0.0 && A.uhat[4 * cidx + 3] == 0.0 &&
+                        A.uhat[4 * cidx] == 1.0 && n0 == 1.0))
+                all_static = 0;
+        }
+        scOn[s] = on;
+    }
+    all_static = __syncthreads_and(all_static);
+
+    // angular sums in direction chunks: E-bar_- (compensated), B1, B2 (eqs.
+    // A1, A2 in the reading of method 3); K = alpha_- dt / (n^0 + D alpha_- dt)
+    const int nchunk = NT / 32;
+    {
+        const int c = s & 31, g = s >> 5;
+        TM Em = 0, cEm = 0, B1 = 0, B2 = 0;
+        if ((c % TXC) < nc && scOn[c]) {
+            const TM u0 = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
+            const TM n0 = scN0[c], adt = scK[c];
+            const TM *row = It + c * ndp;
+            for (int d = g; d < nd; d += nchunk) {
+                TM w = ldT<TM>(A.wT, d);
+                TM t;
+                if (all_static) t = row[d] * w;
+                else {
+                    TM D = u0 - (u1 * ldT<TM>(A.dirT, 3 * d) + u2 * ldT<TM>(A.dirT, 3 * d + 1) + u3 * ldT<TM>(A.dirT, 3 * d + 2));
+                    t = D * D * row[d] * w;
+                    TM K = dv<TM>(adt, n0 + D * adt);
                     B1 += n0 * K * t;
-                    B2 += K * w / D;
+                    B2 += dv<TM>(K * w, D);
                 }
+                TM yk = t - cEm, tk = Em + yk;
+                cEm = (tk - Em) - yk; Em = tk;
             }
         }
-        // every lane of the warp takes part in the shuffles (idle groups add zeros)
-        double dEm = (double)Em - (double)cEm, dB1 = B1, dB2 = B2;
-        for (int o = 1; o < GS; o <<= 1) {
-            dEm += __shfl_xor_sync(0xffffffffu, dEm, o);
-            dB1 += __shfl_xor_sync(0xffffffffu, dB1, o);
-            dB2 += __shfl_xor_sync(0xffffffffu, dB2, o);
+        double *pp = part + (g * NCELL + c) * 6;
+        pp[0] = (double)Em - (double)cEm; pp[1] = B1; pp[2] = B2;
+    }
+    __syncthreads();
+    // one lane per cell: temperature solve and per-cell update constants
+    if (s < NCELL) {
+        int ii, j;
+        size_t cidx = gcell(s, ii, j);
+        if (ii < nc && scOn[s]) {
+            double Em = 0, B1 = 0, B2 = 0;
+            for (int g = 0; g < nchunk; ++g) {
+                const double *pp = part + (g * NCELL + s) * 6;
+                Em += pp[0]; B1 += pp[1]; B2 += pp[2];
+            }
+            const double dt = A.dtk, adt = A.alpha_int[cidx] * dt;
+            if (all_static) {        // D = 1, n^0 = 1: K is per cell
+                double K = adt / (1.0 + adt);
+                B1 = K * Em;
+                B2 = K * A.sumw;
+            }
+            B2 *= dt / FOURPI;
+            const double Y = A.cc_Y[cidx], ug = A.ug_in[cidx], Tm = ug / Y;
+            Teq<double> q{B1, B2, Em + ug, Y, Tm, Em, A.cc_au[cidx], A.cc_as[cidx], A.eta[cidx], A.arad, dt, A.T_exp};
+            double lo = 0.0, hi = q.W, X;
+            bool ok;
+            if (sizeof(TM) == 4) {
+                // FP32 Newton iterations, then one FP64 Newton step
+                Teq<float> qf{(float)q.B1, (float)q.B2, (float)q.W, (float)q.Y, (float)q.Tm, (float)q.Em, (float)q.au,
+                              (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p};
+                float flo = 0.0f, fhi = (float)q.W, fx;
+                newton_E<float>(qf, (float)Em, flo, fhi, 60, 1e-7f, &fx);
+                double h, dh;
+                teq_eval<double>(q, (double)fx, &h, &dh);
+                X = (double)fx - h / dh;
+                ok = X >= 0.0 && X < q.W && Tm + (Em - X) / Y > 0.0;
+                if (!ok) ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
+            } else {
+                ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
+            }
+            if (!ok) atomicAdd(A.fail, 1ull);
+            const double Tp = Tm + (Em - X) / Y;
+            const double aap = A.cc_au[cidx] * tpow_neg<double>(Tp, A.T_exp), atp = aap + A.cc_as[cidx];
+            const double em = A.eta[cidx] * aap * A.arad * Tp * Tp * Tp * Tp + A.cc_as[cidx] * X;
+            sc64[s] = Em;
+            scEm[s] = (TM)(dt * em / FOURPI);
+            scA[s] = (TM)(atp * dt);
         }
-        if (ci < nc && lane8 == 0) { sEm[ci] = dEm; sB1[ci] = dB1; sB2[ci] = dB2; sFlag[ci] = on; }
     }
     __syncthreads();
-    // one lane per cell: FP64 temperature solve and per-cell update constants
-    for (int ci = threadIdx.x; ci < nc; ci += NT) {
-        const int i = i0 + ci;
-        const size_t cidx = ((size_t)k * A.nx1 + j) * A.nx0 + i;
-        const int pt = FLAT ? 0 : (j + A.ng1) * A.gn0 + (i + A.ng0);
-        double n0 = FLAT ? 1.0 : A.pt_n0[pt];
-        sN0[ci] = (TM)n0;
-        if (!sFlag[ci]) { sEm2[ci] = TM(0); sAd[ci] = TM(0); continue; }
-        double rho = A.rho[cidx], ug = A.ug_in[cidx];
-        double Y = rho / (A.gam - 1.0), Tm = ug / Y;
-        double au = A.kap[cidx] * pow(rho, A.rho_exp), as = A.cs[cidx] * rho;
-        TeqArgs q{sB1[ci], sB2[ci] * A.dtk / FOURPI, sEm[ci] + Y * Tm, Y, au, as, A.eta[cidx], A.arad, A.dtk, A.T_exp};
-        double Tp;
-        if (!solve_T(q, Tm, &Tp)) atomicAdd(A.fail, 1ull);
-        double Est = q.W - Y * Tp;
-        double aap = au * tpow_neg(Tp, A.T_exp), atp = aap + as;
-        double em = q.eta * aap * A.arad * Tp * Tp * Tp * Tp + as * Est;
-        sEm2[ci] = (TM)(A.dtk * em / FOURPI);
-        sAd[ci] = (TM)(atp * A.dtk);
-    }
-    __syncthreads();
-    // per-direction update, store
-    for (int ci = 0; ci < nc; ++ci) {
-        const int i = i0 + ci;
-        const size_t cidx = ((size_t)k * A.nx1 + j) * A.nx0 + i;
-        if (!act) continue;
-        TM It0 = It[ci * nd + s];
-        TM v = It0;
-        if (sFlag[ci]) {
-            const int pt = FLAT ? 0 : (j + A.ng1) * A.gn0 + (i + A.ng0);
-            TM x = ldT<TM>(A.dirT, 3 * s), y = ldT<TM>(A.dirT, 3 * s + 1), z = ldT<TM>(A.dirT, 3 * s + 2);
-            TM D = TM(A.uhat[4 * cidx]) - (TM(A.uhat[4 * cidx + 1]) * x + TM(A.uhat[4 * cidx + 2]) * y +
-                                           TM(A.uhat[4 * cidx + 3]) * z);
-            v = (sN0[ci] * It0 + sEm2[ci] / (D * D * D)) / (sN0[ci] + D * sAd[ci]);
-            bool zero = false;
-            if (!FLAT) zero = (A.mask[(size_t)pt * nd + s] & 1) != 0;
-            if (A.n_pole_zero > 0 && (j < A.n_pole_zero || j >= A.nx1 - A.n_pole_zero)) zero = true;
-            if (zero) v = TM(0);
+    // per-direction update (eq. fluid_interaction_discrete with alpha(T_+) and
+    // emission at T_+), masks, store
+    if (act) {
+        for (int lc = 0; lc < NCELL; ++lc) {
+            int ii, j;
+            size_t cidx = gcell(lc, ii, j);
+            if (ii >= nc) continue;
+            TM v = It[lc * ndp + s];
+            if (scOn[lc]) {
+                if (all_static) v = (v + scEm[lc]) / (TM(1) + scA[lc]);
+                else {
+                    TM D = scU[4 * lc] - (scU[4 * lc + 1] * nh[0] + scU[4 * lc + 2] * nh[1] + scU[4 * lc + 3] * nh[2]);
+                    TM n0 = scN0[lc];
+                    v = dv<TM>(n0 * v + dv<TM>(scEm[lc], D * D * D), n0 + D * scA[lc]);
+                }
+                bool zero = A.n_pole_zero > 0 && (j < A.n_pole_zero || j >= A.nx1 - A.n_pole_zero);
+                if (!FLAT) zero = zero || (A.mask[(size_t)((j + A.ng1) * A.gn0 + (i0 + ii + A.ng0)) * nd + s] & 1);
+                if (zero) v = TM(0);
+            }
+            Ip[lc * ndp + s] = IO<TS, TM>::st(A.Iout, cidx * nd + s, v);
         }
-        Ip[ci * nd + s] = IO<TS, TM>::st(A.Iout, cidx * nd + s, v);
     }
     __syncthreads();
-    // exchange ledger and force on the gas
-    for (int c0 = 0; c0 < nc; c0 += cpp) {
-        int ci = c0 + threadIdx.x / GS;
-        bool valid = ci < nc;
-        int cc = valid ? ci : 0;
-        const int i = i0 + cc;
-        const size_t cidx = ((size_t)k * A.nx1 + j) * A.nx0 + i;
-        bool on = valid && sFlag[cc];
+    // exchange ledger: E-bar(I_+) and Delta R^{0 a} in direction chunks
+    {
+        const int c = s & 31, g = s >> 5;
         TM Ep = 0, cEp = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-        if (on) {
-            TM u0 = TM(A.uhat[4 * cidx]), u1 = TM(A.uhat[4 * cidx + 1]), u2 = TM(A.uhat[4 * cidx + 2]),
-               u3 = TM(A.uhat[4 * cidx + 3]);
-            for (int d = lane8; d < nd; d += GS) {
-                TM x = ldT<TM>(A.dirT, 3 * d), y = ldT<TM>(A.dirT, 3 * d + 1), z = ldT<TM>(A.dirT, 3 * d + 2);
+        if ((c % TXC) < nc && scOn[c]) {
+            const TM u0 = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
+            const TM *rp = Ip + c * ndp, *rt = It + c * ndp;
+            for (int d = g; d < nd; d += nchunk) {
                 TM w = ldT<TM>(A.wT, d);
-                TM D = u0 - (u1 * x + u2 * y + u3 * z);
-                TM ip = Ip[cc * nd + d];
-                TM t = D * D * ip * w;
+                TM x = ldT<TM>(A.dirT, 3 * d), y = ldT<TM>(A.dirT, 3 * d + 1), z = ldT<TM>(A.dirT, 3 * d + 2);
+                TM D = all_static ? TM(1) : u0 - (u1 * x + u2 * y + u3 * z);
+                TM t = D * D * rp[d] * w;
                 TM yk = t - cEp, tk = Ep + yk;
                 cEp = (tk - Ep) - yk; Ep = tk;
-                TM dI = (ip - It[cc * nd + d]) * w;
+                TM dI = (rp[d] - rt[d]) * w;
                 r0 += dI; r1 += x * dI; r2 += y * dI; r3 += z * dI;
             }
         }
-        double dEp = (double)Ep - (double)cEp, d0 = r0, d1 = r1, d2 = r2, d3 = r3;
-        for (int o = 1; o < GS; o <<= 1) {
-            dEp += __shfl_xor_sync(0xffffffffu, dEp, o);
-            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-            d3 += __shfl_xor_sync(0xffffffffu, d3, o);
-        }
-        if (valid && lane8 == 0) {
+        double *pp = part + (g * NCELL + c) * 6;
+        pp[0] = (double)Ep - (double)cEp; pp[1] = r0; pp[2] = r1; pp[3] = r2; pp[4] = r3;
+    }
+    __syncthreads();
+    if (s < NCELL) {
+        int ii, j;
+        size_t cidx = gcell(s, ii, j);
+        if (ii < nc) {
             double ugm = A.ug_in[cidx];
-            double ugp = on ? ugm - (dEp - sEm[cc]) : ugm;
-            A.ug_out[cidx] = ugp;
-            A.alpha_out[cidx] = cell_alpha(A, A.rho[cidx], ugp, A.kap[cidx], A.cs[cidx]);
-            if (A.G) {
-                double dR[4] = {d0, d1, d2, d3};
-                if (!on) dR[0] = dR[1] = dR[2] = dR[3] = 0.0;
-                for (int m = 0; m < 4; ++m) {
-                    double g;
-                    if (FLAT) g = dR[m];
-                    else {
-                        const int pt = (j + A.ng1) * A.gn0 + (i + A.ng0);
-                        const double *E = A.pt_e + 16 * (size_t)pt;
-                        g = E[m] * dR[0] + E[4 + m] * dR[1] + E[8 + m] * dR[2] + E[12 + m] * dR[3];
-                    }
-                    A.G[4 * cidx + m] = -g / A.dtk;
+            if (scOn[s]) {
+                double Ep = 0, dR[4] = {0, 0, 0, 0};
+                for (int g = 0; g < nchunk; ++g) {
+                    const double *pp = part + (g * NCELL + s) * 6;
+                    Ep += pp[0]; dR[0] += pp[1]; dR[1] += pp[2]; dR[2] += pp[3]; dR[3] += pp[4];
                 }
+                double ugp = ugm - (Ep - sc64[s]);
+                A.ug_out[cidx] = ugp;
+                double T = ugp / A.cc_Y[cidx];
+                A.alpha_out[cidx] = T > 0.0 ? A.cc_au[cidx] * tpow_neg<double>(T, A.T_exp) + A.cc_as[cidx] : 0.0;
+                if (A.G) {
+                    for (int m = 0; m < 4; ++m) {
+                        double gm;
+                        if (FLAT) gm = dR[m];
+                        else {
+                            const double *E = A.pt_e + 16 * (size_t)((j + A.ng1) * A.gn0 + (i0 + ii + A.ng0));
+                            gm = E[m] * dR[0] + E[4 + m] * dR[1] + E[8 + m] * dR[2] + E[12 + m] * dR[3];
+                        }
+                        A.G[4 * cidx + m] = -gm / A.dtk;
+                    }
+                }
+            } else {
+                A.ug_out[cidx] = ugm;
+                A.alpha_out[cidx] = A.alpha_int[cidx];
+                if (A.G) for (int m = 0; m < 4; ++m) A.G[4 * cidx + m] = 0.0;
             }
         }
     }
 }
 
-__global__ void k_alpha(int ncell, double gam, double rho_floor, double rho_exp, double T_exp,
-                        const double *__restrict__ rho, const double *__restrict__ ug, const double *__restrict__ kap,
-                        const double *__restrict__ cs, double *__restrict__ alpha) {
+__global__ void k_alpha(int ncell, double T_exp, const double *__restrict__ cc_au, const double *__restrict__ cc_as,
+                        const double *__restrict__ cc_Y, const uint8_t *__restrict__ cc_on,
+                        const double *__restrict__ ug, double *__restrict__ alpha) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    double T = cc_Y[c] > 0.0 ? ug[c] / cc_Y[c] : 0.0;
+    alpha[c] = (cc_on[c] && T > 0.0) ? cc_au[c] * tpow_neg<double>(T, T_exp) + cc_as[c] : 0.0;
+}
+
+// per-cell constants of the fluid: alpha^a prefactor kappa rho^m, alpha^s,
+// Y = rho/(Gamma - 1), and the density-floor switch (section 3.7)
+__global__ void k_cellconst(int ncell, double gam, double rho_exp, double rho_floor, const double *__restrict__ rho,
+                            const double *__restrict__ kap, const double *__restrict__ cs, double *__restrict__ au,
+                            double *__restrict__ as, double *__restrict__ Y, uint8_t *__restrict__ on) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     double r = rho[c];
-    if (!(r >= rho_floor) || r <= 0.0) { alpha[c] = 0.0; return; }
-    double T = (gam - 1.0) * ug[c] / r;
-    alpha[c] = kap[c] * pow(r, rho_exp) * pow(T, -T_exp) + cs[c] * r;
+    bool ok = r >= rho_floor && r > 0.0;
+    on[c] = ok;
+    au[c] = ok ? kap[c] * pow(r, rho_exp) : 0.0;
+    as[c] = ok ? cs[c] * r : 0.0;
+    Y[c] = r / (gam - 1.0);
 }
 
-template <typename TS, typename TM, bool FLAT>
+template <typename TS, typename TM, bool FLAT, int BY, int BZ>
 rt_status launch(rt_ctx *c, const StageArgs &A, int NT) {
-    size_t smem = sizeof(TM) * (2 * TX * A.nd + (5 * TX + 1) * 5 + A.nd + 6 * A.nd) + 16 + sizeof(double) * 8 * TX +
-                  sizeof(TM) * 3 * TX + sizeof(int) * TX;
-    auto kern = k_stage<TS, TM, FLAT>;
-    if (smem > 48 * 1024) RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int nseg = (A.nx0 + TX - 1) / TX;
-    size_t nblk = (size_t)nseg * A.nx1 * A.nx2;
+    constexpr int TXC = NCELL / (BY * BZ), NOWN = BY * BZ;
+    const int nd = A.nd, ndp = nd + 1;
+    size_t tm = 2 * NCELL * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NCELL;
+    if (!FLAT) tm += NOWN * nd + 6 * NOWN * nd;
+    size_t smem = sizeof(TM) * tm + 16 + sizeof(double) * (8 * NCELL * 6 + NCELL) +
+                  sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NCELL);
+    auto kern = k_stage<TS, TM, FLAT, BY, BZ>;
+    RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nseg = (A.nx0 + TXC - 1) / TXC;
+    size_t nblk = (size_t)nseg * (A.nx1 / BY) * (A.nx2 / BZ);
     kern<<<(unsigned)nblk, NT, smem, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }
 
+template <typename TS, typename TM, bool FLAT>
+rt_status launch_blk(rt_ctx *c, const StageArgs &A, int NT) {
+    bool by = A.act1 && A.nx1 % 2 == 0, bz = A.act2 && A.nx2 % 2 == 0;
+    if (by && bz) return launch<TS, TM, FLAT, 2, 2>(c, A, NT);
+    if (by) return launch<TS, TM, FLAT, 2, 1>(c, A, NT);
+    return launch<TS, TM, FLAT, 1, 1>(c, A, NT);
+}
+
 }  // namespace
 
-rt_status rt_launch_alpha(rt_ctx *c, const double *ug, double *alpha) {
+rt_status rt_launch_cellconst(rt_ctx *c) {
     const rt_config &f = c->cfg;
-    k_alpha<<<(c->ncell + 255) / 256, 256, 0, c->stream>>>(c->ncell, f.gam, f.rho_floor, f.rho_exp, f.T_exp, c->rho, ug,
-                                                          c->kap, c->cs, alpha);
+    k_cellconst<<<(c->ncell + 255) / 256, 256, 0, c->stream>>>(c->ncell, f.gam, f.rho_exp, f.rho_floor, c->rho, c->kap,
+                                                              c->cs, c->cc_au, c->cc_as, c->cc_Y, c->cc_on);
+    RT_CUDA_TRY(c, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status rt_launch_alpha(rt_ctx *c, const double *ug, double *alpha) {
+    k_alpha<<<(c->ncell + 255) / 256, 256, 0, c->stream>>>(c->ncell, c->cfg.T_exp, c->cc_au, c->cc_as, c->cc_Y,
+                                                          c->cc_on, ug, alpha);
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }
 
 rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout, const double *ug_in,
-                          double *ug_out, const double *alpha_in, double *alpha_out, double dtk, double *G) {
+                          double *ug_out, const double *alpha_in, const double *alpha_int, double *alpha_out,
+                          double dtk, double *G) {
     const rt_config &f = c->cfg;
     const rt_grid *g = c->g;
     StageArgs A{};
@@ -606,13 +769,13 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.beam_dir = f.beam_dir; A.beam_lo = f.beam_lo; A.beam_hi = f.beam_hi; A.beam_I = f.beam_I;
     A.n_pole_zero = f.n_pole_zero;
     A.dx0 = f.dx[0]; A.dx1 = f.dx[1]; A.dx2 = f.dx[2];
-    A.gam = f.gam; A.arad = f.arad; A.rho_exp = f.rho_exp; A.T_exp = f.T_exp; A.rho_floor = f.rho_floor;
-    A.abar = f.abar; A.tau_dt = f.tau_dt; A.limiter = f.limiter; A.ang_recon = f.ang_recon;
+    A.gam = f.gam; A.arad = f.arad; A.T_exp = f.T_exp; A.abar = f.abar; A.sumw = c->sumw;
+    A.tau_dt = f.tau_dt; A.limiter = f.limiter; A.ang_recon = f.ang_recon;
     A.transport = f.transport; A.source = f.source; A.dtk = dtk;
     A.Isrc = Isrc; A.Ibase = Ibase; A.Iout = Iout; A.ug_in = ug_in; A.ug_out = ug_out;
-    A.alpha_in = alpha_in; A.alpha_out = alpha_out;
-    A.rho = c->rho; A.kap = c->kap; A.cs = c->cs; A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.G = G;
-    A.fail = c->fail;
+    A.alpha_in = alpha_in; A.alpha_int = alpha_int; A.alpha_out = alpha_out;
+    A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y; A.cc_on = c->cc_on;
+    A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.G = G; A.fail = c->fail;
     A.mirror = g->mirror; A.nnb = g->nnb; A.nbr = g->nbr; A.ring_edge = g->ring_edge; A.ring_back = g->ring_back;
     A.edge = g->edge;
     bool dbl = f.precision == RT_FP64;
@@ -632,8 +795,10 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     }
     int NT = ((c->nd + 31) / 32) * 32;
     if (NT < 64) NT = 64;
-    if (NT > 256) { c->err = "more than 256 directions per cell are not supported by the stage kernel"; return RT_EINVAL; }
-    if (f.precision == RT_FP64) return flat ? launch<double, double, true>(c, A, NT) : launch<double, double, false>(c, A, NT);
-    if (f.precision == RT_FP32) return flat ? launch<float, float, true>(c, A, NT) : launch<float, float, false>(c, A, NT);
-    return flat ? launch<__nv_bfloat16, float, true>(c, A, NT) : launch<__nv_bfloat16, float, false>(c, A, NT);
+    if (NT > MAXNT) { c->err = "more than 256 directions per cell are not supported by the stage kernel"; return RT_EINVAL; }
+    if (f.precision == RT_FP64)
+        return flat ? launch_blk<double, double, true>(c, A, NT) : launch_blk<double, double, false>(c, A, NT);
+    if (f.precision == RT_FP32)
+        return flat ? launch_blk<float, float, true>(c, A, NT) : launch_blk<float, float, false>(c, A, NT);
+    return flat ? launch_blk<__nv_bfloat16, float, true>(c, A, NT) : launch_blk<__nv_bfloat16, float, false>(c, A, NT);
 }
