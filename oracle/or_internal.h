@@ -85,5 +85,8 @@ double or_cell_alpha(const or_ctx *c, double rho, double ug, double kap, double 
 void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
                         const double *Ibase, double dtk, double *Iout);
 long or_source_step(or_ctx *c, double *I, const double *ug_in, double *ug_out, double dtk, double *G4);
+double or_limiter(int kind, double dl, double dr);
+int or_map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row);
+void or_fill_ghosts(const or_ctx *c, const double *I, double *Ig);
 
 #endif

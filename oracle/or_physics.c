@@ -27,7 +27,7 @@ double or_cell_alpha(const or_ctx *c, double rho, double ug, double kap, double 
 }
 
 /* slope limiter of the piecewise-linear reconstruction (section 3.4) */
-static double limiter(int kind, double dl, double dr) {
+double or_limiter(int kind, double dl, double dr) {
     if (kind == 2) return 0.0;
     if (dl * dr <= 0.0) return 0.0;
     double s = dl > 0.0 ? 1.0 : -1.0;
@@ -67,7 +67,7 @@ double or_face_flux(double n, double IL, double IR, double Il, double Ir,
    (beam) value, 1 otherwise; *mir toggles the pole direction mirror.
    Pole boundary: the ghost at theta < 0 is the cell across the pole
    (theta -> -theta, phi -> phi + pi), seen with theta-hat and phi-hat reversed. */
-static int map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row) {
+int or_map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row) {
     *mir = 0; *fixed_row = -1;
     for (int a = 0; a < 3; ++a) {
         int n = c->c.nx[a];
@@ -88,13 +88,13 @@ static int map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row) {
     return *fixed_row == -1 ? 1 : 0;
 }
 
-static void fill_ghosts(const or_ctx *c, const double *I, double *Ig) {
+void or_fill_ghosts(const or_ctx *c, const double *I, double *Ig) {
     int nd = c->G.nd;
     for (int k = -c->ng[2]; k < c->c.nx[2] + c->ng[2]; ++k)
         for (int j = -c->ng[1]; j < c->c.nx[1] + c->ng[1]; ++j)
             for (int i = -c->ng[0]; i < c->c.nx[0] + c->ng[0]; ++i) {
                 int idx[3] = {i, j, k}, mir, row;
-                int ok = map_cell(c, idx, &mir, &row);
+                int ok = or_map_cell(c, idx, &mir, &row);
                 double *dst = Ig + (size_t)or_gidx(c, i, j, k) * nd;
                 if (!ok) {
                     for (int s = 0; s < nd; ++s)
@@ -208,13 +208,13 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
     size_t ngc = (size_t)c->gn[0] * c->gn[1] * c->gn[2];
     double *Ig = malloc(sizeof(double) * ngc * nd);
     double *alg = malloc(sizeof(double) * ngc), *vg = malloc(sizeof(double) * ngc * 3);
-    fill_ghosts(c, Isrc, Ig);
+    or_fill_ghosts(c, Isrc, Ig);
     /* ghost fluid: the cell a ghost copies (beam ghosts: the adjacent cell) */
     for (int k = -c->ng[2]; k < c->c.nx[2] + c->ng[2]; ++k)
         for (int j = -c->ng[1]; j < c->c.nx[1] + c->ng[1]; ++j)
             for (int i = -c->ng[0]; i < c->c.nx[0] + c->ng[0]; ++i) {
                 int idx[3] = {i, j, k}, mir, row;
-                map_cell(c, idx, &mir, &row);
+                or_map_cell(c, idx, &mir, &row);
                 int ci = or_cidx(c, idx[0], idx[1], idx[2]), gi = or_gidx(c, i, j, k);
                 alg[gi] = or_cell_alpha(c, c->rho[ci], ug_src[ci], c->kap[ci], c->cs[ci]);
                 const double *u = c->ucon + 4 * (size_t)ci;
@@ -261,8 +261,8 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
                             or_tetrad_dir(gf, nh, nf, &n0f);
                             double Im = Ig[(size_t)(gl - stride[a]) * nd + s], Il = Ig[(size_t)gl * nd + s];
                             double Ir = Ig[(size_t)gr * nd + s], Ip = Ig[(size_t)(gr + stride[a]) * nd + s];
-                            double sl = limiter(c->c.limiter, Ir - Il, Il - Im);
-                            double sr = limiter(c->c.limiter, Ip - Ir, Ir - Il);
+                            double sl = or_limiter(c->c.limiter, Ir - Il, Il - Im);
+                            double sr = or_limiter(c->c.limiter, Ip - Ir, Ir - Il);
                             double IL = Il + 0.5 * sl, IR = Ir - 0.5 * sr;
                             double len = c->c.tau_dt ? dtk : sqrt(gf->g[a + 1][a + 1]) * c->c.dx[a];
                             double tau = c->c.abar * 0.5 * (alg[gl] + alg[gr]) * len;
