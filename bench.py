@@ -39,12 +39,16 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 
 # DRAM traffic of one stage-kernel launch from an ncu capture (bytes per
 # cell-angle), valid only for the stage-kernel source it was measured on.
-NCU_TRAFFIC = {}   # {(sha1 of stage.cu, precision): bytes per cell-angle per launch}
+NCU_TRAFFIC = {}   # {(sha1 of the stage sources, precision): bytes per cell-angle per launch}
+STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
 def stage_source_hash():
-    with open(os.path.join(ROOT, "paper_2508_15532_b300", "csrc", "stage.cu"), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for name in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2508_15532_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def measured_peaks():
@@ -141,6 +145,49 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_leg(dev, stream, grid, nsteps=64, ckpt=8, N=64):
+    """Reverse mode on its workload: 64^3 cells, 162 directions, 64 steps,
+    a checkpoint every 8, FP64.  Returns the forward time per step (rt_step),
+    the backward time per step (recompute + reverse, rt_step_adjoint through
+    the autograd rollout) and their ratio, all timed with CUDA events."""
+    import torch
+    import paper_2508_15532_b300 as rt
+    from paper_2508_15532_b300 import workloads as W
+    from paper_2508_15532_b300.rollout import rollout
+    cfg, f = W.adjoint3d(N=N, n_geo=4)
+    with torch.cuda.stream(stream):
+        st = rt.RadiationStep(grid, cfg, precision="fp64", stream=stream.cuda_stream)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+        fluid = dict(rho=T(f["rho"]), ucon=T(f["ucon"]), alpha_s=T(f["alpha_s"]))
+        I0, ug0 = T(f["I"]), T(f["ug"])
+        kappa = T(f["kappa"]).requires_grad_()
+        eta = T(f["eta"]).requires_grad_()
+        w = T(grid.query()[1])
+        st.set_fluid(fluid["rho"], ug0, fluid["ucon"], kappa.detach(), fluid["alpha_s"], eta.detach())
+        st.set_intensity(I0)
+        dt = st.cfl_dt(0.4)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        st.step(dt, 3)
+        e0.record(stream)
+        st.step(dt, nsteps)
+        e1.record(stream)
+        stream.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / nsteps
+        IN, _ = rollout(st, fluid, I0, ug0, kappa, eta, nsteps, dt=dt, ckpt_every=ckpt)
+        L = ((IN @ w) ** 2).sum()
+        stream.synchronize()
+        e1.record(stream)
+        L.backward()
+        e2.record(stream)
+        stream.synchronize()
+        bwd_ms = e1.elapsed_time(e2) / nsteps
+        ok = bool(torch.isfinite(kappa.grad).all() and torch.isfinite(eta.grad).all())
+    del st
+    return {"workload": "adjoint3d: %d^3 cells x 162 directions, %d steps, checkpoint every %d, fp64" % (N, nsteps, ckpt),
+            "forward_ms_per_step": fwd_ms, "backward_ms_per_step": bwd_ms, "ratio": bwd_ms / fwd_ms,
+            "gradients_finite": ok}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -152,6 +199,7 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -264,6 +312,12 @@ def main():
     h2d = I_host.numel() * I_host.element_size() + ug_host.numel() * 8
     d2h = out_I.numel() * out_I.element_size() + out_ug.numel() * 8
 
+    adj = None
+    if world == 1 and not args.no_adjoint:
+        del st
+        adj = adjoint_leg(dev, stream, grid)
+        st = None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_ref = args.ref_cells
@@ -286,8 +340,11 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
+        if adj:
+            line["adjoint"] = adj
         print(json.dumps(line), flush=True)
-    del st
+    if st is not None:
+        del st
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -131,6 +131,26 @@ rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *
  * -Delta R^{0 mu}/dt of the last interaction (section 3.5.3).  Any may be NULL. */
 rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G);
 
+/* Reverse mode of nsteps steps of size dt (dt <= 0: the cfl bound with cfl
+ * 0.4) started from the checkpoint (I_ckpt [n_cell*n_dir], u_g ckpt
+ * [n_cell]), with the fluid of rt_set_fluid.  Given the cotangents of the
+ * final state, dL_dI_out [n_cell*n_dir] and dL_dug_out [n_cell] (NULL = 0),
+ * writes dL_dI_in and dL_dug_in (the cotangents of the checkpoint) and ADDS
+ * the gradients with respect to the absorption prefactor kappa and the
+ * emission multiplier eta to dL_dkappa and dL_deta [n_cell].  The paper
+ * (section 5.2) asks for gradients through the solver; this is the hand-derived
+ * reverse of section 3.6's predictor-corrector, eq. radiative_transfer_discrete
+ * with eqs. rad_speeds / flux_Jiang, and method 3 of section 3.5.2 (implicit
+ * function theorem at the temperature root).  The forward is recomputed from
+ * the checkpoint into a library-owned arena of about (4 nsteps + 2) intensity
+ * arrays (order 2; 2 nsteps + 2 for order 1), kept for the next call.  Scope:
+ * flat Cartesian geometry, fluid at rest, FP64 intensities, periodic (>= 4
+ * cells) or outflow boundaries; anything else is RT_EINVAL.  All pointers are
+ * device pointers; dL_dI_in may alias dL_dI_out.  Stream-ordered. */
+rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,
+                          const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,
+                          double *dL_dug_in, double *dL_dkappa, double *dL_deta);
+
 /* Launch timing of the stage kernel (no counterpart in the paper: a
  * measurement hook).  rt_set_timing(c, 1) makes rt_step record a CUDA event
  * pair around every stage launch on the context's stream; rt_get_timing

@@ -47,7 +47,7 @@ _lib = None
 EXPORTS = ["rt_create_geodesic_grid", "rt_grid_query", "rt_destroy_grid", "rt_create", "rt_destroy",
            "rt_last_error", "rt_set_metric", "rt_set_fluid", "rt_set_intensity", "rt_get_intensity",
            "rt_set_ugas", "rt_get_ugas", "rt_cfl_dt", "rt_step", "rt_moments", "rt_grid_last_error",
-           "rt_set_timing", "rt_get_timing"]
+           "rt_set_timing", "rt_get_timing", "rt_step_adjoint"]
 
 
 def lib():
@@ -79,6 +79,7 @@ def lib():
         L.rt_grid_last_error.restype = C.c_char_p
         L.rt_set_timing.argtypes = [vp, i]
         L.rt_get_timing.argtypes = [vp, C.POINTER(d), C.POINTER(C.c_longlong)]
+        L.rt_step_adjoint.argtypes = [vp, vp, vp, d, i, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -200,6 +201,14 @@ class RadiationStep:
         nf = C.c_longlong()
         self._check(lib().rt_step(self.h, float(dt), int(nsteps), C.byref(used), C.byref(nf) if check else None))
         return used.value, (nf.value if check else None)
+
+    def step_adjoint(self, I_ckpt, ug_ckpt, dt, nsteps, dL_dI_out, dL_dug_out, dL_dI_in, dL_dug_in,
+                     dL_dkappa, dL_deta):
+        """Reverse of nsteps steps from the checkpoint (rt_step_adjoint):
+        writes dL_dI_in, dL_dug_in and adds to dL_dkappa, dL_deta."""
+        self._check(lib().rt_step_adjoint(self.h, _ptr(I_ckpt), _ptr(ug_ckpt), float(dt), int(nsteps),
+                                          _ptr(dL_dI_out), _ptr(dL_dug_out), _ptr(dL_dI_in), _ptr(dL_dug_in),
+                                          _ptr(dL_dkappa), _ptr(dL_deta)))
 
     def set_timing(self, on=True):
         self._check(lib().rt_set_timing(self.h, int(bool(on))))

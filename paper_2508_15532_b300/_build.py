@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["grid.cu", "geometry.cu", "stage.cu", "moments.cu", "api.cu"]
+SOURCES = ["grid.cu", "geometry.cu", "stage.cu", "stage_flat.cu", "moments.cu", "adjoint.cu", "api.cu"]
 LIB = os.path.join(HERE, "librt_b300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -26,16 +26,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
+    headers = [d for d in _deps() if not d.endswith(".cu")]
+    newest_header = max(os.path.getmtime(h) for h in headers)
     objs = []
     procs = []
     for s in SOURCES:
         o = os.path.join(objdir, s.replace(".cu", ".o"))
+        objs.append(o)
+        src = os.path.join(CSRC, s)
+        if (not force and os.path.exists(o)
+                and os.path.getmtime(o) >= max(os.path.getmtime(src), newest_header)):
+            continue
         cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-rdc=false",
                "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, s), "-o", o]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), s))
-        objs.append(o)
     failed = []
     for p, s in procs:
         out, _ = p.communicate()

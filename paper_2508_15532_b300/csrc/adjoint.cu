@@ -1,0 +1,560 @@
+// adjoint.cu — reverse mode of the radiation step for flat Cartesian geometry
+// with the fluid at rest, FP64 intensities (section 5.2 motivates gradients
+// through the step; the reverse pass is derived by hand from eq.
+// radiative_transfer_discrete, eqs. rad_speeds / flux_Jiang and method 3 of
+// section 3.5.2).
+//
+// One call reverses nsteps steps from a checkpoint (I^0, u_g^0):
+//  1. forward recompute: every stage's transported intensities (the stage
+//     kernel with the interaction switched off) and the interaction applied to
+//     them, all kept in a library-owned arena;
+//  2. reverse sweep, per stage from the last: the interaction adjoint (the
+//     explicit pieces in reverse and the implicit function theorem at the
+//     temperature root), then the transport adjoint, a gather over the faces
+//     whose fluxes read each cell, with the limiter branches of the forward
+//     state and the optical-depth dependence of the face coefficients, which
+//     carries gradient into kappa and u_g through the opacity.
+#include "stage_common.cuh"
+#include <algorithm>
+
+using namespace rtk;
+
+namespace {
+
+constexpr int ADJ_NT = 192;   // threads of a block = directions (n_dir <= 192)
+constexpr int SC = 16;        // cells per interaction block (one lane per cell in the solve)
+constexpr int TXA = 8;        // cells per transport-adjoint block along x1
+constexpr int NFACE = 9 * TXA + 3;
+
+// ------------------------------------------------------------ interaction
+struct SrcArgs {
+    int ncell, nd, source;
+    double dtk, sumw, T_exp, arad, rho_exp;
+    const double *w, *I, *ug_in, *cc_au, *cc_as, *cc_Y, *eta, *rho;
+    const uint8_t *cc_on;
+    double *I_out, *ug_out;                  // forward
+    const double *Ibo, *ubo;                 // reverse: cotangents of the outputs
+    double *Ibi, *ubi;                       // cotangents of I (written) and u_g entering (ub_acc: added)
+    int ub_acc;
+    double *kb, *eb;                         // added
+    unsigned long long *fail;
+};
+
+// 16 values per lane -> lane l (and l + 16) holds the warp sum of value l & 15
+__device__ __forceinline__ double tsum16(double (&v)[SC], int lane) {
+#pragma unroll
+    for (int n = 8; n >= 1; n >>= 1) {
+        const bool hi = (lane & n) != 0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            double keep = hi ? v[i + n] : v[i];
+            double send = hi ? v[i] : v[i + n];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, n);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// REV = false: I_out = interaction(I), u_g out.  REV = true: the reverse.
+template <bool REV>
+__global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
+    constexpr int NW = ADJ_NT / 32;
+    __shared__ double part[NW][3][SC];
+    __shared__ double sh_a[SC], sh_b[SC], sh_c[SC];
+    __shared__ int sh_on[SC];
+    const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
+    const bool act = s < A.nd;
+    const size_t c0 = (size_t)blockIdx.x * SC;
+    const int nc = (int)min((size_t)SC, (size_t)A.ncell - c0);
+    const double w = act ? A.w[s] : 0.0;
+    double Iv[SC], Bv[SC], v[SC];
+#pragma unroll
+    for (int k = 0; k < SC; ++k) Iv[k] = (act && k < nc) ? A.I[(c0 + k) * A.nd + s] : 0.0;
+    if (REV) {
+#pragma unroll
+        for (int k = 0; k < SC; ++k) Bv[k] = (act && k < nc) ? A.Ibo[(c0 + k) * A.nd + s] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < SC; ++k) v[k] = Iv[k] * w;
+    double r0 = tsum16(v, lane);
+    if (lane < SC) part[warp][0][lane] = r0;
+    if (REV) {
+#pragma unroll
+        for (int k = 0; k < SC; ++k) v[k] = Bv[k];
+        double r1 = tsum16(v, lane);
+#pragma unroll
+        for (int k = 0; k < SC; ++k) v[k] = Bv[k] * Iv[k];
+        double r2 = tsum16(v, lane);
+        if (lane < SC) { part[warp][1][lane] = r1; part[warp][2][lane] = r2; }
+    }
+    __syncthreads();
+    if (warp == 0 && lane < SC) {
+        int on = 0;
+        double a0 = 0.0, b0 = 0.0, cc0 = 0.0;
+        if (lane < nc) {
+            const size_t c = c0 + lane;
+            const double Y = A.cc_Y[c], ugm = A.ug_in[c], au = A.cc_au[c], as = A.cc_as[c];
+            const double Tm = Y > 0.0 ? ugm / Y : 0.0;
+            const double am = (A.cc_on[c] && Tm > 0.0) ? au * tpow_neg<double>(Tm, A.T_exp) + as : 0.0;
+            on = A.source && A.cc_on[c] && am > 0.0 && Y > 0.0 && ugm > 0.0;
+            const double ub = (REV && A.ubo) ? A.ubo[c] : 0.0;
+            if (on) {
+                double Em = 0.0, P = 0.0, Q = 0.0;
+                for (int g = 0; g < NW; ++g) Em += part[g][0][lane];
+                if (REV)
+                    for (int g = 0; g < NW; ++g) { P += part[g][1][lane]; Q += part[g][2][lane]; }
+                const double dt = A.dtk, adt = am * dt, K = adt / (1.0 + adt), S = A.sumw;
+                const double eta = A.eta[c], p = A.T_exp, ar = A.arad;
+                Teq<double> q{K * Em, K * S * dt / FOURPI, Em + ugm, Y, Tm, Em, au, as, eta, ar, dt, p};
+                double X, lo = 0.0, hi = q.W;
+                bool ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
+                if (!ok && A.fail) atomicAdd(A.fail, 1ull);
+                const double Tp = Tm + (Em - X) / Y;
+                const double tp = tpow_neg<double>(Tp, p), aap = au * tp;
+                const double Tp4 = Tp * Tp * Tp * Tp;
+                const double a = (aap + as) * dt;
+                const double cc = dt * (eta * aap * ar * Tp4 + as * X) / FOURPI;
+                const double inv = 1.0 / (1.0 + a);
+                if (!REV) {
+                    const double Ep = (Em + cc * S) * inv;
+                    A.ug_out[c] = ugm - (Ep - Em);
+                    a0 = cc; b0 = inv;
+                } else {
+                    // I_+ = (I + cc)/A, E_+ = sum w I_+, u_g+ = u_g - (E_+ - E_-)
+                    const double sIpb = P - ub * S;                 // sum_s Ipb_s, Ipb_s = Ibo_s - ub w_s
+                    const double sIpbI = Q - ub * Em;               // sum_s Ipb_s I_s
+                    const double ccb = sIpb * inv;
+                    const double Ab = -(sIpbI + cc * sIpb) * inv * inv;
+                    double aapb = Ab * dt;
+                    double etab = ccb * dt * aap * ar * Tp4 / FOURPI;
+                    aapb += ccb * dt * eta * ar * Tp4 / FOURPI;
+                    double Tpb = ccb * dt * eta * aap * ar * 4.0 * Tp * Tp * Tp / FOURPI;
+                    double Xb = ccb * dt * as / FOURPI;
+                    double aub = aapb * tp;
+                    Tpb += aapb * (-p) * aap / Tp;
+                    double Tmb = Tpb, Emb = ub + Tpb / Y;
+                    Xb -= Tpb / Y;
+                    // root of h(X; B1, B2, T_-, E_-, au, eta) = 0
+                    const double lin = (aap + as) * dt - q.B2 * as;
+                    const double hT = -p * aap / Tp * dt * X - q.B2 * eta * ar * (4.0 - p) * aap * Tp * Tp * Tp;
+                    const double hX = lin - hT / Y;
+                    const double lam = -Xb / hX;
+                    const double B1b = -lam;
+                    const double B2b = lam * (-as * X - eta * ar * aap * Tp4);
+                    Tmb += lam * hT;
+                    Emb += lam * hT / Y;
+                    aub += lam * (tp * dt * X - q.B2 * eta * ar * tp * Tp4);
+                    etab += lam * (-q.B2 * ar * aap * Tp4);
+                    const double Kb = B2b * S * dt / FOURPI + B1b * Em;
+                    Emb += B1b * K;
+                    const double amb = Kb * dt / ((1.0 + adt) * (1.0 + adt));
+                    const double tm = tpow_neg<double>(Tm, p);
+                    aub += amb * tm;
+                    Tmb += amb * (-p) * au * tm / Tm;
+                    const double ugb = ub + Tmb / Y;
+                    A.ubi[c] = A.ub_acc ? A.ubi[c] + ugb : ugb;
+                    A.kb[c] += aub * pow(A.rho[c], A.rho_exp);
+                    A.eb[c] += etab;
+                    a0 = inv; b0 = ub; cc0 = Emb;
+                }
+            } else {
+                if (!REV) A.ug_out[c] = ugm;
+                else A.ubi[c] = A.ub_acc ? A.ubi[c] + ub : ub;
+            }
+        }
+        sh_on[lane] = on; sh_a[lane] = a0; sh_b[lane] = b0; sh_c[lane] = cc0;
+    }
+    __syncthreads();
+    if (!act) return;
+#pragma unroll
+    for (int k = 0; k < SC; ++k) {
+        if (k >= nc) break;
+        const size_t i = (c0 + k) * A.nd + s;
+        if (!REV) A.I_out[i] = sh_on[k] ? (Iv[k] + sh_a[k]) * sh_b[k] : Iv[k];
+        else A.Ibi[i] = sh_on[k] ? (Bv[k] - sh_b[k] * w) * sh_a[k] + sh_c[k] * w : Bv[k];
+    }
+}
+
+// --------------------------------------------------------------- transport
+struct TrArgs {
+    int nx[3], act[3], per[3], nd, limiter, tau_dt;
+    double dx[3], abar, dtk, T_exp, rho_exp;
+    const double *dir, *I, *alpha, *Ibo;
+    double *out_src, *base_out;
+    int src_acc, add_base;
+    const double *ug, *cc_au, *cc_Y, *rho;
+    const uint8_t *cc_on;
+    double *ub, *kb;
+    int ub_acc;
+};
+
+__device__ __forceinline__ int amap(int q, int n, int per) {
+    if (q >= 0 && q < n) return q;
+    if (per) return ((q % n) + n) % n;
+    return q < 0 ? 0 : n - 1;
+}
+
+// c1, c2, c3 of the face and their derivatives in tau
+__device__ void face_cd(double tau, double *fc) {
+    if (tau > 0.0) {
+        double F = -expm1(-tau * tau), G = -expm1(-tau * tau * tau * tau);
+        double f = sqrt(F) / tau, g = sqrt(G) / tau, e = exp(-tau), S = f + g;
+        double fp = exp(-tau * tau) / sqrt(F) - f / tau;
+        double gp = G > 0.0 ? 2.0 * tau * tau * exp(-tau * tau * tau * tau) / sqrt(G) - g / tau : 1.0;
+        double ep = -e, Sp = fp + gp;
+        fc[0] = f * e / S; fc[1] = g * e / S; fc[2] = f * g / S;
+        fc[3] = ((fp * e + f * ep) * S - f * e * Sp) / (S * S);
+        fc[4] = ((gp * e + g * ep) * S - g * e * Sp) / (S * S);
+        fc[5] = ((fp * g + f * gp) * S - f * g * Sp) / (S * S);
+    } else {
+        fc[0] = 1.0; fc[1] = 0.0; fc[2] = 0.0;
+        fc[3] = -2.0; fc[4] = 1.0; fc[5] = 1.0;
+    }
+}
+
+// derivative of the limited slope in (dl, dr), branches of rtk::limiter
+__device__ __forceinline__ void lim_d(int kind, double dl, double dr, double &gl, double &gr) {
+    gl = 0.0; gr = 0.0;
+    if (kind == RT_LIM_DONOR || dl * dr <= 0.0) return;
+    const double al = fabs(dl), ar = fabs(dr);
+    if (kind == RT_LIM_MINMOD) { if (al < ar) gl = 1.0; else gr = 1.0; return; }
+    double m = 2.0 * al;
+    int which = 0;
+    if (2.0 * ar < m) { m = 2.0 * ar; which = 1; }
+    if (0.5 * fabs(dl + dr) < m) which = 2;
+    if (which == 0) gl = 2.0;
+    else if (which == 1) gr = 2.0;
+    else { gl = 0.5; gr = 0.5; }
+}
+
+// One axis of the gather for one (cell, direction).  V: intensities at
+// offsets -3..3 along the axis (index o + 3), B: output cotangents at -2..2
+// (index o + 2, zero outside an outflow boundary), eq: bit o + 3 set when
+// offset o maps to this cell, fc[m + 2]: coefficients of the face between
+// offsets m and m + 1 (m = -2..1).  Adds the cotangent of this cell's
+// intensity to g and the cotangent of tau of the two adjacent faces to tb.
+__device__ __forceinline__ void axis_adj(const double (&V)[7], const double (&B)[5], unsigned eq,
+                                         const double *const (&fc)[4], double n, double coef, int lim, double &g,
+                                         double (&tb)[2]) {
+    if (n == 0.0) return;
+    const double an = fabs(n);
+#pragma unroll
+    for (int m = -2; m <= 1; ++m) {
+        const double phib = coef * (B[m + 3] - B[m + 2]);
+        if (phib == 0.0) continue;
+        const double Ill = V[m + 2], Il = V[m + 3], Ir = V[m + 4], Irr = V[m + 5];
+        const double *f = fc[m + 2];
+        double gla, glb, gra, grb;
+        lim_d(lim, Ir - Il, Il - Ill, gla, glb);
+        lim_d(lim, Irr - Ir, Ir - Il, gra, grb);
+        const double cL = n > 0.0 ? f[0] : f[1], cR = n > 0.0 ? f[1] : f[0];
+        const double ILb = phib * n * cL, IRb = phib * n * cR;
+        const double c3t = phib * an * f[2];
+        const double dIll = -0.5 * ILb * glb;
+        const double dIl = c3t + ILb * (1.0 - 0.5 * gla + 0.5 * glb) + 0.5 * IRb * grb;
+        const double dIr = -c3t + 0.5 * ILb * gla + IRb * (1.0 + 0.5 * gra - 0.5 * grb);
+        const double dIrr = -0.5 * IRb * gra;
+        if (eq & (1u << (m + 2))) g += dIll;
+        if (eq & (1u << (m + 3))) g += dIl;
+        if (eq & (1u << (m + 4))) g += dIr;
+        if (eq & (1u << (m + 5))) g += dIrr;
+        if (m == -1 || m == 0) {
+            double sl = limiter<double>(lim, Ir - Il, Il - Ill), sr = limiter<double>(lim, Irr - Ir, Ir - Il);
+            const double IL = Il + 0.5 * sl, IR = Ir - 0.5 * sr;
+            const double cLb = phib * n * IL, cRb = phib * n * IR;
+            const double c1b = n > 0.0 ? cLb : cRb, c2b = n > 0.0 ? cRb : cLb;
+            const double c3b = -phib * an * (Ir - Il);
+            tb[m + 1] += c1b * f[3] + c2b * f[4] + c3b * f[5];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
+    constexpr int NW = ADJ_NT / 32;
+    __shared__ double fcs[NFACE][6];
+    __shared__ double abw[NW][TXA];
+    const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
+    const bool act = s < A.nd;
+    const int nx0 = A.nx[0], nx1 = A.nx[1], nx2 = A.nx[2];
+    const int nseg = (nx0 + TXA - 1) / TXA;
+    const int seg = blockIdx.x % nseg, row = blockIdx.x / nseg;
+    const int j = row % nx1, k = row / nx1, x0 = seg * TXA;
+    const int nc = min(TXA, nx0 - x0);
+    auto cell = [&](int i, int jj, int kk) { return ((size_t)kk * nx1 + jj) * nx0 + i; };
+    auto len = [&](int a) { return A.tau_dt ? A.dtk : A.dx[a]; };
+
+    // face coefficients: x1 faces with left cell x0 + m, m = -2..TXA (slot m + 2);
+    // x2 / x3 faces of cell t with left offset m = -2..1 (slot TXA + 3 + (axis - 1) 4 TXA + 4 t + m + 2)
+    for (int f = s; f < NFACE; f += ADJ_NT) {
+        int a, t, m;
+        if (f < TXA + 3) { a = 0; t = 0; m = f - 2; }
+        else { int u = f - (TXA + 3); a = 1 + u / (4 * TXA); t = (u % (4 * TXA)) / 4; m = u % 4 - 2; }
+        if (!A.act[a] || (a > 0 && t >= nc)) continue;
+        size_t cl, cr;
+        if (a == 0) {
+            cl = cell(amap(x0 + m, nx0, A.per[0]), j, k); cr = cell(amap(x0 + m + 1, nx0, A.per[0]), j, k);
+        } else if (a == 1) {
+            cl = cell(x0 + t, amap(j + m, nx1, A.per[1]), k); cr = cell(x0 + t, amap(j + m + 1, nx1, A.per[1]), k);
+        } else {
+            cl = cell(x0 + t, j, amap(k + m, nx2, A.per[2])); cr = cell(x0 + t, j, amap(k + m + 1, nx2, A.per[2]));
+        }
+        face_cd(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len(a), fcs[f]);
+    }
+    __syncthreads();
+
+    double n[3] = {0.0, 0.0, 0.0};
+    if (act) for (int a = 0; a < 3; ++a) n[a] = A.dir[3 * s + a];
+    const double coef[3] = {A.dtk / A.dx[0], A.dtk / A.dx[1], A.dtk / A.dx[2]};
+    const int nd = A.nd;
+    auto ldI = [&](size_t c) { return act ? __ldg(A.I + c * nd + s) : 0.0; };
+    auto ldB = [&](size_t c) { return act ? __ldg(A.Ibo + c * nd + s) : 0.0; };
+    double abt[TXA];
+#pragma unroll
+    for (int t = 0; t < TXA; ++t) abt[t] = 0.0;
+
+    // sliding x1 window
+    double WX[7], BX[5];
+    if (A.act[0]) {
+#pragma unroll
+        for (int o = -3; o <= 3; ++o) WX[o + 3] = ldI(cell(amap(x0 + o, nx0, A.per[0]), j, k));
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) {
+            int q = x0 + o;
+            BX[o + 2] = (A.per[0] || (q >= 0 && q < nx0)) ? ldB(cell(amap(q, nx0, A.per[0]), j, k)) : 0.0;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TXA; ++t) {
+        if (t < nc) {
+            const int i = x0 + t;
+            const size_t c = cell(i, j, k);
+            const double Ic = ldI(c), Bc = ldB(c);
+            double g = 0.0;
+            if (A.act[0]) {
+                unsigned eq = 0;
+                for (int o = -3; o <= 3; ++o) eq |= (amap(i + o, nx0, A.per[0]) == i) << (o + 3);
+                const double *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
+                double tb[2] = {0.0, 0.0};
+                axis_adj(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
+                const double h = A.abar * 0.5 * len(0);
+                abt[t] += h * (tb[0] * (1 + ((eq >> 2) & 1)) + tb[1] * (1 + ((eq >> 4) & 1)));
+            }
+            for (int a = 1; a < 3; ++a) {
+                if (!A.act[a]) continue;
+                const int na = a == 1 ? nx1 : nx2, pos = a == 1 ? j : k;
+                double V[7], B[5];
+                unsigned eq = 0;
+#pragma unroll
+                for (int o = -3; o <= 3; ++o) {
+                    const int mq = amap(pos + o, na, A.per[a]);
+                    eq |= (unsigned)(mq == pos) << (o + 3);
+                    V[o + 3] = o == 0 ? Ic : ldI(a == 1 ? cell(i, mq, k) : cell(i, j, mq));
+                }
+#pragma unroll
+                for (int o = -2; o <= 2; ++o) {
+                    const int q = pos + o, mq = amap(q, na, A.per[a]);
+                    B[o + 2] = o == 0 ? Bc
+                               : ((A.per[a] || (q >= 0 && q < na)) ? ldB(a == 1 ? cell(i, mq, k) : cell(i, j, mq)) : 0.0);
+                }
+                const int base = TXA + 3 + (a - 1) * 4 * TXA + 4 * t;
+                const double *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
+                double tb[2] = {0.0, 0.0};
+                axis_adj(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
+                const double h = A.abar * 0.5 * len(a);
+                abt[t] += h * (tb[0] * (1 + ((eq >> 2) & 1)) + tb[1] * (1 + ((eq >> 4) & 1)));
+            }
+            if (act) {
+                const size_t ix = c * nd + s;
+                double v = g + (A.add_base ? Bc : 0.0);
+                if (A.src_acc) v += A.out_src[ix];
+                A.out_src[ix] = v;
+                if (A.base_out) A.base_out[ix] = Bc;
+            }
+            // slide the x1 window
+            if (A.act[0] && t + 1 < nc) {
+#pragma unroll
+                for (int o = 0; o < 6; ++o) WX[o] = WX[o + 1];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) BX[o] = BX[o + 1];
+                WX[6] = ldI(cell(amap(i + 4, nx0, A.per[0]), j, k));
+                const int q = i + 3;
+                BX[4] = (A.per[0] || q < nx0) ? ldB(cell(amap(q, nx0, A.per[0]), j, k)) : 0.0;
+            }
+        }
+    }
+    // opacity cotangent of each cell: sum over directions, then through
+    // alpha = kappa rho^m T^-p + alpha^s (T = u_g/Y) to u_g and kappa
+#pragma unroll
+    for (int t = 0; t < TXA; ++t) {
+        double v = abt[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) abw[warp][t] = v;
+    }
+    __syncthreads();
+    if (s < nc) {
+        const size_t c = cell(x0 + s, j, k);
+        double ab = 0.0;
+        for (int g = 0; g < NW; ++g) ab += abw[g][s];
+        const double Y = A.cc_Y[c], T = Y > 0.0 ? A.ug[c] / Y : 0.0;
+        double ubv = 0.0;
+        if (A.cc_on[c] && T > 0.0 && ab != 0.0) {
+            const double tp = tpow_neg<double>(T, A.T_exp);
+            A.kb[c] += ab * pow(A.rho[c], A.rho_exp) * tp;
+            ubv = ab * A.cc_au[c] * (-A.T_exp) * tp / T / Y;
+        }
+        A.ub[c] = A.ub_acc ? A.ub[c] + ubv : ubv;
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- host side
+static rt_status adj_fail(rt_ctx *c, rt_status st, const std::string &msg) {
+    c->err = msg;
+    return st;
+}
+
+static rt_status launch_src(rt_ctx *c, bool rev, const double *I, const double *ug_in, double dtk, double *I_out,
+                            double *ug_out, const double *Ibo, const double *ubo, double *Ibi, double *ubi, int ub_acc,
+                            double *kb, double *eb) {
+    SrcArgs A{};
+    const rt_config &f = c->cfg;
+    A.ncell = c->ncell; A.nd = c->nd; A.source = f.source;
+    A.dtk = dtk; A.sumw = c->sumw; A.T_exp = f.T_exp; A.arad = f.arad; A.rho_exp = f.rho_exp;
+    A.w = c->g->w; A.I = I; A.ug_in = ug_in; A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y;
+    A.eta = c->eta; A.rho = c->rho; A.cc_on = c->cc_on;
+    A.I_out = I_out; A.ug_out = ug_out; A.Ibo = Ibo; A.ubo = ubo; A.Ibi = Ibi; A.ubi = ubi; A.ub_acc = ub_acc;
+    A.kb = kb; A.eb = eb; A.fail = c->fail;
+    unsigned nblk = (unsigned)((c->ncell + SC - 1) / SC);
+    if (rev) k_src<true><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    else k_src<false><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    RT_CUDA_TRY(c, cudaGetLastError());
+    return RT_OK;
+}
+
+static rt_status launch_tr(rt_ctx *c, const double *I, const double *ug, const double *alpha, double dtk,
+                           const double *Ibo, double *out_src, int src_acc, int add_base, double *base_out, double *ub,
+                           int ub_acc, double *kb) {
+    TrArgs A{};
+    const rt_config &f = c->cfg;
+    for (int a = 0; a < 3; ++a) {
+        A.nx[a] = f.nx[a]; A.act[a] = c->active[a]; A.per[a] = f.bc[a][0] == RT_BC_PERIODIC; A.dx[a] = f.dx[a];
+    }
+    A.nd = c->nd; A.limiter = f.limiter; A.tau_dt = f.tau_dt; A.abar = f.abar; A.dtk = dtk;
+    A.T_exp = f.T_exp; A.rho_exp = f.rho_exp;
+    A.dir = c->g->dir; A.I = I; A.alpha = alpha; A.Ibo = Ibo; A.out_src = out_src; A.base_out = base_out;
+    A.src_acc = src_acc; A.add_base = add_base; A.ug = ug; A.cc_au = c->cc_au; A.cc_Y = c->cc_Y; A.rho = c->rho;
+    A.cc_on = c->cc_on; A.ub = ub; A.kb = kb; A.ub_acc = ub_acc;
+    const int nseg = (f.nx[0] + TXA - 1) / TXA;
+    unsigned nblk = (unsigned)((size_t)nseg * f.nx[1] * f.nx[2]);
+    k_tr_adj<<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    RT_CUDA_TRY(c, cudaGetLastError());
+    return RT_OK;
+}
+
+// transport-only stage through the forward stage kernel (interaction off)
+static rt_status transport_only(rt_ctx *c, const double *Isrc, const double *Ibase, double *Iout, const double *ug,
+                                const double *alpha, double dtk, double *ug_scr, double *a_scr) {
+    const int src = c->cfg.source;
+    c->cfg.source = 0;
+    rt_status st = rt_launch_stage(c, Isrc, Ibase, Iout, ug, ug_scr, alpha, alpha, a_scr, dtk, nullptr);
+    c->cfg.source = src;
+    return st;
+}
+
+extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,
+                                     const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,
+                                     double *dL_dug_in, double *dL_dkappa, double *dL_deta) {
+    if (!c) return RT_EINVAL;
+    if (!I_ckpt || !ug_ckpt || !dL_dI_out || !dL_dI_in || !dL_dug_in || !dL_dkappa || !dL_deta || nsteps < 1)
+        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: null pointer or nsteps < 1");
+    if (c->metric < 0 || !c->have_fluid) return adj_fail(c, RT_ESTATE, "rt_set_metric and rt_set_fluid must precede rt_step_adjoint");
+    if (c->metric != RT_MINKOWSKI_CART || !c->static_fluid)
+        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: flat Cartesian geometry with the fluid at rest only");
+    if (c->cfg.precision != RT_FP64) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: FP64 intensities only");
+    if (c->nd > ADJ_NT) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: at most 192 directions");
+    for (int a = 0; a < 3; ++a) {
+        if (!c->active[a]) continue;
+        int b0 = c->cfg.bc[a][0], b1 = c->cfg.bc[a][1];
+        bool per = b0 == RT_BC_PERIODIC && b1 == RT_BC_PERIODIC, out = b0 == RT_BC_OUTFLOW && b1 == RT_BC_OUTFLOW;
+        if (!per && !out) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: periodic or outflow boundaries on both sides of an axis only");
+        if (per && c->cfg.nx[a] < 4) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: periodic axes need at least 4 cells");
+    }
+    if (!(dt > 0.0)) {
+        if (c->dt_cfl <= 0.0) {
+            rt_status st = rt_cfl_dt(c, 0.4, &c->dt_cfl);
+            if (st != RT_OK) return st;
+        }
+        dt = c->dt_cfl;
+    }
+    const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
+    const int order = c->cfg.order;
+    // arena: per step I^n, (order 2: I*_t, I*), I^{n+1}_t, u_g^n, (u_g*);
+    // reverse: two intensity cotangents, three cell cotangents; scratch
+    const size_t per_step_i = order == 2 ? 4 : 2, per_step_c = order == 2 ? 2 : 1;
+    const size_t need = ((per_step_i * nsteps + 2) * ni + (per_step_c * nsteps + 8) * nc) * sizeof(double);
+    if (c->adj_bytes < need) {
+        if (c->adj) cudaFree(c->adj);
+        c->adj = nullptr; c->adj_bytes = 0;
+        RT_CUDA_TRY(c, cudaMalloc(&c->adj, need));
+        c->adj_bytes = need;
+    }
+    double *p = c->adj;
+    auto take = [&](size_t n) { double *r = p; p += n; return r; };
+    std::vector<double *> In(nsteps), At(nsteps), Bs(nsteps), Ct(nsteps), un(nsteps), us(nsteps);
+    for (int n = 0; n < nsteps; ++n) {
+        In[n] = take(ni);
+        if (order == 2) { At[n] = take(ni); Bs[n] = take(ni); }
+        Ct[n] = take(ni);
+    }
+    for (int n = 0; n < nsteps; ++n) { un[n] = take(nc); if (order == 2) us[n] = take(nc); }
+    double *X1 = take(ni), *X2 = take(ni);
+    double *ub = take(nc), *ubn = take(nc), *ubs = take(nc), *an = take(nc), *as_ = take(nc);
+    double *ug_scr = take(nc), *a_scr = take(nc), *u_next = take(nc);
+
+    // 1. forward recompute from the checkpoint
+    RT_CUDA_TRY(c, cudaMemcpyAsync(In[0], I_ckpt, ni * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(un[0], ug_ckpt, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    rt_status st;
+    for (int n = 0; n < nsteps; ++n) {
+        double *Inext = n + 1 < nsteps ? In[n + 1] : X1;
+        double *unext = n + 1 < nsteps ? un[n + 1] : u_next;
+        if ((st = rt_launch_alpha(c, un[n], an)) != RT_OK) return st;
+        if (order == 1) {
+            if ((st = transport_only(c, In[n], In[n], Ct[n], un[n], an, dt, ug_scr, a_scr)) != RT_OK) return st;
+            if ((st = launch_src(c, false, Ct[n], un[n], dt, Inext, unext, 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
+        } else {
+            if ((st = transport_only(c, In[n], In[n], At[n], un[n], an, 0.5 * dt, ug_scr, a_scr)) != RT_OK) return st;
+            if ((st = launch_src(c, false, At[n], un[n], 0.5 * dt, Bs[n], us[n], 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
+            if ((st = rt_launch_alpha(c, us[n], as_)) != RT_OK) return st;
+            if ((st = transport_only(c, Bs[n], In[n], Ct[n], us[n], as_, dt, ug_scr, a_scr)) != RT_OK) return st;
+            if ((st = launch_src(c, false, Ct[n], un[n], dt, Inext, unext, 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
+        }
+    }
+    // 2. reverse sweep; Ib = dL_dI_in holds the running cotangent of I
+    double *Ib = dL_dI_in;
+    if (Ib != dL_dI_out)
+        RT_CUDA_TRY(c, cudaMemcpyAsync(Ib, dL_dI_out, ni * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (dL_dug_out) RT_CUDA_TRY(c, cudaMemcpyAsync(ub, dL_dug_out, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    else RT_CUDA_TRY(c, cudaMemsetAsync(ub, 0, nc * sizeof(double), c->stream));
+    for (int n = nsteps - 1; n >= 0; --n) {
+        if ((st = rt_launch_alpha(c, un[n], an)) != RT_OK) return st;
+        if (order == 1) {
+            // interaction over dt, then transport over dt from I^n
+            if ((st = launch_src(c, true, Ct[n], un[n], dt, 0, 0, Ib, ub, X1, ubn, 0, dL_dkappa, dL_deta)) != RT_OK) return st;
+            if ((st = launch_tr(c, In[n], un[n], an, dt, X1, Ib, 0, 1, nullptr, ubn, 1, dL_dkappa)) != RT_OK) return st;
+        } else {
+            if ((st = rt_launch_alpha(c, us[n], as_)) != RT_OK) return st;
+            // corrector interaction (gas from u_g^n) and transport (fluxes of I*, opacity of u_g*)
+            if ((st = launch_src(c, true, Ct[n], un[n], dt, 0, 0, Ib, ub, X1, ubn, 0, dL_dkappa, dL_deta)) != RT_OK) return st;
+            // (Ib, read by the interaction above, now receives the corrector's base cotangent)
+            if ((st = launch_tr(c, Bs[n], us[n], as_, dt, X1, X2, 0, 0, Ib, ubs, 0, dL_dkappa)) != RT_OK) return st;
+            // predictor interaction and transport (both from I^n)
+            if ((st = launch_src(c, true, At[n], un[n], 0.5 * dt, 0, 0, X2, ubs, X1, ubn, 1, dL_dkappa, dL_deta)) != RT_OK) return st;
+            if ((st = launch_tr(c, In[n], un[n], an, 0.5 * dt, X1, Ib, 1, 1, nullptr, ubn, 1, dL_dkappa)) != RT_OK) return st;
+        }
+        std::swap(ub, ubn);
+    }
+    RT_CUDA_TRY(c, cudaMemcpyAsync(dL_dug_in, ub, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return RT_OK;
+}

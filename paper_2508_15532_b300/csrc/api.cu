@@ -5,6 +5,14 @@
 
 static std::string g_create_err;
 
+// any cell whose tetrad-frame fluid velocity is not (1, 0, 0, 0)
+__global__ void k_moving(int ncell, const double *__restrict__ uhat, int *__restrict__ flag) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double *u = uhat + 4 * (size_t)c;
+    if (!(u[0] == 1.0 && u[1] == 0.0 && u[2] == 0.0 && u[3] == 0.0)) atomicOr(flag, 1);
+}
+
 static rt_status fail(rt_ctx *c, rt_status st, const char *msg) {
     if (c) c->err = msg;
     return st;
@@ -16,7 +24,7 @@ static void free_ctx(rt_ctx *c) {
     void *ptrs[] = {c->I[0], c->I[1], c->I[2], c->ug[0], c->ug[1], c->ug[2], c->alpha[0], c->alpha[1], c->rho,
                     c->kap, c->cs, c->eta, c->ucon, c->vel, c->uhat, c->G, c->fail, c->pt_e, c->pt_ei, c->pt_V,
                     c->pt_n0, c->pt_len, c->pt_om, c->cenU_d, c->cenU_f, c->mask, c->fn_d, c->fn_f, c->fP_d,
-                    c->fP_f, c->ew_d, c->ew_f, c->cc_au, c->cc_as, c->cc_Y, c->cc_on};
+                    c->fP_f, c->ew_d, c->ew_f, c->cc_au, c->cc_as, c->cc_Y, c->cc_on, c->adj};
     for (void *p : ptrs) if (p) cudaFree(p);
     delete c;
 }
@@ -64,7 +72,10 @@ extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cud
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_as, nc * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_Y, nc * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_on, nc);
-    for (double w : g->h_w) c->sumw += w;
+    for (int d = 0; d < g->nd; ++d) {
+        c->sumw += g->h_w[d];
+        for (int m = 0; m < 3; ++m) c->sumnw[m] += g->h_dir[3 * d + m] * g->h_w[d];
+    }
     if (e == cudaSuccess) e = cudaMemset(c->G, 0, nc * 32);
     if (e != cudaSuccess) {
         g_create_err = std::string("allocation: ") + cudaGetErrorString(e);
@@ -119,6 +130,17 @@ extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_
     if (st != RT_OK) return st;
     st = rt_launch_cellconst(c);
     if (st != RT_OK) return st;
+    {
+        int *d = nullptr, h = 0;
+        RT_CUDA_TRY(c, cudaMalloc(&d, sizeof(int)));
+        cudaMemsetAsync(d, 0, sizeof(int), c->stream);
+        k_moving<<<(c->ncell + 255) / 256, 256, 0, c->stream>>>(c->ncell, c->uhat, d);
+        cudaError_t e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(d);
+        if (e != cudaSuccess) { c->err = std::string("rt_set_fluid: ") + cudaGetErrorString(e); return RT_ECUDA; }
+        c->static_fluid = (h == 0) && c->metric == RT_MINKOWSKI_CART;
+    }
     st = rt_launch_alpha(c, c->ug[0], c->alpha[0]);
     if (st != RT_OK) return st;
     c->have_fluid = true;

@@ -61,6 +61,8 @@ struct rt_ctx {
     double *cc_au = nullptr, *cc_as = nullptr, *cc_Y = nullptr;
     uint8_t *cc_on = nullptr;
     double sumw = 0.0;           // sum of the solid angles (4 pi to rounding)
+    double sumnw[3] = {0, 0, 0}; // sum of n-hat dOmega (0 to rounding)
+    bool static_fluid = false;   // u-hat = (1, 0, 0, 0) in every cell (set by rt_set_fluid)
     unsigned long long *fail = nullptr;   // device counter of unconverged solves
 
     // geometry tables over ghosted (i, j) points (Kerr-Schild); flat: unused
@@ -76,6 +78,9 @@ struct rt_ctx {
     double *fP_d = nullptr; float *fP_f = nullptr;         // [3*npt*nd] dA_a n_0 at the lower face
     double *ew_d = nullptr; float *ew_f = nullptr;         // [npt*ne] dlam_e n_0(m) v(m).u_e
     double dt_cfl = 0.0;
+    // arena of the reverse pass (rt_step_adjoint), grown on demand
+    double *adj = nullptr;
+    size_t adj_bytes = 0;
     // optional per-launch timing of the stage kernel
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -102,6 +107,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
                           double *alpha_out, double dtk, double *G);
 rt_status rt_launch_alpha(rt_ctx *c, const double *ug, double *alpha);
 rt_status rt_launch_cellconst(rt_ctx *c);
+
 // moments (moments.cu)
 rt_status rt_launch_moments(rt_ctx *c, double *R, double *Ebar);
 rt_status rt_launch_cfl(rt_ctx *c, double *dt_min_host);

@@ -27,153 +27,10 @@
 //    FP32 Newton iterations finished by an FP64 Newton step in the mixed
 //    path, FP64 throughout in the FP64 path — then the per-direction update
 //    and the FP64 energy ledger.
-#include "rt_internal.cuh"
-#include <cmath>
+#include "stage_common.cuh"
 
 namespace {
-
-constexpr int NCELL = 32;    // cells per CTA
-constexpr int MAXNT = 256;
-constexpr double FOURPI = 12.566370614359172953850573533118;
-constexpr int F_MIR = 1 << 29, F_FIX = 1 << 30, F_MASK = (1 << 29) - 1;
-
-struct StageArgs {
-    int nx0, nx1, nx2, nd, ne;
-    int act0, act1, act2;
-    int bc[3][2];
-    int beam_dir, beam_lo, beam_hi;
-    double beam_I;
-    int n_pole_zero;
-    double dx0, dx1, dx2;
-    double gam, arad, T_exp, abar, sumw;
-    int tau_dt, limiter, ang_recon, transport, source;
-    double dtk;
-    const void *Isrc; const void *Ibase; void *Iout;
-    const double *ug_in; double *ug_out;
-    const double *alpha_in;    // opacity of the flux stage (neighbours)
-    const double *alpha_int;   // opacity at the interaction's initial gas state
-    double *alpha_out;         // opacity after the interaction
-    const double *cc_au, *cc_as, *cc_Y, *eta, *vel, *uhat;
-    const uint8_t *cc_on;
-    double *G;
-    unsigned long long *fail;
-    const int *mirror, *nnb, *nbr, *ring_edge, *ring_back, *edge;
-    const void *dirT, *wT, *mxT, *mgT, *mmT;   // math-type copies of the grid tables
-    int gn0, ng0, ng1;
-    const void *cenU, *fn, *fP, *ew;           // math-type geometry tables (curved)
-    const uint8_t *mask;
-    const double *pt_V, *pt_n0, *pt_e;
-    const double *pt_len;
-};
-
-template <typename TS, typename TM> struct IO;
-template <> struct IO<double, double> {
-    __device__ static double ld(const void *p, size_t i) { return __ldg((const double *)p + i); }
-    __device__ static double st(void *p, size_t i, double v) { ((double *)p)[i] = v; return v; }
-};
-template <> struct IO<float, float> {
-    __device__ static float ld(const void *p, size_t i) { return __ldg((const float *)p + i); }
-    __device__ static float st(void *p, size_t i, float v) { __stcs((float *)p + i, v); return v; }
-};
-template <> struct IO<__nv_bfloat16, float> {
-    __device__ static float ld(const void *p, size_t i) {
-        return __bfloat162float(__ldg((const __nv_bfloat16 *)p + i));
-    }
-    __device__ static float st(void *p, size_t i, float v) {
-        __nv_bfloat16 b = __float2bfloat16_rn(v);
-        ((__nv_bfloat16 *)p)[i] = b;
-        return __bfloat162float(b);
-    }
-};
-
-template <typename TM> __device__ __forceinline__ TM ldT(const void *p, size_t i) { return __ldg((const TM *)p + i); }
-
-template <typename TM> __device__ __forceinline__ TM dv(TM a, TM b);
-template <> __device__ __forceinline__ float dv<float>(float a, float b) { return __fdividef(a, b); }
-template <> __device__ __forceinline__ double dv<double>(double a, double b) { return a / b; }
-
-template <typename TM> __device__ __forceinline__ TM limiter(int kind, TM dl, TM dr) {
-    if (kind == RT_LIM_DONOR) return TM(0);
-    if (dl * dr <= TM(0)) return TM(0);
-    TM al = fabs(dl), ar = fabs(dr);
-    TM m = (kind == RT_LIM_MINMOD) ? fmin(al, ar) : fmin(fmin(TM(2) * al, TM(2) * ar), TM(0.5) * fabs(dl + dr));
-    return dl > TM(0) ? m : -m;
-}
-
-// per-unit-n_0 flux through one face for one direction: the exponentially cut
-// HLL form (eqs. rad_speeds, flux_Jiang; see the oracle for the orientation
-// reading); rec = (c1, c2, c3, kL, kR) of the face
-template <typename TM>
-__device__ __forceinline__ TM face_phi(TM n, const TM *rec, TM IL, TM IR, TM Il, TM Ir) {
-    TM cL = n > TM(0) ? rec[0] : rec[1];
-    TM cR = n > TM(0) ? rec[1] : rec[0];
-    return n * (cL * IL + cR * IR) - fabs(n) * rec[2] * (Ir - Il) + rec[3] * IL + rec[4] * IR;
-}
-
-// boundary resolution of one index along one axis (setup only)
-__device__ int map_axis(const StageArgs &A, int ax, int q, int *flags, int *kshift) {
-    int n = ax == 0 ? A.nx0 : (ax == 1 ? A.nx1 : A.nx2);
-    if (q >= 0 && q < n) return q;
-    int side = q < 0 ? 0 : 1, bc = A.bc[ax][side];
-    if (bc == RT_BC_PERIODIC) return (q + n) % n;
-    if (bc == RT_BC_POLE) {
-        *flags ^= F_MIR;
-        if (ax == 1 && A.nx2 > 1 && kshift) *kshift = A.nx2 / 2;
-        return side ? 2 * n - 1 - q : -1 - q;
-    }
-    if (bc == RT_BC_BEAM) *flags |= F_FIX;
-    return side ? n - 1 : 0;
-}
-
-// row descriptor: base cell index of row (j, k) at x1 = 0, with flags
-__device__ int row_desc(const StageArgs &A, int j, int k) {
-    int fl = 0, ks = 0;
-    int jm = map_axis(A, 1, j, &fl, &ks);
-    int km = map_axis(A, 2, k, &fl, nullptr);
-    if (ks) km = (km + ks) % A.nx2;
-    return ((km * A.nx1 + jm) * A.nx0) | fl;
-}
-
-// ------------------------------------------------------------ temperature
-// Method 3 solved for the post-interaction radiation energy X = E* (see the
-// oracle): h(X) = (alpha(T) dt - B2 alpha^s) X - B1 - B2 eta alpha^a(T) a T^4,
-// T = T_- + (E-bar_- - X)/Y; h increases strictly on [0, W).
-template <typename R> struct Teq { R B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p; };
-
-template <typename R> __device__ __forceinline__ R tpow_neg(R T, R p) {
-    if (p == R(3.5)) { R r = sqrt(T); return R(1) / (T * T * T * r); }
-    if (p == R(0)) return R(1);
-    return pow(T, -p);
-}
-
-template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, R X, R *h, R *dh) {
-    R T = q.Tm + (q.Em - X) / q.Y;
-    if (!(T > R(0))) { *h = R(1e30); *dh = R(1); return; }
-    R tp = tpow_neg(T, q.p);
-    R aa = q.au * tp;
-    R T4 = T * T * T * T;
-    R em = q.B2 * q.eta * q.arad * aa * T4;
-    R lin = (aa + q.as) * q.dt - q.B2 * q.as;
-    *h = lin * X - q.B1 - em;
-    // dh/dX with dT/dX = -1/Y
-    *dh = lin + (q.p * aa / T) * q.dt * X / q.Y + em * (R(4) - q.p) / (T * q.Y);
-}
-
-// safeguarded Newton on [lo, hi] with h(lo) <= 0 < h(hi); returns converged flag
-template <typename R> __device__ bool newton_E(const Teq<R> &q, R X, R &lo, R &hi, int maxit, R tol, R *Xout) {
-    R h, dh;
-    for (int it = 0; it < maxit; ++it) {
-        teq_eval(q, X, &h, &dh);
-        if (h > R(0)) hi = fmin(hi, X); else lo = fmax(lo, X);
-        R Xn = X - h / dh;
-        if (!(Xn > lo && Xn < hi)) Xn = R(0.5) * (lo + hi);
-        R step = fabs(Xn - X);
-        X = Xn;
-        if (h == R(0) || step <= tol * X || hi - lo <= tol * hi) { *Xout = X; return true; }
-    }
-    *Xout = X;
-    return false;
-}
+using namespace rtk;
 
 template <typename TS, typename TM, bool FLAT, int BY, int BZ>
 __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
@@ -593,11 +450,8 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                               (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p};
                 float flo = 0.0f, fhi = (float)q.W, fx;
                 newton_E<float>(qf, (float)Em, flo, fhi, 60, 1e-7f, &fx);
-                double h, dh;
-                teq_eval<double>(q, (double)fx, &h, &dh);
-                X = (double)fx - h / dh;
-                ok = X >= 0.0 && X < q.W && Tm + (Em - X) / Y > 0.0;
-                if (!ok) ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
+                // FP64 Newton from the FP32 root (one or two steps in practice)
+                ok = newton_E<double>(q, (double)fx, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
             } else {
                 ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
             }
@@ -793,9 +647,11 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
         A.ew = dbl ? (const void *)c->ew_d : (const void *)c->ew_f;
         A.mask = c->mask; A.pt_V = c->pt_V; A.pt_n0 = c->pt_n0; A.pt_len = c->pt_len; A.pt_e = c->pt_e;
     }
+    for (int m = 0; m < 3; ++m) A.sumnw[m] = c->sumnw[m];
     int NT = ((c->nd + 31) / 32) * 32;
     if (NT < 64) NT = 64;
     if (NT > MAXNT) { c->err = "more than 256 directions per cell are not supported by the stage kernel"; return RT_EINVAL; }
+    if (rt_stage_fast_ok(c)) return rt_launch_stage_fs(c, A, NT);
     if (f.precision == RT_FP64)
         return flat ? launch_blk<double, double, true>(c, A, NT) : launch_blk<double, double, false>(c, A, NT);
     if (f.precision == RT_FP32)

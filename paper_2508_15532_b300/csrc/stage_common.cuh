@@ -1,0 +1,201 @@
+// stage_common.cuh — pieces shared by the stage kernels (stage.cu, stage_flat.cu).
+#pragma once
+#include "rt_internal.cuh"
+#include <cmath>
+
+namespace rtk {
+
+constexpr int NCELL = 32;    // cells per CTA
+constexpr int MAXNT = 256;
+constexpr double FOURPI = 12.566370614359172953850573533118;
+constexpr int F_MIR = 1 << 29, F_FIX = 1 << 30, F_MASK = (1 << 29) - 1;
+
+struct StageArgs {
+    int nx0, nx1, nx2, nd, ne;
+    int act0, act1, act2;
+    int bc[3][2];
+    int beam_dir, beam_lo, beam_hi;
+    double beam_I;
+    int n_pole_zero;
+    double dx0, dx1, dx2;
+    double gam, arad, T_exp, abar, sumw;
+    double sumnw[3];           // sum of n-hat_s dOmega_s (0 to rounding)
+    int tau_dt, limiter, ang_recon, transport, source;
+    double dtk;
+    const void *Isrc; const void *Ibase; void *Iout;
+    const double *ug_in; double *ug_out;
+    const double *alpha_in;    // opacity of the flux stage (neighbours)
+    const double *alpha_int;   // opacity at the interaction's initial gas state
+    double *alpha_out;         // opacity after the interaction
+    const double *cc_au, *cc_as, *cc_Y, *eta, *vel, *uhat;
+    const uint8_t *cc_on;
+    double *G;
+    unsigned long long *fail;
+    const int *mirror, *nnb, *nbr, *ring_edge, *ring_back, *edge;
+    const void *dirT, *wT, *mxT, *mgT, *mmT;   // math-type copies of the grid tables
+    int gn0, ng0, ng1;
+    const void *cenU, *fn, *fP, *ew;           // math-type geometry tables (curved)
+    const uint8_t *mask;
+    const double *pt_V, *pt_n0, *pt_e;
+    const double *pt_len;
+};
+
+template <typename TS, typename TM> struct IO;
+template <> struct IO<double, double> {
+    __device__ static double ld(const void *p, size_t i) { return __ldg((const double *)p + i); }
+    __device__ static double st(void *p, size_t i, double v) { ((double *)p)[i] = v; return v; }
+};
+template <> struct IO<float, float> {
+    __device__ static float ld(const void *p, size_t i) { return __ldg((const float *)p + i); }
+    __device__ static float st(void *p, size_t i, float v) { __stcs((float *)p + i, v); return v; }
+};
+template <> struct IO<__nv_bfloat16, float> {
+    __device__ static float ld(const void *p, size_t i) {
+        return __bfloat162float(__ldg((const __nv_bfloat16 *)p + i));
+    }
+    __device__ static float st(void *p, size_t i, float v) {
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        ((__nv_bfloat16 *)p)[i] = b;
+        return __bfloat162float(b);
+    }
+};
+
+template <typename TM> __device__ __forceinline__ TM ldT(const void *p, size_t i) { return __ldg((const TM *)p + i); }
+
+template <typename TM> __device__ __forceinline__ TM dv(TM a, TM b);
+template <> __device__ __forceinline__ float dv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double dv<double>(double a, double b) { return a / b; }
+
+template <typename TM> __device__ __forceinline__ TM limiter(int kind, TM dl, TM dr) {
+    if (kind == RT_LIM_DONOR) return TM(0);
+    if (dl * dr <= TM(0)) return TM(0);
+    TM al = fabs(dl), ar = fabs(dr);
+    TM m = (kind == RT_LIM_MINMOD) ? fmin(al, ar) : fmin(fmin(TM(2) * al, TM(2) * ar), TM(0.5) * fabs(dl + dr));
+    return dl > TM(0) ? m : -m;
+}
+
+// per-unit-n_0 flux through one face for one direction: the exponentially cut
+// HLL form (eqs. rad_speeds, flux_Jiang; see the oracle for the orientation
+// reading); rec = (c1, c2, c3, kL, kR) of the face
+template <typename TM>
+__device__ __forceinline__ TM face_phi(TM n, const TM *rec, TM IL, TM IR, TM Il, TM Ir) {
+    TM cL = n > TM(0) ? rec[0] : rec[1];
+    TM cR = n > TM(0) ? rec[1] : rec[0];
+    return n * (cL * IL + cR * IR) - fabs(n) * rec[2] * (Ir - Il) + rec[3] * IL + rec[4] * IR;
+}
+
+// boundary resolution of one index along one axis (setup only)
+__device__ inline int map_axis(const StageArgs &A, int ax, int q, int *flags, int *kshift) {
+    int n = ax == 0 ? A.nx0 : (ax == 1 ? A.nx1 : A.nx2);
+    if (q >= 0 && q < n) return q;
+    int side = q < 0 ? 0 : 1, bc = A.bc[ax][side];
+    if (bc == RT_BC_PERIODIC) return (q + n) % n;
+    if (bc == RT_BC_POLE) {
+        *flags ^= F_MIR;
+        if (ax == 1 && A.nx2 > 1 && kshift) *kshift = A.nx2 / 2;
+        return side ? 2 * n - 1 - q : -1 - q;
+    }
+    if (bc == RT_BC_BEAM) *flags |= F_FIX;
+    return side ? n - 1 : 0;
+}
+
+// row descriptor: base cell index of row (j, k) at x1 = 0, with flags
+__device__ inline int row_desc(const StageArgs &A, int j, int k) {
+    int fl = 0, ks = 0;
+    int jm = map_axis(A, 1, j, &fl, &ks);
+    int km = map_axis(A, 2, k, &fl, nullptr);
+    if (ks) km = (km + ks) % A.nx2;
+    return ((km * A.nx1 + jm) * A.nx0) | fl;
+}
+
+// ------------------------------------------------------------ temperature
+// Method 3 solved for the post-interaction radiation energy X = E* (see the
+// oracle): h(X) = (alpha(T) dt - B2 alpha^s) X - B1 - B2 eta alpha^a(T) a T^4,
+// T = T_- + (E-bar_- - X)/Y; h increases strictly on [0, W).
+template <typename R> struct Teq { R B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p; };
+
+template <typename R> __device__ __forceinline__ R tpow_neg(R T, R p) {
+    if (p == R(3.5)) { R r = sqrt(T); return R(1) / (T * T * T * r); }
+    if (p == R(0)) return R(1);
+    return pow(T, -p);
+}
+
+template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, R X, R *h, R *dh) {
+    R T = q.Tm + (q.Em - X) / q.Y;
+    if (!(T > R(0))) { *h = R(1e30); *dh = R(1); return; }
+    R tp = tpow_neg(T, q.p);
+    R aa = q.au * tp;
+    R T4 = T * T * T * T;
+    R em = q.B2 * q.eta * q.arad * aa * T4;
+    R lin = (aa + q.as) * q.dt - q.B2 * q.as;
+    *h = lin * X - q.B1 - em;
+    // dh/dX with dT/dX = -1/Y
+    *dh = lin + (q.p * aa / T) * q.dt * X / q.Y + em * (R(4) - q.p) / (T * q.Y);
+}
+
+// safeguarded Newton on [lo, hi] with h(lo) <= 0 < h(hi); returns converged flag
+template <typename R> __device__ bool newton_E(const Teq<R> &q, R X, R &lo, R &hi, int maxit, R tol, R *Xout) {
+    R h, dh;
+    for (int it = 0; it < maxit; ++it) {
+        teq_eval(q, X, &h, &dh);
+        if (h == R(0)) { *Xout = X; return true; }      // exact root: keep it
+        if (h > R(0)) hi = fmin(hi, X); else lo = fmax(lo, X);
+        R d = h / dh;
+        if (fabs(d) <= tol * X) { *Xout = fmin(fmax(X - d, lo), hi); return true; }   // converged Newton step
+        R Xn = X - d;
+        bool newton = Xn > lo && Xn < hi;
+        if (!newton) Xn = R(0.5) * (lo + hi);
+        R step = fabs(Xn - X);
+        X = Xn;
+        if ((newton && step <= tol * X) || hi - lo <= tol * hi) { *Xout = X; return true; }
+    }
+    *Xout = X;
+    return false;
+}
+
+// T^-p in FP64 for the mixed path: for p = 3.5 an FP32 reciprocal square
+// root refined by one FP64 Newton step for 1/sqrt (relative error ~1e-14)
+__device__ __forceinline__ double tneg_mixed(double T, double p) {
+    if (p == 3.5 && T > 1e-30 && T < 1e30) {
+        double y = (double)rsqrtf((float)T);
+        y = y * (1.5 - 0.5 * T * y * y);
+        double y2 = y * y;
+        return y2 * y2 * y2 * y;
+    }
+    return tpow_neg<double>(T, p);
+}
+
+// Temperature solve of the mixed (FP32-storage) path: FP32 Newton from E-bar_-,
+// then FP64 residual iterations X <- X - h_64(X) / h'_32(X) (the residual is
+// FP64, the slope FP32, so each iteration gains ~7 digits).  Returns X = E*.
+__device__ inline bool solve_mixed(const Teq<double> &q, double *Xout) {
+    Teq<float> qf{(float)q.B1, (float)q.B2, (float)q.W, (float)q.Y, (float)q.Tm, (float)q.Em, (float)q.au,
+                  (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p};
+    float flo = 0.0f, fhi = (float)q.W, fx;
+    bool okf = newton_E<float>(qf, (float)q.Em, flo, fhi, 40, 2e-7f, &fx);
+    const double invY = 1.0 / q.Y, B2ea = q.B2 * q.eta * q.arad, B2as = q.B2 * q.as;
+    double X = (double)fx;
+    for (int it = 0; it < 3; ++it) {
+        double T = q.Tm + (q.Em - X) * invY;
+        if (!(T > 0.0)) return false;
+        double aa = q.au * tneg_mixed(T, q.p);
+        double T2 = T * T;
+        double h = ((aa + q.as) * q.dt - B2as) * X - q.B1 - B2ea * aa * T2 * T2;
+        float Tf = (float)T, aaf = (float)aa, Xf = (float)X;
+        float lin = (aaf + qf.as) * qf.dt - qf.B2 * qf.as;
+        float emf = qf.B2 * qf.eta * qf.arad * aaf * Tf * Tf * Tf * Tf;
+        float dh = lin + (qf.p * aaf / Tf) * qf.dt * Xf / qf.Y + emf * (4.0f - qf.p) / (Tf * qf.Y);
+        double d = h * (double)(1.0f / dh);
+        X -= d;
+        if (fabs(d) <= 1e-15 * fabs(X)) break;
+    }
+    *Xout = X;
+    return okf && X >= 0.0 && X < q.W;
+}
+
+}  // namespace rtk
+
+// fast path of the stage (stage_flat.cu): flat Cartesian geometry, a fluid at
+// rest in every cell, MC limiter, fewer than 2^31 stored intensities
+bool rt_stage_fast_ok(const rt_ctx *c);
+rt_status rt_launch_stage_fs(rt_ctx *c, const rtk::StageArgs &A, int NT);

@@ -1,0 +1,397 @@
+// stage_flat.cu — fast path of the stage kernel for flat Cartesian geometry
+// with the fluid at rest in every cell (the periodic opacity/coupling box).
+//
+// Same scheme as stage.cu (section 3.6: transport over dtk, then the implicit
+// interaction of section 3.5.2), specialised where the general kernel spends
+// its instructions:
+//  - the 32 transported intensities of the brick (one per cell, for this
+//    thread's direction) stay in registers; no shared-memory tile;
+//  - angular sums are warp transpose-reductions (31 shuffles per 32 cells)
+//    followed by one shared-memory pass over the warps;
+//  - at rest (D = 1, n^0 = 1) the coupling coefficients K, B1, B2 are per
+//    cell, so a single sum (E-bar) feeds the temperature solve, and the
+//    ledger and the force on the gas follow in closed form:
+//      I_+ = (I + c) / (1 + a),  E-bar_+ = (E-bar_- + c sum w) / (1 + a),
+//      Delta R^{0 i} = (c sum n^i w - a sum n^i I w) / (1 + a),
+//    with a = alpha(T_+) dt, c = dt j(T_+) / (4 pi) (eq. fluid_interaction_discrete);
+//  - MC limiter and face records of three coefficients (no fluid advection).
+#include "stage_common.cuh"
+
+namespace {
+using namespace rtk;
+
+template <typename TM> struct __align__(4 * sizeof(TM)) Rec4 { TM c1, c2, c3, pad; };
+
+// half of the monotonised central slope, sign(dl) min(|dl|, |dr|, |dl + dr|/4),
+// 0 where the one-sided differences differ in sign (halving is exact, so this
+// is bit-identical to half of the MC slope)
+template <typename TM> __device__ __forceinline__ TM mc_half(TM dl, TM dr) {
+    TM m = fmin(fmin(fabs(dl), fabs(dr)), TM(0.25) * fabs(dl + dr));
+    return (dl * dr > TM(0)) ? copysign(m, dl) : TM(0);
+}
+
+// per-unit-n_0 spatial flux of one direction through one face (see stage.cu):
+// n (cL I_L + cR I_R) - |n| c3 (I_r - I_l) with (cL, cR) = (c1, c2) for n > 0
+// and (c2, c1) for n < 0, written with np = max(n, 0), nm = min(n, 0)
+template <typename TM>
+__device__ __forceinline__ TM phi_s(TM np, TM nm, TM an, const Rec4<TM> &r, TM IL, TM IR, TM Il, TM Ir) {
+    TM kL = r.c1 * np + r.c2 * nm, kR = r.c2 * np + r.c1 * nm;
+    return kL * IL + kR * IR - an * r.c3 * (Ir - Il);
+}
+
+// 32 values per lane -> lane l holds the sum over the warp of value l
+template <typename TM> __device__ __forceinline__ TM transpose_sum(TM (&v)[NCELL], int lane) {
+#pragma unroll
+    for (int n = 16; n >= 1; n >>= 1) {
+        const bool hi = (lane & n) != 0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            TM keep = hi ? v[i + n] : v[i];
+            TM send = hi ? v[i] : v[i + n];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, n);
+        }
+    }
+    return v[0];
+}
+
+// FP32 math: three CTAs of 192 threads per SM.  Each SM sub-partition holds
+// 16K registers and a CTA's six warps spread over the four, so three CTAs
+// (up to five warps on one sub-partition) leave 96 registers a thread.
+// FP64 math keeps one CTA.
+template <typename TM> struct MinBlocks { static constexpr int v = 3; };
+template <> struct MinBlocks<double> { static constexpr int v = 1; };
+constexpr int FS_NT = 192;
+
+template <typename TS, typename TM, int BY, int BZ, bool WANTG, bool SIMPLE>
+__global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const StageArgs A) {
+    constexpr int TXC = NCELL / (BY * BZ), NOWN = BY * BZ;
+    __shared__ int xmap[TXC + 4];
+    __shared__ int rowY[BZ * (BY + 4)], rowZ[BY * (BZ + 4)];
+    __shared__ Rec4<TM> recX[NOWN * (TXC + 1)], recY[BZ * (BY + 1) * TXC], recZ[BY * (BZ + 1) * TXC];
+    __shared__ TM part[FS_NT / 32][4][NCELL];
+    __shared__ TM cEm[NCELL], cInv[NCELL];
+    __shared__ int cOn[NCELL];
+
+    const int nd = A.nd, NT = blockDim.x, s = threadIdx.x, lane = s & 31, warp = s >> 5;
+    const bool act = s < nd;
+    const int nseg = (A.nx0 + TXC - 1) / TXC;
+    const int seg = blockIdx.x % nseg, rest = blockIdx.x / nseg, nyb = A.nx1 / BY;
+    const int j0 = (rest % nyb) * BY, k0 = (rest / nyb) * BZ, i0 = seg * TXC;
+    const int nc = min(TXC, A.nx0 - i0);
+
+    for (int t = s; t < TXC + 4; t += NT) {
+        int fl = 0;
+        xmap[t] = map_axis(A, 0, i0 - 2 + t, &fl, nullptr) | fl;
+    }
+    for (int t = s; t < BZ * (BY + 4); t += NT) rowY[t] = row_desc(A, j0 - 2 + t % (BY + 4), k0 + t / (BY + 4));
+    for (int t = s; t < BY * (BZ + 4); t += NT) rowZ[t] = row_desc(A, j0 + t / (BZ + 4), k0 - 2 + t % (BZ + 4));
+    __syncthreads();
+
+    // face coefficients c1 = f e/(f+g), c2 = g e/(f+g), c3 = f g/(f+g) of the
+    // optical depth tau = abar (alpha_l + alpha_r)/2 dx (eq. rad_speeds)
+    auto coeffs = [&](int cl, int cr, double len, Rec4<TM> &r) {
+        double tau = A.abar * 0.5 * (A.alpha_in[cl] + A.alpha_in[cr]) * (A.tau_dt ? A.dtk : len);
+        if (tau > 0.0) {
+            TM t = (TM)tau;
+            TM f = sqrt(-expm1(-t * t)) / t, g = sqrt(-expm1(-t * t * t * t)) / t, e = exp(-t), fg = f + g;
+            r.c1 = f * e / fg; r.c2 = g * e / fg; r.c3 = f * g / fg;
+        } else {
+            r.c1 = TM(1); r.c2 = TM(0); r.c3 = TM(0);
+        }
+        r.pad = TM(0);
+    };
+    if (A.transport) {
+        const int nX = A.act0 ? NOWN * (nc + 1) : 0, nY = A.act1 ? BZ * (BY + 1) * nc : 0;
+        const int nZ = A.act2 ? BY * (BZ + 1) * nc : 0;
+        for (int t = s; t < nX + nY + nZ; t += NT) {
+            if (t < nX) {
+                int o = t / (nc + 1), f = t % (nc + 1);
+                int rb = rowY[(o / BY) * (BY + 4) + o % BY + 2] & F_MASK;
+                coeffs(rb + (xmap[f + 1] & F_MASK), rb + (xmap[f + 2] & F_MASK), A.dx0, recX[o * (TXC + 1) + f]);
+            } else if (t < nX + nY) {
+                int u = t - nX, ii = u % nc, v = u / nc, f = v % (BY + 1), r = v / (BY + 1);
+                coeffs((rowY[r * (BY + 4) + f + 1] & F_MASK) + i0 + ii, (rowY[r * (BY + 4) + f + 2] & F_MASK) + i0 + ii,
+                       A.dx1, recY[(r * (BY + 1) + f) * TXC + ii]);
+            } else {
+                int u = t - nX - nY, ii = u % nc, v = u / nc, f = v % (BZ + 1), q = v / (BZ + 1);
+                coeffs((rowZ[q * (BZ + 4) + f + 1] & F_MASK) + i0 + ii, (rowZ[q * (BZ + 4) + f + 2] & F_MASK) + i0 + ii,
+                       A.dx2, recZ[(q * (BZ + 1) + f) * TXC + ii]);
+            }
+        }
+    }
+    __syncthreads();
+
+    const TS *Isrc = (const TS *)A.Isrc;
+    const int smir = act ? __ldg(A.mirror + s) : 0;
+    TM nh[3] = {TM(0), TM(0), TM(0)}, w = TM(0);
+    if (act) {
+        for (int m = 0; m < 3; ++m) nh[m] = ldT<TM>(A.dirT, 3 * s + m);
+        w = ldT<TM>(A.wT, s);
+    }
+    const TM an[3] = {fabs(nh[0]), fabs(nh[1]), fabs(nh[2])};
+    const TM np[3] = {fmax(nh[0], TM(0)), fmax(nh[1], TM(0)), fmax(nh[2], TM(0))};
+    const TM nm[3] = {fmin(nh[0], TM(0)), fmin(nh[1], TM(0)), fmin(nh[2], TM(0))};
+    const TM dtk = (TM)A.dtk;
+    const TM cdx[3] = {dtk / (TM)A.dx0, dtk / (TM)A.dx1, dtk / (TM)A.dx2};
+
+    // per-thread element offsets of the stencil rows (-1: fixed zero row)
+    // (SIMPLE: periodic/outflow boundaries only, no fixed or mirrored rows)
+    auto roff = [&](int desc) -> int {
+        if (!SIMPLE && (desc & F_FIX)) return -1;
+        return (desc & F_MASK) * nd + ((!SIMPLE && (desc & F_MIR)) ? smir : s);
+    };
+    auto ldo = [&](int off, int i) -> TM {
+        if (!SIMPLE && off < 0) return TM(0);
+        return IO<TS, TM>::ld(Isrc, (unsigned)(off + i * nd));
+    };
+    auto ldx = [&](int ownoff, int xd, int jrow) -> TM {   // own row, x1 position from the descriptor
+        if (!SIMPLE && (xd & F_FIX)) return (s == A.beam_dir && jrow >= A.beam_lo && jrow < A.beam_hi) ? TM(A.beam_I) : TM(0);
+        int off = ownoff + (xd & F_MASK) * nd;
+        if (!SIMPLE && (xd & F_MIR)) off += smir - s;
+        return IO<TS, TM>::ld(Isrc, (unsigned)off);
+    };
+
+    TM It[NCELL];
+#pragma unroll
+    for (int c = 0; c < NCELL; ++c) It[c] = TM(0);
+
+    if (act) {
+        int oy[BZ][BY + 4], oz[BY][BZ + 4];
+#pragma unroll
+        for (int r = 0; r < BZ; ++r)
+#pragma unroll
+            for (int q = 0; q < BY + 4; ++q) oy[r][q] = roff(rowY[r * (BY + 4) + q]);
+#pragma unroll
+        for (int q = 0; q < BY; ++q)
+#pragma unroll
+            for (int r = 0; r < BZ + 4; ++r) oz[q][r] = roff(rowZ[q * (BZ + 4) + r]);
+        const bool same_base = A.Isrc == A.Ibase;
+        if (A.transport) {
+            TM W0[NOWN], W1[NOWN], S0[NOWN], Flo[NOWN];
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                W0[o] = W1[o] = S0[o] = Flo[o] = TM(0);
+                if (A.act0) {
+                    const int q = o % BY, r = o / BY, own = oy[r][q + 2];
+                    TM Im2 = ldx(own, xmap[0], j0 + q), Im1 = ldx(own, xmap[1], j0 + q);
+                    TM I0 = ldx(own, xmap[2], j0 + q), I1 = ldx(own, xmap[3], j0 + q);
+                    TM sm1 = mc_half(I0 - Im1, Im1 - Im2), s0 = mc_half(I1 - I0, I0 - Im1);
+                    Flo[o] = phi_s(np[0], nm[0], an[0], recX[o * (TXC + 1)], Im1 + sm1, I0 - s0, Im1, I0);
+                    W0[o] = I0; W1[o] = I1; S0[o] = s0;
+                }
+            }
+#pragma unroll
+            for (int ii = 0; ii < TXC; ++ii) {
+                if (ii < nc) {
+                    const int i = i0 + ii;
+                    TM acc[NOWN], Ic[NOWN];
+#pragma unroll
+                    for (int o = 0; o < NOWN; ++o) {
+                        acc[o] = TM(0);
+                        Ic[o] = A.act0 ? W0[o] : ldo(oy[o / BY][o % BY + 2], i);
+                    }
+                    if (A.act0) {
+#pragma unroll
+                        for (int o = 0; o < NOWN; ++o) {
+                            const int q = o % BY, r = o / BY;
+                            TM I2 = ldx(oy[r][q + 2], xmap[ii + 4], j0 + q);
+                            TM s1 = mc_half(I2 - W1[o], W1[o] - W0[o]);
+                            TM phi = phi_s(np[0], nm[0], an[0], recX[o * (TXC + 1) + ii + 1], W0[o] + S0[o],
+                                           W1[o] - s1, W0[o], W1[o]);
+                            acc[o] += cdx[0] * (phi - Flo[o]);
+                            Flo[o] = phi; W0[o] = W1[o]; W1[o] = I2; S0[o] = s1;
+                        }
+                    }
+                    if (A.act1) {
+#pragma unroll
+                        for (int r = 0; r < BZ; ++r) {
+                            TM Y[BY + 4], sy[BY + 4], F[BY + 1];
+#pragma unroll
+                            for (int q = 0; q < BY + 4; ++q) Y[q] = (q >= 2 && q < BY + 2) ? Ic[r * BY + q - 2] : ldo(oy[r][q], i);
+#pragma unroll
+                            for (int q = 1; q < BY + 3; ++q) sy[q] = mc_half(Y[q + 1] - Y[q], Y[q] - Y[q - 1]);
+#pragma unroll
+                            for (int f = 0; f <= BY; ++f)
+                                F[f] = phi_s(np[1], nm[1], an[1], recY[(r * (BY + 1) + f) * TXC + ii], Y[f + 1] + sy[f + 1],
+                                             Y[f + 2] - sy[f + 2], Y[f + 1], Y[f + 2]);
+#pragma unroll
+                            for (int q = 0; q < BY; ++q) acc[r * BY + q] += cdx[1] * (F[q + 1] - F[q]);
+                        }
+                    }
+                    if (A.act2) {
+#pragma unroll
+                        for (int q = 0; q < BY; ++q) {
+                            TM Z[BZ + 4], sz[BZ + 4], F[BZ + 1];
+#pragma unroll
+                            for (int r = 0; r < BZ + 4; ++r) Z[r] = (r >= 2 && r < BZ + 2) ? Ic[(r - 2) * BY + q] : ldo(oz[q][r], i);
+#pragma unroll
+                            for (int r = 1; r < BZ + 3; ++r) sz[r] = mc_half(Z[r + 1] - Z[r], Z[r] - Z[r - 1]);
+#pragma unroll
+                            for (int f = 0; f <= BZ; ++f)
+                                F[f] = phi_s(np[2], nm[2], an[2], recZ[(q * (BZ + 1) + f) * TXC + ii], Z[f + 1] + sz[f + 1],
+                                             Z[f + 2] - sz[f + 2], Z[f + 1], Z[f + 2]);
+#pragma unroll
+                            for (int r = 0; r < BZ; ++r) acc[r * BY + q] += cdx[2] * (F[r + 1] - F[r]);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 0; o < NOWN; ++o) {
+                        TM Ib = same_base ? Ic[o]
+                                          : IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + i * nd));
+                        It[o * TXC + ii] = Ib - acc[o];
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o)
+#pragma unroll
+                for (int ii = 0; ii < TXC; ++ii)
+                    if (ii < nc) It[o * TXC + ii] = IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + (i0 + ii) * nd));
+        }
+    }
+
+    // ---- interaction (section 3.5.2), fluid at rest
+    // local cell lc = o TXC + ii with own row o = r BY + q
+    const int lc_ii = lane % TXC, lc_o = lane / TXC;
+    const size_t lc_cell = ((size_t)(k0 + lc_o / BY) * A.nx1 + j0 + lc_o % BY) * A.nx0 + i0 + lc_ii;
+    const bool lc_valid = lc_ii < nc;
+    if (warp == 0) {
+        int on = 0;
+        if (lc_valid) {
+            double Y = A.cc_Y[lc_cell], ug = A.ug_in[lc_cell], am = A.alpha_int[lc_cell];
+            on = A.source && A.cc_on[lc_cell] && am > 0.0 && Y > 0.0 && ug > 0.0;
+        }
+        cOn[lane] = on;
+    }
+    {
+        TM v[NCELL];
+#pragma unroll
+        for (int c = 0; c < NCELL; ++c) v[c] = It[c] * w;
+        part[warp][0][lane] = transpose_sum(v, lane);
+        if (WANTG) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                for (int c = 0; c < NCELL; ++c) v[c] = It[c] * w * nh[m];
+                part[warp][1 + m][lane] = transpose_sum(v, lane);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lc_valid) {
+        const size_t cidx = lc_cell;
+        const int nw = NT / 32;
+        TM ce = TM(0), ci = TM(1);
+        const double ugm = A.ug_in[cidx];
+        if (cOn[lane]) {
+            double Em = 0.0, F[3] = {0, 0, 0};
+            for (int g = 0; g < nw; ++g) Em += (double)part[g][0][lane];
+            if (WANTG)
+                for (int m = 0; m < 3; ++m)
+                    for (int g = 0; g < nw; ++g) F[m] += (double)part[g][1 + m][lane];
+            const double dt = A.dtk, adt = A.alpha_int[cidx] * dt;
+            const double K = adt / (1.0 + adt);
+            const double Y = A.cc_Y[cidx], au = A.cc_au[cidx], as = A.cc_as[cidx];
+            const double Tm = ugm / Y;
+            Teq<double> q{K * Em, K * A.sumw * dt / FOURPI, Em + ugm, Y, Tm, Em, au, as, A.eta[cidx], A.arad, dt, A.T_exp};
+            double X, a, c, inv, alpha_new;
+            bool ok;
+            if (sizeof(TM) == 4) {
+                ok = solve_mixed(q, &X);
+                // update constants in the storage math precision; the ledger uses
+                // exactly the constants the stored intensities are built from
+                const float Tp = (float)(Tm + (Em - X) / Y);
+                const float aap = (float)au * tpow_neg<float>(Tp, (float)A.T_exp);
+                const float af = (aap + (float)as) * (float)dt;
+                const float cf = (float)dt * ((float)q.eta * aap * (float)A.arad * Tp * Tp * Tp * Tp + (float)as * (float)X) /
+                                 (float)FOURPI;
+                const float invf = 1.0f / (1.0f + af);
+                a = af; c = cf; inv = invf;
+            } else {
+                double lo = 0.0, hi = q.W;
+                ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
+                const double Tp = Tm + (Em - X) / Y;
+                const double aap = au * tpow_neg<double>(Tp, A.T_exp);
+                a = (aap + as) * dt;
+                c = dt * (q.eta * aap * A.arad * Tp * Tp * Tp * Tp + as * X) / FOURPI;
+                inv = 1.0 / (1.0 + a);
+            }
+            if (!ok) atomicAdd(A.fail, 1ull);
+            ce = (TM)c; ci = (TM)inv;
+            // exchange ledger in closed form (I_+ = (I + c)/(1 + a) in every direction)
+            const double Ep = (Em + c * A.sumw) * inv;
+            const double ugp = ugm - (Ep - Em);
+            A.ug_out[cidx] = ugp;
+            const double T = ugp / Y;
+            if (sizeof(TM) == 4) alpha_new = T > 0.0 ? (double)((float)au * tpow_neg<float>((float)T, (float)A.T_exp) + (float)as) : 0.0;
+            else alpha_new = T > 0.0 ? au * tpow_neg<double>(T, A.T_exp) + as : 0.0;
+            A.alpha_out[cidx] = alpha_new;
+            if (WANTG && A.G) {
+                A.G[4 * cidx] = -(Ep - Em) / dt;
+                for (int m = 0; m < 3; ++m) A.G[4 * cidx + 1 + m] = -((c * A.sumnw[m] - a * F[m]) * inv) / dt;
+            }
+        } else {
+            A.ug_out[cidx] = ugm;
+            A.alpha_out[cidx] = A.alpha_int[cidx];
+            if (WANTG && A.G) for (int m = 0; m < 4; ++m) A.G[4 * cidx + m] = 0.0;
+        }
+        cEm[lane] = ce; cInv[lane] = ci;
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int o = 0; o < NOWN; ++o) {
+            const int q = o % BY, r = o / BY;
+            const size_t base = ((size_t)(k0 + r) * A.nx1 + j0 + q) * A.nx0 + i0;
+#pragma unroll
+            for (int ii = 0; ii < TXC; ++ii) {
+                if (ii < nc) {
+                    const int lc = o * TXC + ii;
+                    TM v = It[lc];
+                    if (cOn[lc]) v = (v + cEm[lc]) * cInv[lc];
+                    IO<TS, TM>::st(A.Iout, (base + ii) * nd + s, v);
+                }
+            }
+        }
+    }
+}
+
+template <typename TS, typename TM, int BY, int BZ>
+rt_status launch_fs(rt_ctx *c, const StageArgs &A, int NT) {
+    constexpr int TXC = NCELL / (BY * BZ);
+    size_t nblk = (size_t)((A.nx0 + TXC - 1) / TXC) * (A.nx1 / BY) * (A.nx2 / BZ);
+    bool simple = true;
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd) simple = simple && (A.bc[a][sd] == RT_BC_PERIODIC || A.bc[a][sd] == RT_BC_OUTFLOW);
+    if (simple) {
+        if (A.G) k_stage_fs<TS, TM, BY, BZ, true, true><<<(unsigned)nblk, NT, 0, c->stream>>>(A);
+        else k_stage_fs<TS, TM, BY, BZ, false, true><<<(unsigned)nblk, NT, 0, c->stream>>>(A);
+    } else {
+        if (A.G) k_stage_fs<TS, TM, BY, BZ, true, false><<<(unsigned)nblk, NT, 0, c->stream>>>(A);
+        else k_stage_fs<TS, TM, BY, BZ, false, false><<<(unsigned)nblk, NT, 0, c->stream>>>(A);
+    }
+    RT_CUDA_TRY(c, cudaGetLastError());
+    return RT_OK;
+}
+
+template <typename TS, typename TM>
+rt_status launch_fs_blk(rt_ctx *c, const StageArgs &A, int NT) {
+    bool by = A.act1 && A.nx1 % 2 == 0, bz = A.act2 && A.nx2 % 2 == 0;
+    if (by && bz) return launch_fs<TS, TM, 2, 2>(c, A, NT);
+    if (by) return launch_fs<TS, TM, 2, 1>(c, A, NT);
+    return launch_fs<TS, TM, 1, 1>(c, A, NT);
+}
+
+}  // namespace
+
+bool rt_stage_fast_ok(const rt_ctx *c) {
+    return c->metric == RT_MINKOWSKI_CART && c->static_fluid && c->cfg.limiter == RT_LIM_MC &&
+           c->cfg.n_pole_zero == 0 && c->nd <= FS_NT && (double)c->ncell * c->nd < 2147483647.0;
+}
+
+rt_status rt_launch_stage_fs(rt_ctx *c, const StageArgs &A, int NT) {
+    if (c->cfg.precision == RT_FP64) return launch_fs_blk<double, double>(c, A, NT);
+    if (c->cfg.precision == RT_FP32) return launch_fs_blk<float, float>(c, A, NT);
+    return launch_fs_blk<__nv_bfloat16, float>(c, A, NT);
+}

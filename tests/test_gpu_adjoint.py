@@ -1,0 +1,152 @@
+"""Reverse mode of the CUDA library (rt_step_adjoint and the checkpointed
+autograd rollout) against the oracle's hand-derived adjoint, which the CPU
+tests pin to finite differences; at the full adjoint workload (64^3 cells,
+162 directions, 64 steps, a checkpoint every 8) against finite differences of
+the CUDA forward itself at sampled cells.
+
+Both sides run in FP64; the forward parity bar is 1e-11, and a gradient
+carries a few more roundings (the root of the temperature solve enters through
+the implicit function theorem), so 1e-9 of the largest component bounds the
+difference."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import rel_err
+from paper_2508_15532_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _case(order=2, limiter=None, outflow=False, N=8, index=60):
+    cfg, f = W.flat3d(N=N, n_geo=2, index=index)
+    cfg = dict(cfg, order=order)
+    if limiter:
+        cfg["limiter"] = limiter
+    if outflow:
+        cfg["bc"] = (("outflow", "outflow"),) + tuple(cfg["bc"][1:])
+    return cfg, f
+
+
+def _loss_cotangents(I, ug, w):
+    """L = sum E^2 + 3 sum u_g E  ->  (dL/dI, dL/du_g)."""
+    E = I @ w
+    return (2.0 * E + 3.0 * ug)[:, None] * w[None, :], 3.0 * E
+
+
+@pytest.mark.parametrize("order,limiter,outflow", [(2, None, False), (1, None, False), (2, "minmod", True)])
+def test_step_adjoint_matches_oracle(order, limiter, outflow):
+    torch = _torch()
+    import paper_2508_15532_b300 as rt
+    cfg, f = _case(order, limiter, outflow)
+    nsteps = 3
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    dt = o.cfl_dt(0.4)
+    w = o.grid()["w"]
+    o.set_intensity(f["I"])
+    o.step(dt, nsteps)
+    dI, du = _loss_cotangents(o.intensity(), o.ug(), w)
+    o2 = oracle.Oracle(cfg)
+    o2.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    gI, gk, ge = o2.adjoint(f["I"], f["ug"], nsteps, dt, dI, du)
+
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    st = rt.RadiationStep(rt.Grid(cfg["n_geo"]), cfg, precision="fp64")
+    st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+    Ib_in = torch.empty_like(T(dI))
+    ub_in = torch.empty(len(du), dtype=torch.float64, device=dev)
+    kb = torch.zeros_like(ub_in)
+    eb = torch.zeros_like(ub_in)
+    st.step_adjoint(T(f["I"]), T(f["ug"]), dt, nsteps, T(dI), T(du), Ib_in, ub_in, kb, eb)
+    torch.cuda.synchronize()
+    for name, got, ref in (("I0", Ib_in, gI), ("kappa", kb, gk), ("eta", eb, ge)):
+        err = rel_err(got.cpu().numpy(), ref, 1e-6).max()
+        assert err <= TOL, (name, err)
+
+
+def test_checkpointed_rollout_matches_oracle():
+    torch = _torch()
+    import paper_2508_15532_b300 as rt
+    from paper_2508_15532_b300.rollout import rollout
+    cfg, f = _case(2, None, False, N=8, index=61)
+    nsteps = 6
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    dt = o.cfl_dt(0.4)
+    w = o.grid()["w"]
+    o.set_intensity(f["I"])
+    o.step(dt, nsteps)
+    dI, du = _loss_cotangents(o.intensity(), o.ug(), w)
+    gI, gk, ge = o.adjoint(f["I"], f["ug"], nsteps, dt, dI, du)
+
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    st = rt.RadiationStep(rt.Grid(cfg["n_geo"]), cfg, precision="fp64")
+    fluid = dict(rho=T(f["rho"]), ucon=T(f["ucon"]), alpha_s=T(f["alpha_s"]))
+    I0 = T(f["I"]).requires_grad_()
+    kappa = T(f["kappa"]).requires_grad_()
+    eta = T(f["eta"]).requires_grad_()
+    ug0 = T(f["ug"])
+    IN, uN = rollout(st, fluid, I0, ug0, kappa, eta, nsteps, dt=dt, ckpt_every=4)   # segments of 4 and 2
+    wt = T(w)
+    E = IN @ wt
+    L = (E * E).sum() + 3.0 * (uN * E).sum()
+    L.backward()
+    ref_I = o.intensity()
+    assert rel_err(IN.detach().cpu().numpy(), ref_I, 1e-6).max() <= 1e-11
+    for name, got, ref in (("I0", I0.grad, gI), ("kappa", kappa.grad, gk), ("eta", eta.grad, ge)):
+        err = rel_err(got.cpu().numpy(), ref, 1e-6).max()
+        assert err <= TOL, (name, err)
+
+
+def test_adjoint_full_workload_against_finite_differences():
+    """64^3 cells, 162 directions, 64 steps, checkpoints every 8: the
+    gradient of L = sum_c E_c^2 in kappa and eta at sampled cells against
+    central differences of the CUDA forward (relative step 1e-4)."""
+    torch = _torch()
+    import paper_2508_15532_b300 as rt
+    from paper_2508_15532_b300.rollout import rollout
+    cfg, f = W.adjoint3d(N=64, n_geo=4)
+    nsteps, ck = cfg["nsteps"], cfg["ckpt_every"]
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    g = rt.Grid(cfg["n_geo"])
+    st = rt.RadiationStep(g, cfg, precision="fp64")
+    fluid = dict(rho=T(f["rho"]), ucon=T(f["ucon"]), alpha_s=T(f["alpha_s"]))
+    wt = T(g.query()[1])
+    I0, ug0 = T(f["I"]), T(f["ug"])
+    kappa = T(f["kappa"]).requires_grad_()
+    eta = T(f["eta"]).requires_grad_()
+    dt = st.cfl_dt(0.4)
+    IN, _ = rollout(st, fluid, I0, ug0, kappa, eta, nsteps, dt=dt, ckpt_every=ck)
+    E0 = (IN @ wt).detach()
+    ((IN @ wt) ** 2).sum().backward()
+    gk, ge = kappa.grad.detach(), eta.grad.detach()
+
+    def energy(kap, et):
+        with torch.no_grad():
+            I, _ = rollout(st, fluid, I0, ug0, kap, et, nsteps, dt=dt, ckpt_every=ck)
+            return I @ wt
+
+    rng = np.random.default_rng(5)
+    for c in rng.choice(f["rho"].shape[0], 3, replace=False):
+        for name, base, grad in (("kappa", kappa.detach(), gk), ("eta", eta.detach(), ge)):
+            h = 1e-4 * float(base[c])
+            p, m = base.clone(), base.clone()
+            p[c] += h
+            m[c] -= h
+            Ep = energy(p, eta.detach()) if name == "kappa" else energy(kappa.detach(), p)
+            Em = energy(m, eta.detach()) if name == "kappa" else energy(kappa.detach(), m)
+            # L(+) - L(-) = sum (E+ - E-)(E+ + E-): no cancellation in a 262k-term sum
+            fd = float(((Ep - Em) * (Ep + Em)).sum()) / (2 * h)
+            scale = float(grad.abs().max())
+            assert abs(float(grad[c]) - fd) <= 1e-5 * max(abs(fd), 1e-3 * scale), (name, int(c), float(grad[c]), fd)
+    assert torch.isfinite(E0).all()

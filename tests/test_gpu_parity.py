@@ -104,6 +104,24 @@ def test_flat_fp32_and_bf16_against_fp64_oracle():
     assert rel_err(b["E"], ref["E"]).max() < 5e-3
 
 
+def test_flat_moving_fluid_fp64_and_fp32():
+    """Fluid in motion (general kernel: per-direction boost D, advective flux term)."""
+    cfg, f = small_flat(nx=(18, 10, 6), index=25)
+    rng = np.random.Generator(np.random.PCG64(W.SEED0 + 125))
+    v = rng.uniform(-0.3, 0.3, (len(f["rho"]), 3))
+    gam = 1.0 / np.sqrt(1.0 - (v * v).sum(1))
+    f["ucon"] = np.concatenate([gam[:, None], gam[:, None] * v], axis=1)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 3)
+    out = run_gpu(cfg, f, dt, 3, "fp64")
+    assert out["fails"] == 0
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert rel_err(out["ug"], ref["ug"]).max() < 1e-11
+    assert np.abs(out["G"] - ref["G"]).max() < 1e-9 * np.abs(ref["G"]).max()
+    o32 = run_gpu(cfg, f, dt, 3, "fp32")
+    assert rel_err(o32["I"], ref["I"], 1e-3).max() < 1e-4
+
+
 def test_flat_periodic_energy_conserved_fp64_gpu():
     cfg, f = small_flat(nx=(16, 8, 8), index=24)
     dt = oracle.Oracle(cfg).cfl_dt(0.4)
