@@ -269,6 +269,60 @@ __device__ __forceinline__ void axis_adj(const double (&V)[7], const double (&B)
     }
 }
 
+// limited slope of a cell and its derivatives in (dl, dr)
+__device__ __forceinline__ double lim_dv(int kind, double dl, double dr, double &gl, double &gr) {
+    lim_d(kind, dl, dr, gl, gr);
+    return limiter<double>(kind, dl, dr);
+}
+
+// axis_adj for a cell whose stencil maps to seven distinct cells (every
+// interior cell, and every cell of a periodic axis): only offset 0 is this
+// cell, so face m needs only the derivative at its own stencil position 0 -
+// the right neighbour's slope for m = -2, the full pair for m = -1 and 0, the
+// left cell's slope for m = 1 - and the slopes of offsets -1, 0, 1.
+__device__ __forceinline__ void axis_adj_int(const double (&V)[7], const double (&B)[5], const double *const (&fc)[4],
+                                             double n, double coef, int lim, double &g, double (&tb)[2]) {
+    if (n == 0.0) return;
+    const double an = fabs(n);
+    const bool pos = n > 0.0;
+    double ga[3], gb[3], sv[3];
+#pragma unroll
+    for (int q = -1; q <= 1; ++q) sv[q + 1] = lim_dv(lim, V[q + 4] - V[q + 3], V[q + 3] - V[q + 2], ga[q + 1], gb[q + 1]);
+    const double ph[4] = {coef * (B[1] - B[0]), coef * (B[2] - B[1]), coef * (B[3] - B[2]), coef * (B[4] - B[3])};
+    // m = -2: this cell is I_{r+1}; IR = I_r - s_r/2 with s_r the slope of offset -1
+    {
+        const double *f = fc[0];
+        const double IRb = ph[0] * n * (pos ? f[1] : f[0]);
+        g += -0.5 * IRb * ga[0];
+    }
+    // m = -1: this cell is I_r
+    {
+        const double *f = fc[1];
+        const double cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
+        const double ILb = ph[1] * n * cL, IRb = ph[1] * n * cR, c3t = ph[1] * an * f[2];
+        g += -c3t + 0.5 * ILb * ga[0] + IRb * (1.0 + 0.5 * ga[1] - 0.5 * gb[1]);
+        const double IL = V[2] + 0.5 * sv[0], IR = V[3] - 0.5 * sv[1];
+        const double cLb = ph[1] * n * IL, cRb = ph[1] * n * IR;
+        tb[0] += (pos ? cLb : cRb) * f[3] + (pos ? cRb : cLb) * f[4] - ph[1] * an * (V[3] - V[2]) * f[5];
+    }
+    // m = 0: this cell is I_l
+    {
+        const double *f = fc[2];
+        const double cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
+        const double ILb = ph[2] * n * cL, IRb = ph[2] * n * cR, c3t = ph[2] * an * f[2];
+        g += c3t + ILb * (1.0 - 0.5 * ga[1] + 0.5 * gb[1]) + 0.5 * IRb * gb[2];
+        const double IL = V[3] + 0.5 * sv[1], IR = V[4] - 0.5 * sv[2];
+        const double cLb = ph[2] * n * IL, cRb = ph[2] * n * IR;
+        tb[1] += (pos ? cLb : cRb) * f[3] + (pos ? cRb : cLb) * f[4] - ph[2] * an * (V[4] - V[3]) * f[5];
+    }
+    // m = 1: this cell is I_{l-1}; IL = I_l + s_l/2 with s_l the slope of offset 1
+    {
+        const double *f = fc[3];
+        const double ILb = ph[3] * n * (pos ? f[0] : f[1]);
+        g += -0.5 * ILb * gb[2];
+    }
+}
+
 __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
     constexpr int NW = ADJ_NT / 32;
     __shared__ double fcs[NFACE][6];
@@ -335,7 +389,8 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
                 for (int o = -3; o <= 3; ++o) eq |= (amap(i + o, nx0, A.per[0]) == i) << (o + 3);
                 const double *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
                 double tb[2] = {0.0, 0.0};
-                axis_adj(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
+                if (eq == (1u << 3)) axis_adj_int(WX, BX, fc, n[0], coef[0], A.limiter, g, tb);
+                else axis_adj(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
                 const double h = A.abar * 0.5 * len(0);
                 abt[t] += h * (tb[0] * (1 + ((eq >> 2) & 1)) + tb[1] * (1 + ((eq >> 4) & 1)));
             }
@@ -359,7 +414,8 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
                 const int base = TXA + 3 + (a - 1) * 4 * TXA + 4 * t;
                 const double *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
                 double tb[2] = {0.0, 0.0};
-                axis_adj(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
+                if (eq == (1u << 3)) axis_adj_int(V, B, fc, n[a], coef[a], A.limiter, g, tb);
+                else axis_adj(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
                 const double h = A.abar * 0.5 * len(a);
                 abt[t] += h * (tb[0] * (1 + ((eq >> 2) & 1)) + tb[1] * (1 + ((eq >> 4) & 1)));
             }
