@@ -118,6 +118,25 @@ rt_status rt_get_ugas(rt_ctx *c, double *u_gas);
  * directions.  Written to *dt. */
 rt_status rt_cfl_dt(rt_ctx *c, double cfl, double *dt);
 
+/* rt_cfl_dt without device allocation (the paper has no counterpart: this is
+ * an interface for callers that cannot allocate).  rt_cfl_dt obtains its
+ * reduction word with cudaMalloc/cudaFree on every call; a host code whose
+ * memory manager owns the device (a caching allocator or a fixed pool) or a
+ * time loop that must not synchronise the device between steps cannot allow
+ * that.  This variant reduces in a file-scope static device array of 8193
+ * doubles (64 KB) that every GPU loading the library holds until exit.
+ * Same result as rt_cfl_dt.  Runs on the current device, which must be the
+ * context's.  Limit: nx[0]*nx[1]*n_dir (point, direction) items, or n_dir for
+ * flat geometry, at most 8192*2048 = 16,777,216; beyond it returns RT_EINVAL
+ * with a message naming the limit.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  Every call on a device shares the one array:
+ * calls whose kernels overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  Nothing needs clearing between calls:
+ * each slot read is written earlier in the same call.  Synchronises the
+ * context's stream; allocates nothing. */
+rt_status rt_cfl_dt_noalloc(rt_ctx *c, double cfl, double *dt);
+
 /* nsteps steps of size dt (dt <= 0: the cfl bound with cfl 0.4), section 3.6:
  * predictor transport over dt/2 + interaction over dt/2, corrector transport
  * over dt with the predictor fluxes + interaction over dt.  *n_fail (may be

@@ -47,7 +47,7 @@ _lib = None
 EXPORTS = ["rt_create_geodesic_grid", "rt_grid_query", "rt_destroy_grid", "rt_create", "rt_destroy",
            "rt_last_error", "rt_set_metric", "rt_set_fluid", "rt_set_intensity", "rt_get_intensity",
            "rt_set_ugas", "rt_get_ugas", "rt_cfl_dt", "rt_step", "rt_moments", "rt_grid_last_error",
-           "rt_set_timing", "rt_get_timing", "rt_step_adjoint"]
+           "rt_set_timing", "rt_get_timing", "rt_cfl_dt_noalloc", "rt_step_adjoint"]
 
 
 def lib():
@@ -79,6 +79,7 @@ def lib():
         L.rt_grid_last_error.restype = C.c_char_p
         L.rt_set_timing.argtypes = [vp, i]
         L.rt_get_timing.argtypes = [vp, C.POINTER(d), C.POINTER(C.c_longlong)]
+        L.rt_cfl_dt_noalloc.argtypes = [vp, d, C.POINTER(d)]
         L.rt_step_adjoint.argtypes = [vp, vp, vp, d, i, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
@@ -194,6 +195,14 @@ class RadiationStep:
     def cfl_dt(self, cfl=0.4):
         d = C.c_double()
         self._check(lib().rt_cfl_dt(self.h, float(cfl), C.byref(d)))
+        return d.value
+
+    def cfl_dt_noalloc(self, cfl=0.4):
+        """cfl_dt for callers that cannot allocate device memory between
+        steps: the reduction runs in a fixed static scratch array inside the
+        library (see rt_cfl_dt_noalloc)."""
+        d = C.c_double()
+        self._check(lib().rt_cfl_dt_noalloc(self.h, float(cfl), C.byref(d)))
         return d.value
 
     def step(self, dt, nsteps=1, check=False):
