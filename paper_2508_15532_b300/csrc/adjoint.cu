@@ -1,5 +1,5 @@
 // adjoint.cu — reverse mode of the radiation step for flat Cartesian geometry
-// with the fluid at rest, FP64 intensities (section 5.2 motivates gradients
+// with the fluid at rest, FP64 or FP32 intensities (section 5.2 motivates gradients
 // through the step; the reverse pass is derived by hand from eq.
 // radiative_transfer_discrete, eqs. rad_speeds / flux_Jiang and method 3 of
 // section 3.5.2).
@@ -30,9 +30,11 @@ constexpr int NFACE = 9 * TXA + 3;
 struct SrcArgs {
     int ncell, nd, source;
     double dtk, sumw, T_exp, arad, rho_exp;
-    const double *w, *I, *ug_in, *cc_au, *cc_as, *cc_Y, *eta, *rho;
+    const double *w, *ug_in, *cc_au, *cc_as, *cc_Y, *eta, *rho;
+    const void *I;                           // storage type of the context
     const uint8_t *cc_on;
-    double *I_out, *ug_out;                  // forward
+    void *I_out;                             // forward (storage type)
+    double *ug_out;
     const double *Ibo, *ubo;                 // reverse: cotangents of the outputs
     double *Ibi, *ubi;                       // cotangents of I (written) and u_g entering (ub_acc: added)
     int ub_acc;
@@ -55,8 +57,15 @@ __device__ __forceinline__ double tsum16(double (&v)[SC], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
+// intensity of storage type TS as FP64, and back
+template <typename TS> __device__ __forceinline__ double ld64(const void *p, size_t i) {
+    return (double)__ldg((const TS *)p + i);
+}
+template <typename TS> __device__ __forceinline__ void st64(void *p, size_t i, double v) { ((TS *)p)[i] = (TS)v; }
+
 // REV = false: I_out = interaction(I), u_g out.  REV = true: the reverse.
-template <bool REV>
+// The per-cell arithmetic is FP64 for every storage type TS.
+template <bool REV, typename TS>
 __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     constexpr int NW = ADJ_NT / 32;
     __shared__ double part[NW][3][SC];
@@ -69,7 +78,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     const double w = act ? A.w[s] : 0.0;
     double Iv[SC], Bv[SC], v[SC];
 #pragma unroll
-    for (int k = 0; k < SC; ++k) Iv[k] = (act && k < nc) ? A.I[(c0 + k) * A.nd + s] : 0.0;
+    for (int k = 0; k < SC; ++k) Iv[k] = (act && k < nc) ? ld64<TS>(A.I, (c0 + k) * A.nd + s) : 0.0;
     if (REV) {
 #pragma unroll
         for (int k = 0; k < SC; ++k) Bv[k] = (act && k < nc) ? A.Ibo[(c0 + k) * A.nd + s] : 0.0;
@@ -170,7 +179,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     for (int k = 0; k < SC; ++k) {
         if (k >= nc) break;
         const size_t i = (c0 + k) * A.nd + s;
-        if (!REV) A.I_out[i] = sh_on[k] ? (Iv[k] + sh_a[k]) * sh_b[k] : Iv[k];
+        if (!REV) st64<TS>(A.I_out, i, sh_on[k] ? (Iv[k] + sh_a[k]) * sh_b[k] : Iv[k]);
         else A.Ibi[i] = sh_on[k] ? (Bv[k] - sh_b[k] * w) * sh_a[k] + sh_c[k] * w : Bv[k];
     }
 }
@@ -179,7 +188,8 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
 struct TrArgs {
     int nx[3], act[3], per[3], nd, limiter, tau_dt;
     double dx[3], abar, dtk, T_exp, rho_exp;
-    const double *dir, *I, *alpha, *Ibo;
+    const double *dir, *alpha, *Ibo;
+    const void *I;                           // storage type of the context
     double *out_src, *base_out;
     int src_acc, add_base;
     const double *ug, *cc_au, *cc_Y, *rho;
@@ -213,18 +223,18 @@ __device__ void face_cd(double tau, double *fc) {
 }
 
 // derivative of the limited slope in (dl, dr), branches of rtk::limiter
-__device__ __forceinline__ void lim_d(int kind, double dl, double dr, double &gl, double &gr) {
-    gl = 0.0; gr = 0.0;
-    if (kind == RT_LIM_DONOR || dl * dr <= 0.0) return;
-    const double al = fabs(dl), ar = fabs(dr);
-    if (kind == RT_LIM_MINMOD) { if (al < ar) gl = 1.0; else gr = 1.0; return; }
-    double m = 2.0 * al;
+template <typename TM> __device__ __forceinline__ void lim_d(int kind, TM dl, TM dr, TM &gl, TM &gr) {
+    gl = TM(0); gr = TM(0);
+    if (kind == RT_LIM_DONOR || dl * dr <= TM(0)) return;
+    const TM al = fabs(dl), ar = fabs(dr);
+    if (kind == RT_LIM_MINMOD) { if (al < ar) gl = TM(1); else gr = TM(1); return; }
+    TM m = TM(2) * al;
     int which = 0;
-    if (2.0 * ar < m) { m = 2.0 * ar; which = 1; }
-    if (0.5 * fabs(dl + dr) < m) which = 2;
-    if (which == 0) gl = 2.0;
-    else if (which == 1) gr = 2.0;
-    else { gl = 0.5; gr = 0.5; }
+    if (TM(2) * ar < m) { m = TM(2) * ar; which = 1; }
+    if (TM(0.5) * fabs(dl + dr) < m) which = 2;
+    if (which == 0) gl = TM(2);
+    else if (which == 1) gr = TM(2);
+    else { gl = TM(0.5); gr = TM(0.5); }
 }
 
 // One axis of the gather for one (cell, direction).  V: intensities at
@@ -233,46 +243,46 @@ __device__ __forceinline__ void lim_d(int kind, double dl, double dr, double &gl
 // offset o maps to this cell, fc[m + 2]: coefficients of the face between
 // offsets m and m + 1 (m = -2..1).  Adds the cotangent of this cell's
 // intensity to g and the cotangent of tau of the two adjacent faces to tb.
-__device__ __forceinline__ void axis_adj(const double (&V)[7], const double (&B)[5], unsigned eq,
-                                         const double *const (&fc)[4], double n, double coef, int lim, double &g,
-                                         double (&tb)[2]) {
-    if (n == 0.0) return;
-    const double an = fabs(n);
+template <typename TM>
+__device__ __forceinline__ void axis_adj(const TM (&V)[7], const TM (&B)[5], unsigned eq, const TM *const (&fc)[4],
+                                         TM n, TM coef, int lim, TM &g, TM (&tb)[2]) {
+    if (n == TM(0)) return;
+    const TM an = fabs(n), h = TM(0.5), one = TM(1);
 #pragma unroll
     for (int m = -2; m <= 1; ++m) {
-        const double phib = coef * (B[m + 3] - B[m + 2]);
-        if (phib == 0.0) continue;
-        const double Ill = V[m + 2], Il = V[m + 3], Ir = V[m + 4], Irr = V[m + 5];
-        const double *f = fc[m + 2];
-        double gla, glb, gra, grb;
-        lim_d(lim, Ir - Il, Il - Ill, gla, glb);
-        lim_d(lim, Irr - Ir, Ir - Il, gra, grb);
-        const double cL = n > 0.0 ? f[0] : f[1], cR = n > 0.0 ? f[1] : f[0];
-        const double ILb = phib * n * cL, IRb = phib * n * cR;
-        const double c3t = phib * an * f[2];
-        const double dIll = -0.5 * ILb * glb;
-        const double dIl = c3t + ILb * (1.0 - 0.5 * gla + 0.5 * glb) + 0.5 * IRb * grb;
-        const double dIr = -c3t + 0.5 * ILb * gla + IRb * (1.0 + 0.5 * gra - 0.5 * grb);
-        const double dIrr = -0.5 * IRb * gra;
+        const TM phib = coef * (B[m + 3] - B[m + 2]);
+        if (phib == TM(0)) continue;
+        const TM Ill = V[m + 2], Il = V[m + 3], Ir = V[m + 4], Irr = V[m + 5];
+        const TM *f = fc[m + 2];
+        TM gla, glb, gra, grb;
+        lim_d<TM>(lim, Ir - Il, Il - Ill, gla, glb);
+        lim_d<TM>(lim, Irr - Ir, Ir - Il, gra, grb);
+        const TM cL = n > TM(0) ? f[0] : f[1], cR = n > TM(0) ? f[1] : f[0];
+        const TM ILb = phib * n * cL, IRb = phib * n * cR;
+        const TM c3t = phib * an * f[2];
+        const TM dIll = -h * ILb * glb;
+        const TM dIl = c3t + ILb * (one - h * gla + h * glb) + h * IRb * grb;
+        const TM dIr = -c3t + h * ILb * gla + IRb * (one + h * gra - h * grb);
+        const TM dIrr = -h * IRb * gra;
         if (eq & (1u << (m + 2))) g += dIll;
         if (eq & (1u << (m + 3))) g += dIl;
         if (eq & (1u << (m + 4))) g += dIr;
         if (eq & (1u << (m + 5))) g += dIrr;
         if (m == -1 || m == 0) {
-            double sl = limiter<double>(lim, Ir - Il, Il - Ill), sr = limiter<double>(lim, Irr - Ir, Ir - Il);
-            const double IL = Il + 0.5 * sl, IR = Ir - 0.5 * sr;
-            const double cLb = phib * n * IL, cRb = phib * n * IR;
-            const double c1b = n > 0.0 ? cLb : cRb, c2b = n > 0.0 ? cRb : cLb;
-            const double c3b = -phib * an * (Ir - Il);
+            TM sl = limiter<TM>(lim, Ir - Il, Il - Ill), sr = limiter<TM>(lim, Irr - Ir, Ir - Il);
+            const TM IL = Il + h * sl, IR = Ir - h * sr;
+            const TM cLb = phib * n * IL, cRb = phib * n * IR;
+            const TM c1b = n > TM(0) ? cLb : cRb, c2b = n > TM(0) ? cRb : cLb;
+            const TM c3b = -phib * an * (Ir - Il);
             tb[m + 1] += c1b * f[3] + c2b * f[4] + c3b * f[5];
         }
     }
 }
 
 // limited slope of a cell and its derivatives in (dl, dr)
-__device__ __forceinline__ double lim_dv(int kind, double dl, double dr, double &gl, double &gr) {
-    lim_d(kind, dl, dr, gl, gr);
-    return limiter<double>(kind, dl, dr);
+template <typename TM> __device__ __forceinline__ TM lim_dv(int kind, TM dl, TM dr, TM &gl, TM &gr) {
+    lim_d<TM>(kind, dl, dr, gl, gr);
+    return limiter<TM>(kind, dl, dr);
 }
 
 // axis_adj for a cell whose stencil maps to seven distinct cells (every
@@ -280,52 +290,56 @@ __device__ __forceinline__ double lim_dv(int kind, double dl, double dr, double 
 // cell, so face m needs only the derivative at its own stencil position 0 -
 // the right neighbour's slope for m = -2, the full pair for m = -1 and 0, the
 // left cell's slope for m = 1 - and the slopes of offsets -1, 0, 1.
-__device__ __forceinline__ void axis_adj_int(const double (&V)[7], const double (&B)[5], const double *const (&fc)[4],
-                                             double n, double coef, int lim, double &g, double (&tb)[2]) {
-    if (n == 0.0) return;
-    const double an = fabs(n);
-    const bool pos = n > 0.0;
-    double ga[3], gb[3], sv[3];
+template <typename TM>
+__device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5], const TM *const (&fc)[4], TM n, TM coef,
+                                             int lim, TM &g, TM (&tb)[2]) {
+    if (n == TM(0)) return;
+    const TM an = fabs(n), h = TM(0.5), one = TM(1);
+    const bool pos = n > TM(0);
+    TM ga[3], gb[3], sv[3];
 #pragma unroll
-    for (int q = -1; q <= 1; ++q) sv[q + 1] = lim_dv(lim, V[q + 4] - V[q + 3], V[q + 3] - V[q + 2], ga[q + 1], gb[q + 1]);
-    const double ph[4] = {coef * (B[1] - B[0]), coef * (B[2] - B[1]), coef * (B[3] - B[2]), coef * (B[4] - B[3])};
+    for (int q = -1; q <= 1; ++q) sv[q + 1] = lim_dv<TM>(lim, V[q + 4] - V[q + 3], V[q + 3] - V[q + 2], ga[q + 1], gb[q + 1]);
+    const TM ph[4] = {coef * (B[1] - B[0]), coef * (B[2] - B[1]), coef * (B[3] - B[2]), coef * (B[4] - B[3])};
     // m = -2: this cell is I_{r+1}; IR = I_r - s_r/2 with s_r the slope of offset -1
     {
-        const double *f = fc[0];
-        const double IRb = ph[0] * n * (pos ? f[1] : f[0]);
-        g += -0.5 * IRb * ga[0];
+        const TM *f = fc[0];
+        const TM IRb = ph[0] * n * (pos ? f[1] : f[0]);
+        g += -h * IRb * ga[0];
     }
     // m = -1: this cell is I_r
     {
-        const double *f = fc[1];
-        const double cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
-        const double ILb = ph[1] * n * cL, IRb = ph[1] * n * cR, c3t = ph[1] * an * f[2];
-        g += -c3t + 0.5 * ILb * ga[0] + IRb * (1.0 + 0.5 * ga[1] - 0.5 * gb[1]);
-        const double IL = V[2] + 0.5 * sv[0], IR = V[3] - 0.5 * sv[1];
-        const double cLb = ph[1] * n * IL, cRb = ph[1] * n * IR;
+        const TM *f = fc[1];
+        const TM cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
+        const TM ILb = ph[1] * n * cL, IRb = ph[1] * n * cR, c3t = ph[1] * an * f[2];
+        g += -c3t + h * ILb * ga[0] + IRb * (one + h * ga[1] - h * gb[1]);
+        const TM IL = V[2] + h * sv[0], IR = V[3] - h * sv[1];
+        const TM cLb = ph[1] * n * IL, cRb = ph[1] * n * IR;
         tb[0] += (pos ? cLb : cRb) * f[3] + (pos ? cRb : cLb) * f[4] - ph[1] * an * (V[3] - V[2]) * f[5];
     }
     // m = 0: this cell is I_l
     {
-        const double *f = fc[2];
-        const double cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
-        const double ILb = ph[2] * n * cL, IRb = ph[2] * n * cR, c3t = ph[2] * an * f[2];
-        g += c3t + ILb * (1.0 - 0.5 * ga[1] + 0.5 * gb[1]) + 0.5 * IRb * gb[2];
-        const double IL = V[3] + 0.5 * sv[1], IR = V[4] - 0.5 * sv[2];
-        const double cLb = ph[2] * n * IL, cRb = ph[2] * n * IR;
+        const TM *f = fc[2];
+        const TM cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
+        const TM ILb = ph[2] * n * cL, IRb = ph[2] * n * cR, c3t = ph[2] * an * f[2];
+        g += c3t + ILb * (one - h * ga[1] + h * gb[1]) + h * IRb * gb[2];
+        const TM IL = V[3] + h * sv[1], IR = V[4] - h * sv[2];
+        const TM cLb = ph[2] * n * IL, cRb = ph[2] * n * IR;
         tb[1] += (pos ? cLb : cRb) * f[3] + (pos ? cRb : cLb) * f[4] - ph[2] * an * (V[4] - V[3]) * f[5];
     }
     // m = 1: this cell is I_{l-1}; IL = I_l + s_l/2 with s_l the slope of offset 1
     {
-        const double *f = fc[3];
-        const double ILb = ph[3] * n * (pos ? f[0] : f[1]);
-        g += -0.5 * ILb * gb[2];
+        const TM *f = fc[3];
+        const TM ILb = ph[3] * n * (pos ? f[0] : f[1]);
+        g += -h * ILb * gb[2];
     }
 }
 
+// TS: storage of the intensities, TM: per-element arithmetic (cotangents are
+// loaded and stored in FP64; per-cell sums are FP64)
+template <typename TS, typename TM>
 __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
     constexpr int NW = ADJ_NT / 32;
-    __shared__ double fcs[NFACE][6];
+    __shared__ TM fcs[NFACE][6];
     __shared__ double abw[NW][TXA];
     const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
     const bool act = s < A.nd;
@@ -352,29 +366,31 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
         } else {
             cl = cell(x0 + t, j, amap(k + m, nx2, A.per[2])); cr = cell(x0 + t, j, amap(k + m + 1, nx2, A.per[2]));
         }
-        face_cd(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len(a), fcs[f]);
+        double fd[6];
+        face_cd(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len(a), fd);
+        for (int q = 0; q < 6; ++q) fcs[f][q] = (TM)fd[q];
     }
     __syncthreads();
 
-    double n[3] = {0.0, 0.0, 0.0};
-    if (act) for (int a = 0; a < 3; ++a) n[a] = A.dir[3 * s + a];
-    const double coef[3] = {A.dtk / A.dx[0], A.dtk / A.dx[1], A.dtk / A.dx[2]};
+    TM n[3] = {TM(0), TM(0), TM(0)};
+    if (act) for (int a = 0; a < 3; ++a) n[a] = (TM)A.dir[3 * s + a];
+    const TM coef[3] = {TM(A.dtk / A.dx[0]), TM(A.dtk / A.dx[1]), TM(A.dtk / A.dx[2])};
     const int nd = A.nd;
-    auto ldI = [&](size_t c) { return act ? __ldg(A.I + c * nd + s) : 0.0; };
-    auto ldB = [&](size_t c) { return act ? __ldg(A.Ibo + c * nd + s) : 0.0; };
+    auto ldI = [&](size_t c) -> TM { return act ? IO<TS, TM>::ld(A.I, c * nd + s) : TM(0); };
+    auto ldB = [&](size_t c) -> double { return act ? __ldg(A.Ibo + c * nd + s) : 0.0; };
     double abt[TXA];
 #pragma unroll
     for (int t = 0; t < TXA; ++t) abt[t] = 0.0;
 
     // sliding x1 window
-    double WX[7], BX[5];
+    TM WX[7], BX[5];
     if (A.act[0]) {
 #pragma unroll
         for (int o = -3; o <= 3; ++o) WX[o + 3] = ldI(cell(amap(x0 + o, nx0, A.per[0]), j, k));
 #pragma unroll
         for (int o = -2; o <= 2; ++o) {
             int q = x0 + o;
-            BX[o + 2] = (A.per[0] || (q >= 0 && q < nx0)) ? ldB(cell(amap(q, nx0, A.per[0]), j, k)) : 0.0;
+            BX[o + 2] = (A.per[0] || (q >= 0 && q < nx0)) ? (TM)ldB(cell(amap(q, nx0, A.per[0]), j, k)) : TM(0);
         }
     }
 #pragma unroll
@@ -382,22 +398,23 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
         if (t < nc) {
             const int i = x0 + t;
             const size_t c = cell(i, j, k);
-            const double Ic = ldI(c), Bc = ldB(c);
-            double g = 0.0;
+            const TM Ic = ldI(c);
+            const double Bc = ldB(c);
+            TM g = TM(0);
             if (A.act[0]) {
                 unsigned eq = 0;
                 for (int o = -3; o <= 3; ++o) eq |= (amap(i + o, nx0, A.per[0]) == i) << (o + 3);
-                const double *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
-                double tb[2] = {0.0, 0.0};
-                if (eq == (1u << 3)) axis_adj_int(WX, BX, fc, n[0], coef[0], A.limiter, g, tb);
-                else axis_adj(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
+                const TM *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
+                TM tb[2] = {TM(0), TM(0)};
+                if (eq == (1u << 3)) axis_adj_int<TM>(WX, BX, fc, n[0], coef[0], A.limiter, g, tb);
+                else axis_adj<TM>(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
                 const double h = A.abar * 0.5 * len(0);
-                abt[t] += h * (tb[0] * (1 + ((eq >> 2) & 1)) + tb[1] * (1 + ((eq >> 4) & 1)));
+                abt[t] += h * ((double)tb[0] * (1 + ((eq >> 2) & 1)) + (double)tb[1] * (1 + ((eq >> 4) & 1)));
             }
             for (int a = 1; a < 3; ++a) {
                 if (!A.act[a]) continue;
                 const int na = a == 1 ? nx1 : nx2, pos = a == 1 ? j : k;
-                double V[7], B[5];
+                TM V[7], B[5];
                 unsigned eq = 0;
 #pragma unroll
                 for (int o = -3; o <= 3; ++o) {
@@ -408,20 +425,20 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
 #pragma unroll
                 for (int o = -2; o <= 2; ++o) {
                     const int q = pos + o, mq = amap(q, na, A.per[a]);
-                    B[o + 2] = o == 0 ? Bc
-                               : ((A.per[a] || (q >= 0 && q < na)) ? ldB(a == 1 ? cell(i, mq, k) : cell(i, j, mq)) : 0.0);
+                    B[o + 2] = o == 0 ? (TM)Bc
+                               : ((A.per[a] || (q >= 0 && q < na)) ? (TM)ldB(a == 1 ? cell(i, mq, k) : cell(i, j, mq)) : TM(0));
                 }
                 const int base = TXA + 3 + (a - 1) * 4 * TXA + 4 * t;
-                const double *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
-                double tb[2] = {0.0, 0.0};
-                if (eq == (1u << 3)) axis_adj_int(V, B, fc, n[a], coef[a], A.limiter, g, tb);
-                else axis_adj(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
+                const TM *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
+                TM tb[2] = {TM(0), TM(0)};
+                if (eq == (1u << 3)) axis_adj_int<TM>(V, B, fc, n[a], coef[a], A.limiter, g, tb);
+                else axis_adj<TM>(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
                 const double h = A.abar * 0.5 * len(a);
-                abt[t] += h * (tb[0] * (1 + ((eq >> 2) & 1)) + tb[1] * (1 + ((eq >> 4) & 1)));
+                abt[t] += h * ((double)tb[0] * (1 + ((eq >> 2) & 1)) + (double)tb[1] * (1 + ((eq >> 4) & 1)));
             }
             if (act) {
                 const size_t ix = c * nd + s;
-                double v = g + (A.add_base ? Bc : 0.0);
+                double v = (double)g + (A.add_base ? Bc : 0.0);
                 if (A.src_acc) v += A.out_src[ix];
                 A.out_src[ix] = v;
                 if (A.base_out) A.base_out[ix] = Bc;
@@ -434,7 +451,7 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
                 for (int o = 0; o < 4; ++o) BX[o] = BX[o + 1];
                 WX[6] = ldI(cell(amap(i + 4, nx0, A.per[0]), j, k));
                 const int q = i + 3;
-                BX[4] = (A.per[0] || q < nx0) ? ldB(cell(amap(q, nx0, A.per[0]), j, k)) : 0.0;
+                BX[4] = (A.per[0] || q < nx0) ? (TM)ldB(cell(amap(q, nx0, A.per[0]), j, k)) : TM(0);
             }
         }
     }
@@ -470,7 +487,7 @@ static rt_status adj_fail(rt_ctx *c, rt_status st, const std::string &msg) {
     return st;
 }
 
-static rt_status launch_src(rt_ctx *c, bool rev, const double *I, const double *ug_in, double dtk, double *I_out,
+static rt_status launch_src(rt_ctx *c, bool rev, const void *I, const double *ug_in, double dtk, void *I_out,
                             double *ug_out, const double *Ibo, const double *ubo, double *Ibi, double *ubi, int ub_acc,
                             double *kb, double *eb) {
     SrcArgs A{};
@@ -482,13 +499,19 @@ static rt_status launch_src(rt_ctx *c, bool rev, const double *I, const double *
     A.I_out = I_out; A.ug_out = ug_out; A.Ibo = Ibo; A.ubo = ubo; A.Ibi = Ibi; A.ubi = ubi; A.ub_acc = ub_acc;
     A.kb = kb; A.eb = eb; A.fail = c->fail;
     unsigned nblk = (unsigned)((c->ncell + SC - 1) / SC);
-    if (rev) k_src<true><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-    else k_src<false><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    const bool f64 = c->cfg.precision == RT_FP64;
+    if (rev) {
+        if (f64) k_src<true, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+        else k_src<true, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    } else {
+        if (f64) k_src<false, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+        else k_src<false, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    }
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }
 
-static rt_status launch_tr(rt_ctx *c, const double *I, const double *ug, const double *alpha, double dtk,
+static rt_status launch_tr(rt_ctx *c, const void *I, const double *ug, const double *alpha, double dtk,
                            const double *Ibo, double *out_src, int src_acc, int add_base, double *base_out, double *ub,
                            int ub_acc, double *kb) {
     TrArgs A{};
@@ -503,13 +526,14 @@ static rt_status launch_tr(rt_ctx *c, const double *I, const double *ug, const d
     A.cc_on = c->cc_on; A.ub = ub; A.kb = kb; A.ub_acc = ub_acc;
     const int nseg = (f.nx[0] + TXA - 1) / TXA;
     unsigned nblk = (unsigned)((size_t)nseg * f.nx[1] * f.nx[2]);
-    k_tr_adj<<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    if (c->cfg.precision == RT_FP64) k_tr_adj<double, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    else k_tr_adj<float, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }
 
 // transport-only stage through the forward stage kernel (interaction off)
-static rt_status transport_only(rt_ctx *c, const double *Isrc, const double *Ibase, double *Iout, const double *ug,
+static rt_status transport_only(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout, const double *ug,
                                 const double *alpha, double dtk, double *ug_scr, double *a_scr) {
     const int src = c->cfg.source;
     c->cfg.source = 0;
@@ -527,7 +551,7 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     if (c->metric < 0 || !c->have_fluid) return adj_fail(c, RT_ESTATE, "rt_set_metric and rt_set_fluid must precede rt_step_adjoint");
     if (c->metric != RT_MINKOWSKI_CART || !c->static_fluid)
         return adj_fail(c, RT_EINVAL, "rt_step_adjoint: flat Cartesian geometry with the fluid at rest only");
-    if (c->cfg.precision != RT_FP64) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: FP64 intensities only");
+    if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: FP64 or FP32 intensities only");
     if (c->nd > ADJ_NT) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: at most 192 directions");
     for (int a = 0; a < 3; ++a) {
         if (!c->active[a]) continue;
@@ -545,35 +569,41 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     }
     const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
     const int order = c->cfg.order;
-    // arena: per step I^n, (order 2: I*_t, I*), I^{n+1}_t, u_g^n, (u_g*);
-    // reverse: two intensity cotangents, three cell cotangents; scratch
-    const size_t per_step_i = order == 2 ? 4 : 2, per_step_c = order == 2 ? 2 : 1;
-    const size_t need = ((per_step_i * nsteps + 2) * ni + (per_step_c * nsteps + 8) * nc) * sizeof(double);
+    // arena: per step I^n, (order 2: I*_t, I*), I^{n+1}_t in the storage
+    // type, u_g^n, (u_g*); reverse: two FP64 intensity cotangents and eight
+    // per-cell buffers
+    const size_t es = c->esize, per_step_i = order == 2 ? 4 : 2, per_step_c = order == 2 ? 2 : 1;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t bI = up(ni * es), bX = up(ni * 8), bC = up(nc * 8);
+    const size_t need = per_step_i * nsteps * bI + 2 * bX + (per_step_c * nsteps + 8) * bC;
     if (c->adj_bytes < need) {
         if (c->adj) cudaFree(c->adj);
         c->adj = nullptr; c->adj_bytes = 0;
         RT_CUDA_TRY(c, cudaMalloc(&c->adj, need));
         c->adj_bytes = need;
     }
-    double *p = c->adj;
-    auto take = [&](size_t n) { double *r = p; p += n; return r; };
-    std::vector<double *> In(nsteps), At(nsteps), Bs(nsteps), Ct(nsteps), un(nsteps), us(nsteps);
+    char *p = (char *)c->adj;
+    auto take = [&](size_t b) { char *r = p; p += b; return r; };
+    std::vector<void *> In(nsteps), At(nsteps), Bs(nsteps), Ct(nsteps);
+    std::vector<double *> un(nsteps), us(nsteps);
     for (int n = 0; n < nsteps; ++n) {
-        In[n] = take(ni);
-        if (order == 2) { At[n] = take(ni); Bs[n] = take(ni); }
-        Ct[n] = take(ni);
+        In[n] = take(bI);
+        if (order == 2) { At[n] = take(bI); Bs[n] = take(bI); }
+        Ct[n] = take(bI);
     }
-    for (int n = 0; n < nsteps; ++n) { un[n] = take(nc); if (order == 2) us[n] = take(nc); }
-    double *X1 = take(ni), *X2 = take(ni);
-    double *ub = take(nc), *ubn = take(nc), *ubs = take(nc), *an = take(nc), *as_ = take(nc);
-    double *ug_scr = take(nc), *a_scr = take(nc), *u_next = take(nc);
+    for (int n = 0; n < nsteps; ++n) { un[n] = (double *)take(bC); if (order == 2) us[n] = (double *)take(bC); }
+    double *X1 = (double *)take(bX), *X2 = (double *)take(bX);
+    double *ub = (double *)take(bC), *ubn = (double *)take(bC), *ubs = (double *)take(bC), *an = (double *)take(bC);
+    double *as_ = (double *)take(bC), *ug_scr = (double *)take(bC), *a_scr = (double *)take(bC);
+    double *u_next = (double *)take(bC);
+    void *I_last = X2;   // the recompute's final state is never read: any buffer of ni * es bytes
 
     // 1. forward recompute from the checkpoint
-    RT_CUDA_TRY(c, cudaMemcpyAsync(In[0], I_ckpt, ni * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(In[0], I_ckpt, ni * es, cudaMemcpyDeviceToDevice, c->stream));
     RT_CUDA_TRY(c, cudaMemcpyAsync(un[0], ug_ckpt, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     rt_status st;
     for (int n = 0; n < nsteps; ++n) {
-        double *Inext = n + 1 < nsteps ? In[n + 1] : X1;
+        void *Inext = n + 1 < nsteps ? In[n + 1] : I_last;
         double *unext = n + 1 < nsteps ? un[n + 1] : u_next;
         if ((st = rt_launch_alpha(c, un[n], an)) != RT_OK) return st;
         if (order == 1) {

@@ -41,7 +41,7 @@ class _Rollout(torch.autograd.Function):
         uN = torch.empty(nc, dtype=torch.float64, device=dev)
         st.get_intensity(IN)
         st.get_ugas(uN)
-        ctx.st, ctx.fluid, ctx.dt, ctx.segs = st, fluid, dt, segs
+        ctx.st, ctx.fluid, ctx.dt, ctx.segs, ctx.I_dtype = st, fluid, dt, segs, I0.dtype
         ctx.ck_I, ctx.ck_u, ctx.kappa, ctx.eta, ctx.ug0 = ck_I, ck_u, kappa, eta, ug0.detach()
         return IN, uN
 
@@ -61,7 +61,7 @@ class _Rollout(torch.autograd.Function):
             st.step_adjoint(ctx.ck_I[idx], ctx.ck_u[idx], ctx.dt, ctx.segs[idx], Ib, ub, Ib_in, ub_in, kb, eb)
             Ib, Ib_in = Ib_in, Ib
             ub, ub_in = ub_in, ub
-        return Ib, ub, kb, eb, None, None, None, None, None
+        return Ib.to(ctx.I_dtype), ub, kb, eb, None, None, None, None, None
 
 
 def rollout(st: RadiationStep, fluid: dict, I0, ug0, kappa, eta, nsteps: int, dt: float = None,
@@ -69,7 +69,9 @@ def rollout(st: RadiationStep, fluid: dict, I0, ug0, kappa, eta, nsteps: int, dt
     """(I_N, u_g,N) after nsteps steps of size dt (None: the cfl bound with
     cfl 0.4) from (I0, ug0), differentiable in I0, ug0, kappa and eta.
 
-    ``st`` is a RadiationStep with FP64 intensities on flat geometry;
+    ``st`` is a RadiationStep on flat geometry with FP64 intensities (an FP64
+    reverse pass) or FP32 intensities (FP32 per-element arithmetic with FP64
+    per-cell sums and FP64 cotangents);
     ``fluid`` holds the device tensors rho, ucon and alpha_s (float64).  The
     library works on the step's stream, so that stream must be the current
     one (the backward runs on the forward's stream).

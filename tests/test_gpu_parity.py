@@ -159,3 +159,36 @@ def test_kerr_fp32_against_fp64_oracle():
     ref = run_oracle(cfg, f, dt, 5)
     out = run_gpu(cfg, f, dt, 5, "fp32")
     assert rel_err(out["I"], ref["I"], 1e-3).max() < 1e-4
+
+
+def test_full_box_fp32_sampled_against_oracle():
+    """The bench's workload and launch configuration (128^3 x 162, FP32
+    storage, two steps) against the oracle on sampled sub-boxes.  A cell after
+    one step depends on cells at most 4 away along each axis (2 per stage), so
+    the oracle run on a 24^3 window with outflow edges is exact on the window's
+    central 8^3 after two steps; windows that wrap the periodic boundary check
+    the CUDA path's periodic indexing at full size."""
+    N, nsteps, n, core = 128, 2, 24, 8
+    cfg, f = W.flat3d(N=N, n_geo=4, intensity_dtype=np.float32)
+    dt = oracle.Oracle(dict(cfg, nx=(8, 8, 8))).cfl_dt(0.4)
+    out = run_gpu(cfg, f, dt, nsteps, "fp32")
+    assert out["fails"] == 0
+    nd = f["I"].shape[1]
+    I3 = out["I"].reshape(N, N, N, nd)
+    u3 = out["ug"].reshape(N, N, N)
+    rng = np.random.default_rng(11)
+    starts = [(N - n // 2, N - n // 2, N - n // 2)] + [tuple(int(x) for x in rng.integers(0, N, 3)) for _ in range(3)]
+    for st in starts:
+        ii = [(st[a] + np.arange(n)) % N for a in range(3)]
+        sel = np.ix_(ii[2], ii[1], ii[0])
+        sub = lambda a: np.ascontiguousarray(a.reshape(N, N, N, *a.shape[1:])[sel].reshape(n ** 3, *a.shape[1:]))
+        fs = {k: sub(np.asarray(f[k])) for k in ("rho", "ug", "ucon", "kappa", "alpha_s", "eta")}
+        fs["I"] = sub(np.asarray(f["I"], dtype=np.float64))
+        cs = W.base_config(4, (n, n, n), (0, 0, 0), (1.0 / N,) * 3, (("outflow", "outflow"),) * 3)
+        ref = run_oracle(cs, fs, dt, nsteps)
+        c = slice(core, n - core)
+        Ir = ref["I"].reshape(n, n, n, nd)[c, c, c]
+        Ig = I3[sel][c, c, c]
+        assert rel_err(Ig, Ir, 1e-3).max() < 1e-4, st
+        ur = ref["ug"].reshape(n, n, n)[c, c, c]
+        assert rel_err(u3[sel][c, c, c], ur).max() < 1e-4, st
