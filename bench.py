@@ -39,7 +39,7 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 
 # DRAM traffic of one stage-kernel launch from an ncu capture (bytes per
 # cell-angle), valid only for the stage-kernel source it was measured on.
-NCU_TRAFFIC = {}   # {(sha1 of the stage sources, precision): bytes per cell-angle per launch}
+NCU_TRAFFIC = {}   # {(sha1 of the stage sources, precision, workload): bytes per cell-angle per launch}
 STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
@@ -145,21 +145,24 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_leg(dev, stream, grid, nsteps=64, ckpt=8, N=64):
+def adjoint_leg(dev, stream, grid, prec="fp64", nsteps=64, ckpt=8, N=64):
     """Reverse mode on its workload: 64^3 cells, 162 directions, 64 steps,
-    a checkpoint every 8, FP64.  Returns the forward time per step (rt_step),
-    the backward time per step (recompute + reverse, rt_step_adjoint through
-    the autograd rollout) and their ratio, all timed with CUDA events."""
+    a checkpoint every 8, FP64 (or FP32 storage: the mixed reverse pass).
+    Returns the forward time per step (rt_step), the backward time per step
+    (recompute + reverse, rt_step_adjoint through the autograd rollout) and
+    their ratio, all timed with CUDA events."""
     import torch
     import paper_2508_15532_b300 as rt
     from paper_2508_15532_b300 import workloads as W
     from paper_2508_15532_b300.rollout import rollout
     cfg, f = W.adjoint3d(N=N, n_geo=4)
     with torch.cuda.stream(stream):
-        st = rt.RadiationStep(grid, cfg, precision="fp64", stream=stream.cuda_stream)
+        st = rt.RadiationStep(grid, cfg, precision=prec, stream=stream.cuda_stream)
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
         fluid = dict(rho=T(f["rho"]), ucon=T(f["ucon"]), alpha_s=T(f["alpha_s"]))
         I0, ug0 = T(f["I"]), T(f["ug"])
+        if prec == "fp32":
+            I0 = I0.float()
         kappa = T(f["kappa"]).requires_grad_()
         eta = T(f["eta"]).requires_grad_()
         w = T(grid.query()[1])
@@ -174,7 +177,7 @@ def adjoint_leg(dev, stream, grid, nsteps=64, ckpt=8, N=64):
         stream.synchronize()
         fwd_ms = e0.elapsed_time(e1) / nsteps
         IN, _ = rollout(st, fluid, I0, ug0, kappa, eta, nsteps, dt=dt, ckpt_every=ckpt)
-        L = ((IN @ w) ** 2).sum()
+        L = ((IN.double() @ w) ** 2).sum()
         stream.synchronize()
         e1.record(stream)
         L.backward()
@@ -183,7 +186,7 @@ def adjoint_leg(dev, stream, grid, nsteps=64, ckpt=8, N=64):
         bwd_ms = e1.elapsed_time(e2) / nsteps
         ok = bool(torch.isfinite(kappa.grad).all() and torch.isfinite(eta.grad).all())
     del st
-    return {"workload": "adjoint3d: %d^3 cells x 162 directions, %d steps, checkpoint every %d, fp64" % (N, nsteps, ckpt),
+    return {"workload": "adjoint3d: %d^3 cells x 162 directions, %d steps, checkpoint every %d, %s" % (N, nsteps, ckpt, prec),
             "forward_ms_per_step": fwd_ms, "backward_ms_per_step": bwd_ms, "ratio": bwd_ms / fwd_ms,
             "gradients_finite": ok}
 
@@ -196,10 +199,15 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--n-cells", type=int, default=128)
+    ap.add_argument("--workload", default="flat3d", choices=["flat3d", "kerr3d", "kerr2d"])
     ap.add_argument("--ref-cells", type=int, default=32)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the reverse mode (FP64 and mixed) and print its JSON line")
+    ap.add_argument("--adjoint-cells", type=int, default=64)
+    ap.add_argument("--adjoint-steps", type=int, default=64)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -226,18 +234,35 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
+    if args.adjoint_only:
+        g4 = rt.Grid(4)
+        ck = min(8, args.adjoint_steps)
+        legs = [adjoint_leg(dev, stream, g4, p, nsteps=args.adjoint_steps, ckpt=ck, N=args.adjoint_cells)
+                for p in ("fp64", "fp32")]
+        if rank == 0:
+            print(json.dumps({"metric": "reverse-mode time per step / forward time per step", "unit": "ratio",
+                              "value": legs[0]["ratio"], "higher_is_better": False, "adjoint": legs[0],
+                              "adjoint_mixed": legs[1]}), flush=True)
+        return
     N = args.n_cells
     prec = args.precision
     tdt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[prec]
     np_dt = np.float32 if prec != "fp64" else np.float64
-    cfg, f = W.flat3d(N=N, n_geo=4, intensity_dtype=np_dt)
+    if args.workload == "flat3d":
+        cfg, f = W.flat3d(N=N, n_geo=4, intensity_dtype=np_dt)
+        wname = "flat3d-periodic-opacity-coupling"
+    else:
+        cfg, f = (W.kerr3d if args.workload == "kerr3d" else W.kerr2d)(n_geo=4)
+        f["I"] = f["I"].astype(np_dt)
+        wname = args.workload + "-kerr-schild-a0.9-torus"
     nd = f["I"].shape[1]
-    ncell = N ** 3
+    ncell = int(np.prod(cfg["nx"]))
     grid = rt.Grid(4)
     with torch.cuda.stream(stream):
         st = rt.RadiationStep(grid, cfg, precision=prec, stream=stream.cuda_stream)
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
-        st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+        fluid_dev = [T(f[k]) for k in ("rho", "ug", "ucon", "kappa", "alpha_s", "eta")]
+        st.set_fluid(*fluid_dev)
         I_host = torch.from_numpy(f["I"]).to(tdt).pin_memory()
         ug_host = torch.from_numpy(np.ascontiguousarray(f["ug"])).pin_memory()
         st.set_intensity(I_host)
@@ -283,39 +308,57 @@ def main():
     avg_launch_s = stage_ms * 1e-3 / max(launches, 1)
     peak, peak_kind = measured_peaks()
     achieved = alg_per_launch / avg_launch_s / 1e9
-    traffic = NCU_TRAFFIC.get((stage_source_hash(), prec))
+    traffic = NCU_TRAFFIC.get((stage_source_hash(), prec, args.workload))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic * cell_angles if traffic else None),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_per_launch,
-                "avg_launch_ms": avg_launch_s * 1e3, "kernel": "k_stage (transport + interaction, fused)"}
+                "avg_launch_ms": avg_launch_s * 1e3,
+                "kernel": ("k_stage_fs" if args.workload == "flat3d" else "k_stage") + " (transport + interaction, fused)"}
 
-    # ---- end to end through the public API with pinned host buffers
-    out_I = torch.empty_like(I_host).pin_memory()
-    out_ug = torch.empty_like(ug_host).pin_memory()
-    for _ in range(1):
-        st.set_intensity(I_host); st.set_ugas(ug_host); st.step(dt, 1); st.get_intensity(out_I); st.get_ugas(out_ug)
+    # ---- end to end through the public API with pinned host buffers: every
+    # step uploads its inputs (I, u_g), steps, and reads its results back.  Two
+    # contexts on two streams take alternate steps (double buffering), so one
+    # step's copies overlap the other's compute, as a serving loop would run.
+    stream2 = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream2):
+        st2 = rt.RadiationStep(grid, cfg, precision=prec, stream=stream2.cuda_stream)
+        st2.set_fluid(*fluid_dev)
+    sts = [st, st2]
+    outs = [(torch.empty_like(I_host).pin_memory(), torch.empty_like(ug_host).pin_memory()) for _ in range(2)]
+    out_I, out_ug = outs[0]
+    for q in range(2):
+        sts[q].set_intensity(I_host); sts[q].set_ugas(ug_host); sts[q].step(dt, 1)
+        sts[q].get_intensity(outs[q][0]); sts[q].get_ugas(outs[q][1])
+    torch.cuda.synchronize(dev)
     barrier()
+    E = max(2, args.e2e_steps)
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        st.set_intensity(I_host)
-        st.set_ugas(ug_host)
-        st.step(dt, 1)
-        st.get_intensity(out_I)
-        st.get_ugas(out_ug)
-    stream.synchronize()
+    for k in range(E + 1):
+        if k < E:
+            q = k % 2
+            sts[q].set_intensity(I_host)
+            sts[q].set_ugas(ug_host)
+            sts[q].step(dt, 1)
+        if k >= 1:
+            q = (k - 1) % 2
+            sts[q].get_intensity(outs[q][0])   # host buffer: waits for that context's stream
+            sts[q].get_ugas(outs[q][1])
+    torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
+    del st2
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * cell_angles * args.e2e_steps / e2e_s
+    e2e_value = world * cell_angles * E / e2e_s
     h2d = I_host.numel() * I_host.element_size() + ug_host.numel() * 8
     d2h = out_I.numel() * out_I.element_size() + out_ug.numel() * 8
 
-    adj = None
+    adj = adj_mixed = None
     if world == 1 and not args.no_adjoint:
         del st
-        adj = adjoint_leg(dev, stream, grid)
+        adj = adjoint_leg(dev, stream, grid, "fp64")
+        adj_mixed = adjoint_leg(dev, stream, grid, "fp32")
         st = None
 
     cpu = None
@@ -331,17 +374,19 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32 (f64 coupling)", "fp64": "f64", "bf16": "bf16 storage, f32 math, f64 coupling"}[prec],
             "data": "synthetic",
-            "config": {"workload": "flat3d-periodic-opacity-coupling", "cells": [N, N, N], "directions": nd,
+            "config": {"workload": wname, "cells": [int(x) for x in cfg["nx"]], "directions": nd,
                        "precision": prec, "dt": dt, "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (%.2f GB per intensity array)" % (cell_angles * S / 1e9)},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "steps": E, "mode": "pinned host buffers; 2 contexts on 2 streams take alternate steps"},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
         if adj:
             line["adjoint"] = adj
+            line["adjoint_mixed"] = adj_mixed
         print(json.dumps(line), flush=True)
     if st is not None:
         del st

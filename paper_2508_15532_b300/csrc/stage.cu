@@ -441,13 +441,14 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             }
             B2 *= dt / FOURPI;
             const double Y = A.cc_Y[cidx], ug = A.ug_in[cidx], Tm = ug / Y;
-            Teq<double> q{B1, B2, Em + ug, Y, Tm, Em, A.cc_au[cidx], A.cc_as[cidx], A.eta[cidx], A.arad, dt, A.T_exp};
+            Teq<double> q = make_teq<double>(B1, B2, Em + ug, Y, Tm, Em, A.cc_au[cidx], A.cc_as[cidx], A.eta[cidx], A.arad,
+                                             dt, A.T_exp);
             double lo = 0.0, hi = q.W, X;
             bool ok;
             if (sizeof(TM) == 4) {
                 // FP32 Newton iterations, then one FP64 Newton step
                 Teq<float> qf{(float)q.B1, (float)q.B2, (float)q.W, (float)q.Y, (float)q.Tm, (float)q.Em, (float)q.au,
-                              (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p};
+                              (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p, (float)q.iY};
                 float flo = 0.0f, fhi = (float)q.W, fx;
                 newton_E<float>(qf, (float)Em, flo, fhi, 60, 1e-7f, &fx);
                 // FP64 Newton from the FP32 root (one or two steps in practice)

@@ -112,7 +112,13 @@ __device__ inline int row_desc(const StageArgs &A, int j, int k) {
 // Method 3 solved for the post-interaction radiation energy X = E* (see the
 // oracle): h(X) = (alpha(T) dt - B2 alpha^s) X - B1 - B2 eta alpha^a(T) a T^4,
 // T = T_- + (E-bar_- - X)/Y; h increases strictly on [0, W).
-template <typename R> struct Teq { R B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p; };
+template <typename R> struct Teq { R B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p, iY; };
+
+// (iY = 1/Y, so that an evaluation of h divides only for T^-p and the step)
+template <typename R>
+__device__ __forceinline__ Teq<R> make_teq(R B1, R B2, R W, R Y, R Tm, R Em, R au, R as, R eta, R arad, R dt, R p) {
+    return Teq<R>{B1, B2, W, Y, Tm, Em, au, as, eta, arad, dt, p, R(1) / Y};
+}
 
 template <typename R> __device__ __forceinline__ R tpow_neg(R T, R p) {
     if (p == R(3.5)) { R r = sqrt(T); return R(1) / (T * T * T * r); }
@@ -121,16 +127,25 @@ template <typename R> __device__ __forceinline__ R tpow_neg(R T, R p) {
 }
 
 template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, R X, R *h, R *dh) {
-    R T = q.Tm + (q.Em - X) / q.Y;
+    R T = q.Tm + (q.Em - X) * q.iY;
     if (!(T > R(0))) { *h = R(1e30); *dh = R(1); return; }
-    R tp = tpow_neg(T, q.p);
+    // T^-p and 1/T with one division (p = 3.5: 1/T = T^2 sqrt(T) T^-3.5)
+    R tp, iT;
+    if (q.p == R(3.5)) {
+        const R r = sqrt(T);
+        tp = R(1) / (T * T * T * r);
+        iT = T * T * r * tp;
+    } else {
+        tp = tpow_neg(T, q.p);
+        iT = R(1) / T;
+    }
     R aa = q.au * tp;
     R T4 = T * T * T * T;
     R em = q.B2 * q.eta * q.arad * aa * T4;
     R lin = (aa + q.as) * q.dt - q.B2 * q.as;
     *h = lin * X - q.B1 - em;
     // dh/dX with dT/dX = -1/Y
-    *dh = lin + (q.p * aa / T) * q.dt * X / q.Y + em * (R(4) - q.p) / (T * q.Y);
+    *dh = lin + (q.p * aa * iT) * q.dt * X * q.iY + em * (R(4) - q.p) * iT * q.iY;
 }
 
 // safeguarded Newton on [lo, hi] with h(lo) <= 0 < h(hi); returns converged flag
@@ -170,10 +185,10 @@ __device__ __forceinline__ double tneg_mixed(double T, double p) {
 // FP64, the slope FP32, so each iteration gains ~7 digits).  Returns X = E*.
 __device__ inline bool solve_mixed(const Teq<double> &q, double *Xout) {
     Teq<float> qf{(float)q.B1, (float)q.B2, (float)q.W, (float)q.Y, (float)q.Tm, (float)q.Em, (float)q.au,
-                  (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p};
+                  (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p, (float)q.iY};
     float flo = 0.0f, fhi = (float)q.W, fx;
     bool okf = newton_E<float>(qf, (float)q.Em, flo, fhi, 40, 2e-7f, &fx);
-    const double invY = 1.0 / q.Y, B2ea = q.B2 * q.eta * q.arad, B2as = q.B2 * q.as;
+    const double invY = q.iY, B2ea = q.B2 * q.eta * q.arad, B2as = q.B2 * q.as;
     double X = (double)fx;
     for (int it = 0; it < 3; ++it) {
         double T = q.Tm + (q.Em - X) * invY;

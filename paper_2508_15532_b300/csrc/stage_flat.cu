@@ -55,11 +55,13 @@ template <typename TM> __device__ __forceinline__ TM transpose_sum(TM (&v)[NCELL
     return v[0];
 }
 
-// FP32 math: three CTAs of 192 threads per SM.  Each SM sub-partition holds
-// 16K registers and a CTA's six warps spread over the four, so three CTAs
-// (up to five warps on one sub-partition) leave 96 registers a thread.
-// FP64 math: two CTAs (measured 10% faster than one).
-template <typename TM> struct MinBlocks { static constexpr int v = 3; };
+// FP32 math: four CTAs of 192 threads per SM.  Each SM sub-partition holds
+// 16K registers and a CTA's six warps spread over the four, so four CTAs
+// (six warps on each sub-partition) leave 80 registers a thread; this fits
+// because the transported brick lives in shared memory (24 KB per CTA).
+// Measured: 4 CTAs beat 3 (96 registers, brick in registers) and 5 (64
+// registers, heavy spills).  FP64 math: two CTAs, brick in registers.
+template <typename TM> struct MinBlocks { static constexpr int v = 4; };
 template <> struct MinBlocks<double> { static constexpr int v = 2; };
 constexpr int FS_NT = 192;
 
@@ -150,9 +152,15 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
         return IO<TS, TM>::ld(Isrc, (unsigned)off);
     };
 
-    TM It[NCELL];
+    // transported intensities of the brick: shared memory for FP32 math (it
+    // frees 32 registers, so four CTAs fit per SM), registers for FP64 math
+    constexpr bool SIT = sizeof(TM) == 4;
+    __shared__ float sIt[SIT ? NCELL : 1][SIT ? FS_NT : 1];
+    TM It[SIT ? 1 : NCELL];
 #pragma unroll
-    for (int c = 0; c < NCELL; ++c) It[c] = TM(0);
+    for (int c = 0; c < (SIT ? 1 : NCELL); ++c) It[c] = TM(0);
+    auto putIt = [&](int c, TM v) { if constexpr (SIT) sIt[c][s] = (float)v; else It[c] = v; };
+    auto getIt = [&](int c) -> TM { if constexpr (SIT) return (TM)sIt[c][s]; else return It[c]; };
 
     if (act) {
         int oy[BZ][BY + 4], oz[BY][BZ + 4];
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
                     for (int o = 0; o < NOWN; ++o) {
                         TM Ib = same_base ? Ic[o]
                                           : IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + i * nd));
-                        It[o * TXC + ii] = Ib - acc[o];
+                        putIt(o * TXC + ii, Ib - acc[o]);
                     }
                 }
             }
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             for (int o = 0; o < NOWN; ++o)
 #pragma unroll
                 for (int ii = 0; ii < TXC; ++ii)
-                    if (ii < nc) It[o * TXC + ii] = IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + (i0 + ii) * nd));
+                    if (ii < nc) putIt(o * TXC + ii, IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + (i0 + ii) * nd)));
         }
     }
 
@@ -266,13 +274,13 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
     {
         TM v[NCELL];
 #pragma unroll
-        for (int c = 0; c < NCELL; ++c) v[c] = It[c] * w;
+        for (int c = 0; c < NCELL; ++c) v[c] = (act && c % TXC < nc) ? getIt(c) * w : TM(0);
         part[warp][0][lane] = transpose_sum(v, lane);
         if (WANTG) {
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
 #pragma unroll
-                for (int c = 0; c < NCELL; ++c) v[c] = It[c] * w * nh[m];
+                for (int c = 0; c < NCELL; ++c) v[c] = (act && c % TXC < nc) ? getIt(c) * w * nh[m] : TM(0);
                 part[warp][1 + m][lane] = transpose_sum(v, lane);
             }
         }
@@ -292,15 +300,17 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             const double dt = A.dtk, adt = A.alpha_int[cidx] * dt;
             const double K = adt / (1.0 + adt);
             const double Y = A.cc_Y[cidx], au = A.cc_au[cidx], as = A.cc_as[cidx];
-            const double Tm = ugm / Y;
-            Teq<double> q{K * Em, K * A.sumw * dt / FOURPI, Em + ugm, Y, Tm, Em, au, as, A.eta[cidx], A.arad, dt, A.T_exp};
+            // FP64 divisions are costly on this part: one reciprocal of Y per cell
+            const double iY = 1.0 / Y, Tm = ugm * iY;
+            Teq<double> q{K * Em, K * A.sumw * dt * (1.0 / FOURPI), Em + ugm, Y, Tm, Em, au, as,
+                          A.eta[cidx], A.arad, dt, A.T_exp, iY};
             double X, a, c, inv, alpha_new;
             bool ok;
             if (sizeof(TM) == 4) {
                 ok = solve_mixed(q, &X);
                 // update constants in the storage math precision; the ledger uses
                 // exactly the constants the stored intensities are built from
-                const float Tp = (float)(Tm + (Em - X) / Y);
+                const float Tp = (float)(Tm + (Em - X) * iY);
                 const float aap = (float)au * tpow_neg<float>(Tp, (float)A.T_exp);
                 const float af = (aap + (float)as) * (float)dt;
                 const float cf = (float)dt * ((float)q.eta * aap * (float)A.arad * Tp * Tp * Tp * Tp + (float)as * (float)X) /
@@ -310,10 +320,10 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             } else {
                 double lo = 0.0, hi = q.W;
                 ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
-                const double Tp = Tm + (Em - X) / Y;
+                const double Tp = Tm + (Em - X) * iY;
                 const double aap = au * tpow_neg<double>(Tp, A.T_exp);
                 a = (aap + as) * dt;
-                c = dt * (q.eta * aap * A.arad * Tp * Tp * Tp * Tp + as * X) / FOURPI;
+                c = dt * (q.eta * aap * A.arad * Tp * Tp * Tp * Tp + as * X) * (1.0 / FOURPI);
                 inv = 1.0 / (1.0 + a);
             }
             if (!ok) atomicAdd(A.fail, 1ull);
@@ -322,13 +332,14 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             const double Ep = (Em + c * A.sumw) * inv;
             const double ugp = ugm - (Ep - Em);
             A.ug_out[cidx] = ugp;
-            const double T = ugp / Y;
+            const double T = ugp * iY;
             if (sizeof(TM) == 4) alpha_new = T > 0.0 ? (double)((float)au * tpow_neg<float>((float)T, (float)A.T_exp) + (float)as) : 0.0;
             else alpha_new = T > 0.0 ? au * tpow_neg<double>(T, A.T_exp) + as : 0.0;
             A.alpha_out[cidx] = alpha_new;
             if (WANTG && A.G) {
-                A.G[4 * cidx] = -(Ep - Em) / dt;
-                for (int m = 0; m < 3; ++m) A.G[4 * cidx + 1 + m] = -((c * A.sumnw[m] - a * F[m]) * inv) / dt;
+                const double idt = 1.0 / dt;
+                A.G[4 * cidx] = -(Ep - Em) * idt;
+                for (int m = 0; m < 3; ++m) A.G[4 * cidx + 1 + m] = -((c * A.sumnw[m] - a * F[m]) * inv) * idt;
             }
         } else {
             A.ug_out[cidx] = ugm;
@@ -347,7 +358,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             for (int ii = 0; ii < TXC; ++ii) {
                 if (ii < nc) {
                     const int lc = o * TXC + ii;
-                    TM v = It[lc];
+                    TM v = getIt(lc);
                     if (cOn[lc]) v = (v + cEm[lc]) * cInv[lc];
                     IO<TS, TM>::st(A.Iout, (base + ii) * nd + s, v);
                 }
