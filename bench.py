@@ -39,7 +39,10 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 
 # DRAM traffic of one stage-kernel launch from an ncu capture (bytes per
 # cell-angle), valid only for the stage-kernel source it was measured on.
-NCU_TRAFFIC = {}   # {(sha1 of the stage sources, precision, workload): bytes per cell-angle per launch}
+# DRAM bytes (read + write) per cell-angle per stage launch, averaged over the
+# two launches of a step, from an ncu capture of the 64^3 box; traffic scales
+# with the cells (each cell is read once per source array and written once)
+NCU_TRAFFIC = {("4b8d66fa2690", "fp32", "flat3d"): 10.03}   # {(sha1 of the stage sources, precision, workload): B}
 STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
