@@ -182,7 +182,8 @@ __device__ __forceinline__ double tneg_mixed(double T, double p) {
 
 // Temperature solve of the mixed (FP32-storage) path: FP32 Newton from E-bar_-,
 // then FP64 residual iterations X <- X - h_64(X) / h'_32(X) (the residual is
-// FP64, the slope FP32, so each iteration gains ~7 digits).  Returns X = E*.
+// FP64, the slope FP32, so each iteration gains ~7 digits; one suffices after
+// a converged FP32 Newton, up to three otherwise).  Returns X = E*.
 __device__ inline bool solve_mixed(const Teq<double> &q, double *Xout) {
     Teq<float> qf{(float)q.B1, (float)q.B2, (float)q.W, (float)q.Y, (float)q.Tm, (float)q.Em, (float)q.au,
                   (float)q.as, (float)q.eta, (float)q.arad, (float)q.dt, (float)q.p, (float)q.iY};
@@ -202,7 +203,9 @@ __device__ inline bool solve_mixed(const Teq<double> &q, double *Xout) {
         float dh = lin + (qf.p * aaf / Tf) * qf.dt * Xf / qf.Y + emf * (4.0f - qf.p) / (Tf * qf.Y);
         double d = h * (double)(1.0f / dh);
         X -= d;
-        if (fabs(d) <= 1e-15 * fabs(X)) break;
+        // each iteration multiplies the error by the slope's FP32 error (~1e-7):
+        // a correction below 1e-6 X leaves an error below ~1e-13 X
+        if (fabs(d) <= 1e-6 * fabs(X)) break;
     }
     *Xout = X;
     return okf && X >= 0.0 && X < q.W;
