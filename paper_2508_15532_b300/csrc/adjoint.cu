@@ -30,42 +30,46 @@ constexpr int NFACE = 9 * TXA + 3;
 struct SrcArgs {
     int ncell, nd, source;
     double dtk, sumw, T_exp, arad, rho_exp;
-    const double *w, *ug_in, *cc_au, *cc_as, *cc_Y, *eta, *rho;
+    const double *w, *ug_in, *cc_au, *cc_as, *cc_Y, *eta, *rho, *kap;
     const void *I;                           // storage type of the context
     const uint8_t *cc_on;
     void *I_out;                             // forward (storage type)
     double *ug_out;
-    const double *Ibo, *ubo;                 // reverse: cotangents of the outputs
-    double *Ibi, *ubi;                       // cotangents of I (written) and u_g entering (ub_acc: added)
+    const void *Ibo;                         // reverse: cotangent of the output intensities (type R)
+    const double *ubo;                       // cotangent of the output u_g
+    void *Ibi;                               // cotangent of I (written, type R)
+    double *ubi;                             // cotangent of u_g entering (ub_acc: added)
     int ub_acc;
     double *kb, *eb;                         // added
     unsigned long long *fail;
 };
 
+// rho^m = (kappa rho^m) / kappa, the derivative of alpha^a's prefactor in
+// kappa, without an FP64 pow where kappa is nonzero
+__device__ __forceinline__ double rho_m(double au, double kap, double rho, double m) {
+    return kap != 0.0 ? au / kap : pow(rho, m);
+}
+
 // 16 values per lane -> lane l (and l + 16) holds the warp sum of value l & 15
-__device__ __forceinline__ double tsum16(double (&v)[SC], int lane) {
+template <typename R> __device__ __forceinline__ R tsum16(R (&v)[SC], int lane) {
 #pragma unroll
     for (int n = 8; n >= 1; n >>= 1) {
         const bool hi = (lane & n) != 0;
 #pragma unroll
         for (int i = 0; i < n; ++i) {
-            double keep = hi ? v[i + n] : v[i];
-            double send = hi ? v[i] : v[i + n];
+            R keep = hi ? v[i + n] : v[i];
+            R send = hi ? v[i] : v[i + n];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, n);
         }
     }
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-// intensity of storage type TS as FP64, and back
-template <typename TS> __device__ __forceinline__ double ld64(const void *p, size_t i) {
-    return (double)__ldg((const TS *)p + i);
-}
-template <typename TS> __device__ __forceinline__ void st64(void *p, size_t i, double v) { ((TS *)p)[i] = (TS)v; }
-
 // REV = false: I_out = interaction(I), u_g out.  REV = true: the reverse.
-// The per-cell arithmetic is FP64 for every storage type TS.
-template <bool REV, typename TS>
+// R is the storage and per-element arithmetic type of intensities and their
+// cotangents (FP64, or FP32 for the mixed pass); warp partial sums are in R,
+// the sums over warps and the per-cell arithmetic in FP64.
+template <bool REV, typename R>
 __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     constexpr int NW = ADJ_NT / 32;
     __shared__ double part[NW][3][SC];
@@ -75,26 +79,27 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     const bool act = s < A.nd;
     const size_t c0 = (size_t)blockIdx.x * SC;
     const int nc = (int)min((size_t)SC, (size_t)A.ncell - c0);
-    const double w = act ? A.w[s] : 0.0;
-    double Iv[SC], Bv[SC], v[SC];
+    const R w = act ? (R)A.w[s] : R(0);
+    const R *Isrc = (const R *)A.I, *Bsrc = (const R *)A.Ibo;
+    R Iv[SC], Bv[SC], v[SC];
 #pragma unroll
-    for (int k = 0; k < SC; ++k) Iv[k] = (act && k < nc) ? ld64<TS>(A.I, (c0 + k) * A.nd + s) : 0.0;
+    for (int k = 0; k < SC; ++k) Iv[k] = (act && k < nc) ? __ldg(Isrc + (c0 + k) * A.nd + s) : R(0);
     if (REV) {
 #pragma unroll
-        for (int k = 0; k < SC; ++k) Bv[k] = (act && k < nc) ? A.Ibo[(c0 + k) * A.nd + s] : 0.0;
+        for (int k = 0; k < SC; ++k) Bv[k] = (act && k < nc) ? __ldg(Bsrc + (c0 + k) * A.nd + s) : R(0);
     }
 #pragma unroll
     for (int k = 0; k < SC; ++k) v[k] = Iv[k] * w;
-    double r0 = tsum16(v, lane);
-    if (lane < SC) part[warp][0][lane] = r0;
+    R r0 = tsum16<R>(v, lane);
+    if (lane < SC) part[warp][0][lane] = (double)r0;
     if (REV) {
 #pragma unroll
         for (int k = 0; k < SC; ++k) v[k] = Bv[k];
-        double r1 = tsum16(v, lane);
+        R r1 = tsum16<R>(v, lane);
 #pragma unroll
         for (int k = 0; k < SC; ++k) v[k] = Bv[k] * Iv[k];
-        double r2 = tsum16(v, lane);
-        if (lane < SC) { part[warp][1][lane] = r1; part[warp][2][lane] = r2; }
+        R r2 = tsum16<R>(v, lane);
+        if (lane < SC) { part[warp][1][lane] = (double)r1; part[warp][2][lane] = (double)r2; }
     }
     __syncthreads();
     if (warp == 0 && lane < SC) {
@@ -103,8 +108,10 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
         if (lane < nc) {
             const size_t c = c0 + lane;
             const double Y = A.cc_Y[c], ugm = A.ug_in[c], au = A.cc_au[c], as = A.cc_as[c];
-            const double Tm = Y > 0.0 ? ugm / Y : 0.0;
-            const double am = (A.cc_on[c] && Tm > 0.0) ? au * tpow_neg<double>(Tm, A.T_exp) + as : 0.0;
+            // FP64 divisions are costly on this part: reciprocals once per cell
+            const double iY = Y > 0.0 ? 1.0 / Y : 0.0, Tm = ugm * iY;
+            const double tm = Tm > 0.0 ? tpow_neg<double>(Tm, A.T_exp) : 0.0;
+            const double am = (A.cc_on[c] && Tm > 0.0) ? au * tm + as : 0.0;
             on = A.source && A.cc_on[c] && am > 0.0 && Y > 0.0 && ugm > 0.0;
             const double ub = (REV && A.ubo) ? A.ubo[c] : 0.0;
             if (on) {
@@ -112,17 +119,20 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
                 for (int g = 0; g < NW; ++g) Em += part[g][0][lane];
                 if (REV)
                     for (int g = 0; g < NW; ++g) { P += part[g][1][lane]; Q += part[g][2][lane]; }
-                const double dt = A.dtk, adt = am * dt, K = adt / (1.0 + adt), S = A.sumw;
+                constexpr double i4pi = 1.0 / FOURPI;
+                const double dt = A.dtk, adt = am * dt, i1a = 1.0 / (1.0 + adt), K = adt * i1a, S = A.sumw;
                 const double eta = A.eta[c], p = A.T_exp, ar = A.arad;
-                Teq<double> q{K * Em, K * S * dt / FOURPI, Em + ugm, Y, Tm, Em, au, as, eta, ar, dt, p};
+                Teq<double> q{K * Em, K * S * dt * i4pi, Em + ugm, Y, Tm, Em, au, as, eta, ar, dt, p, iY};
                 double X, lo = 0.0, hi = q.W;
-                bool ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
+                bool ok;
+                if constexpr (sizeof(R) == 4) ok = solve_mixed(q, &X);   // as the FP32 forward solves it
+                else ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
                 if (!ok && A.fail) atomicAdd(A.fail, 1ull);
-                const double Tp = Tm + (Em - X) / Y;
+                const double Tp = Tm + (Em - X) * iY;
                 const double tp = tpow_neg<double>(Tp, p), aap = au * tp;
                 const double Tp4 = Tp * Tp * Tp * Tp;
                 const double a = (aap + as) * dt;
-                const double cc = dt * (eta * aap * ar * Tp4 + as * X) / FOURPI;
+                const double cc = dt * (eta * aap * ar * Tp4 + as * X) * i4pi;
                 const double inv = 1.0 / (1.0 + a);
                 if (!REV) {
                     const double Ep = (Em + cc * S) * inv;
@@ -135,34 +145,36 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
                     const double ccb = sIpb * inv;
                     const double Ab = -(sIpbI + cc * sIpb) * inv * inv;
                     double aapb = Ab * dt;
-                    double etab = ccb * dt * aap * ar * Tp4 / FOURPI;
-                    aapb += ccb * dt * eta * ar * Tp4 / FOURPI;
-                    double Tpb = ccb * dt * eta * aap * ar * 4.0 * Tp * Tp * Tp / FOURPI;
-                    double Xb = ccb * dt * as / FOURPI;
+                    // 1/Tp without a division for p = 3.5: Tp^2 sqrt(Tp) Tp^-3.5
+                    const double iTpx = p == 3.5 ? Tp * Tp * sqrt(Tp) * tp : 1.0 / Tp;
+                    const double ccbd = ccb * dt * i4pi;
+                    double etab = ccbd * aap * ar * Tp4;
+                    aapb += ccbd * eta * ar * Tp4;
+                    double Tpb = ccbd * eta * aap * ar * 4.0 * Tp * Tp * Tp;
+                    double Xb = ccbd * as;
                     double aub = aapb * tp;
-                    Tpb += aapb * (-p) * aap / Tp;
-                    double Tmb = Tpb, Emb = ub + Tpb / Y;
-                    Xb -= Tpb / Y;
+                    Tpb += aapb * (-p) * aap * iTpx;
+                    double Tmb = Tpb, Emb = ub + Tpb * iY;
+                    Xb -= Tpb * iY;
                     // root of h(X; B1, B2, T_-, E_-, au, eta) = 0
                     const double lin = (aap + as) * dt - q.B2 * as;
-                    const double hT = -p * aap / Tp * dt * X - q.B2 * eta * ar * (4.0 - p) * aap * Tp * Tp * Tp;
-                    const double hX = lin - hT / Y;
+                    const double hT = -p * aap * iTpx * dt * X - q.B2 * eta * ar * (4.0 - p) * aap * Tp * Tp * Tp;
+                    const double hX = lin - hT * iY;
                     const double lam = -Xb / hX;
                     const double B1b = -lam;
                     const double B2b = lam * (-as * X - eta * ar * aap * Tp4);
                     Tmb += lam * hT;
-                    Emb += lam * hT / Y;
+                    Emb += lam * hT * iY;
                     aub += lam * (tp * dt * X - q.B2 * eta * ar * tp * Tp4);
                     etab += lam * (-q.B2 * ar * aap * Tp4);
-                    const double Kb = B2b * S * dt / FOURPI + B1b * Em;
+                    const double Kb = B2b * S * dt * i4pi + B1b * Em;
                     Emb += B1b * K;
-                    const double amb = Kb * dt / ((1.0 + adt) * (1.0 + adt));
-                    const double tm = tpow_neg<double>(Tm, p);
+                    const double amb = Kb * dt * i1a * i1a;
                     aub += amb * tm;
-                    Tmb += amb * (-p) * au * tm / Tm;
-                    const double ugb = ub + Tmb / Y;
+                    Tmb += amb * (-p) * au * tm * (p == 3.5 ? Tm * Tm * tm * sqrt(Tm) : 1.0 / Tm);
+                    const double ugb = ub + Tmb * iY;
                     A.ubi[c] = A.ub_acc ? A.ubi[c] + ugb : ugb;
-                    A.kb[c] += aub * pow(A.rho[c], A.rho_exp);
+                    A.kb[c] += aub * rho_m(au, A.kap[c], A.rho[c], A.rho_exp);
                     A.eb[c] += etab;
                     a0 = inv; b0 = ub; cc0 = Emb;
                 }
@@ -179,8 +191,8 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     for (int k = 0; k < SC; ++k) {
         if (k >= nc) break;
         const size_t i = (c0 + k) * A.nd + s;
-        if (!REV) st64<TS>(A.I_out, i, sh_on[k] ? (Iv[k] + sh_a[k]) * sh_b[k] : Iv[k]);
-        else A.Ibi[i] = sh_on[k] ? (Bv[k] - sh_b[k] * w) * sh_a[k] + sh_c[k] * w : Bv[k];
+        if (!REV) ((R *)A.I_out)[i] = sh_on[k] ? (Iv[k] + (R)sh_a[k]) * (R)sh_b[k] : Iv[k];
+        else ((R *)A.Ibi)[i] = sh_on[k] ? (Bv[k] - (R)sh_b[k] * w) * (R)sh_a[k] + (R)sh_c[k] * w : Bv[k];
     }
 }
 
@@ -188,11 +200,13 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
 struct TrArgs {
     int nx[3], act[3], per[3], nd, limiter, tau_dt;
     double dx[3], abar, dtk, T_exp, rho_exp;
-    const double *dir, *alpha, *Ibo;
-    const void *I;                           // storage type of the context
-    double *out_src, *base_out;
+    double coef[3], hl[3];                   // dtk/dx_a, and d tau/d alpha of one side of an a-face
+    const double *dir, *alpha;
+    const void *I;                           // intensities (type R)
+    const void *Ibo;                         // cotangent of the stage output (type R)
+    void *out_src, *base_out;                // cotangents written (type R)
     int src_acc, add_base;
-    const double *ug, *cc_au, *cc_Y, *rho;
+    const double *ug, *cc_au, *cc_Y, *rho, *kap;
     const uint8_t *cc_on;
     double *ub, *kb;
     int ub_acc;
@@ -204,21 +218,22 @@ __device__ __forceinline__ int amap(int q, int n, int per) {
     return q < 0 ? 0 : n - 1;
 }
 
-// c1, c2, c3 of the face and their derivatives in tau
-__device__ void face_cd(double tau, double *fc) {
-    if (tau > 0.0) {
-        double F = -expm1(-tau * tau), G = -expm1(-tau * tau * tau * tau);
-        double f = sqrt(F) / tau, g = sqrt(G) / tau, e = exp(-tau), S = f + g;
-        double fp = exp(-tau * tau) / sqrt(F) - f / tau;
-        double gp = G > 0.0 ? 2.0 * tau * tau * exp(-tau * tau * tau * tau) / sqrt(G) - g / tau : 1.0;
-        double ep = -e, Sp = fp + gp;
+// c1, c2, c3 of the face and their derivatives in tau (in the pass's type)
+template <typename TM> __device__ void face_cd(TM tau, TM *fc) {
+    if (tau > TM(0)) {
+        TM t2 = tau * tau, t4 = t2 * t2;
+        TM F = -expm1(-t2), G = -expm1(-t4);
+        TM f = sqrt(F) / tau, g = sqrt(G) / tau, e = exp(-tau), S = f + g;
+        TM fp = exp(-t2) / sqrt(F) - f / tau;
+        TM gp = G > TM(0) ? TM(2) * t2 * exp(-t4) / sqrt(G) - g / tau : TM(1);
+        TM ep = -e, Sp = fp + gp, iS2 = TM(1) / (S * S);
         fc[0] = f * e / S; fc[1] = g * e / S; fc[2] = f * g / S;
-        fc[3] = ((fp * e + f * ep) * S - f * e * Sp) / (S * S);
-        fc[4] = ((gp * e + g * ep) * S - g * e * Sp) / (S * S);
-        fc[5] = ((fp * g + f * gp) * S - f * g * Sp) / (S * S);
+        fc[3] = ((fp * e + f * ep) * S - f * e * Sp) * iS2;
+        fc[4] = ((gp * e + g * ep) * S - g * e * Sp) * iS2;
+        fc[5] = ((fp * g + f * gp) * S - f * g * Sp) * iS2;
     } else {
-        fc[0] = 1.0; fc[1] = 0.0; fc[2] = 0.0;
-        fc[3] = -2.0; fc[4] = 1.0; fc[5] = 1.0;
+        fc[0] = TM(1); fc[1] = TM(0); fc[2] = TM(0);
+        fc[3] = TM(-2); fc[4] = TM(1); fc[5] = TM(1);
     }
 }
 
@@ -279,8 +294,19 @@ __device__ __forceinline__ void axis_adj(const TM (&V)[7], const TM (&B)[5], uns
     }
 }
 
-// limited slope of a cell and its derivatives in (dl, dr)
+// limited slope of a cell and its derivatives in (dl, dr); the MC case with
+// selects only (same branches as lim_d: 0.5|dl+dr| wins when it is below
+// both 2|dl| and 2|dr|, 2|dr| wins over 2|dl| when strictly smaller)
 template <typename TM> __device__ __forceinline__ TM lim_dv(int kind, TM dl, TM dr, TM &gl, TM &gr) {
+    if (kind == RT_LIM_MC) {
+        const TM a2l = TM(2) * fabs(dl), a2r = TM(2) * fabs(dr), ah = TM(0.5) * fabs(dl + dr);
+        const bool ok = dl * dr > TM(0);
+        const TM mlr = fmin(a2l, a2r);
+        const bool w2 = ah < mlr, w1 = !w2 && a2r < a2l;
+        gl = ok ? (w2 ? TM(0.5) : (w1 ? TM(0) : TM(2))) : TM(0);
+        gr = ok ? (w2 ? TM(0.5) : (w1 ? TM(2) : TM(0))) : TM(0);
+        return ok ? copysign(fmin(mlr, ah), dl) : TM(0);
+    }
     lim_d<TM>(kind, dl, dr, gl, gr);
     return limiter<TM>(kind, dl, dr);
 }
@@ -334,9 +360,10 @@ __device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5],
     }
 }
 
-// TS: storage of the intensities, TM: per-element arithmetic (cotangents are
-// loaded and stored in FP64; per-cell sums are FP64)
-template <typename TS, typename TM>
+// TM: storage and per-element arithmetic of intensities and their cotangents
+// (FP64, or FP32 for the mixed pass); the opacity cotangents are summed over
+// warps and chained to u_g and kappa in FP64
+template <typename TM>
 __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
     constexpr int NW = ADJ_NT / 32;
     __shared__ TM fcs[NFACE][6];
@@ -366,103 +393,104 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
         } else {
             cl = cell(x0 + t, j, amap(k + m, nx2, A.per[2])); cr = cell(x0 + t, j, amap(k + m + 1, nx2, A.per[2]));
         }
-        double fd[6];
-        face_cd(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len(a), fd);
-        for (int q = 0; q < 6; ++q) fcs[f][q] = (TM)fd[q];
+        face_cd<TM>(TM(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len(a)), fcs[f]);
     }
     __syncthreads();
 
     TM n[3] = {TM(0), TM(0), TM(0)};
     if (act) for (int a = 0; a < 3; ++a) n[a] = (TM)A.dir[3 * s + a];
-    const TM coef[3] = {TM(A.dtk / A.dx[0]), TM(A.dtk / A.dx[1]), TM(A.dtk / A.dx[2])};
+    // (host-computed: FP64 divisions per thread would cost more than the cell's work)
+    const TM coef[3] = {TM(A.coef[0]), TM(A.coef[1]), TM(A.coef[2])};
+    const TM hl[3] = {TM(A.hl[0]), TM(A.hl[1]), TM(A.hl[2])};
     const int nd = A.nd;
-    auto ldI = [&](size_t c) -> TM { return act ? IO<TS, TM>::ld(A.I, c * nd + s) : TM(0); };
-    auto ldB = [&](size_t c) -> double { return act ? __ldg(A.Ibo + c * nd + s) : 0.0; };
-    double abt[TXA];
+    // 32-bit element offsets (the host checks n_cell * n_dir < 2^31)
+    const TM *Ip = (const TM *)A.I + s, *Bp = (const TM *)A.Ibo + s;
+    auto ldI = [&](int off) -> TM { return act ? __ldg(Ip + off) : TM(0); };
+    auto ldB = [&](int off) -> TM { return act ? __ldg(Bp + off) : TM(0); };
+    auto eo = [&](int i, int jj, int kk) -> int { return ((kk * nx1 + jj) * nx0 + i) * nd; };
+
+    // x2 / x3 stencils of the block's row (j, k): mapped indices, which
+    // offsets are this cell, and which cotangent positions exist
+    int ry[7], rz[7];   // element offsets of the stencil rows at x1 = 0
+    unsigned eqa[3] = {0u, 0u, 0u}, ina[3] = {0u, 0u, 0u};
 #pragma unroll
-    for (int t = 0; t < TXA; ++t) abt[t] = 0.0;
+    for (int o = -3; o <= 3; ++o) {
+        const int my = amap(j + o, nx1, A.per[1]), mz = amap(k + o, nx2, A.per[2]);
+        ry[o + 3] = eo(0, my, k);
+        rz[o + 3] = eo(0, j, mz);
+        eqa[1] |= (unsigned)(my == j) << (o + 3);
+        eqa[2] |= (unsigned)(mz == k) << (o + 3);
+        ina[1] |= (unsigned)(A.per[1] || (j + o >= 0 && j + o < nx1)) << (o + 3);
+        ina[2] |= (unsigned)(A.per[2] || (k + o >= 0 && k + o < nx2)) << (o + 3);
+    }
 
     // sliding x1 window
     TM WX[7], BX[5];
     if (A.act[0]) {
 #pragma unroll
-        for (int o = -3; o <= 3; ++o) WX[o + 3] = ldI(cell(amap(x0 + o, nx0, A.per[0]), j, k));
+        for (int o = -3; o <= 3; ++o) WX[o + 3] = ldI(eo(amap(x0 + o, nx0, A.per[0]), j, k));
 #pragma unroll
         for (int o = -2; o <= 2; ++o) {
             int q = x0 + o;
-            BX[o + 2] = (A.per[0] || (q >= 0 && q < nx0)) ? (TM)ldB(cell(amap(q, nx0, A.per[0]), j, k)) : TM(0);
+            BX[o + 2] = (A.per[0] || (q >= 0 && q < nx0)) ? ldB(eo(amap(q, nx0, A.per[0]), j, k)) : TM(0);
         }
     }
+#pragma unroll 1
+    for (int t = 0; t < nc; ++t) {
+        const int i = x0 + t;
+        const int ce = eo(i, j, k), ie = i * nd;
+        const TM Ic = ldI(ce), Bc = ldB(ce);
+        TM g = TM(0), abt = TM(0);
+        if (A.act[0]) {
+            unsigned eq = 0;
 #pragma unroll
-    for (int t = 0; t < TXA; ++t) {
-        if (t < nc) {
-            const int i = x0 + t;
-            const size_t c = cell(i, j, k);
-            const TM Ic = ldI(c);
-            const double Bc = ldB(c);
-            TM g = TM(0);
-            if (A.act[0]) {
-                unsigned eq = 0;
-                for (int o = -3; o <= 3; ++o) eq |= (amap(i + o, nx0, A.per[0]) == i) << (o + 3);
-                const TM *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
-                TM tb[2] = {TM(0), TM(0)};
-                if (eq == (1u << 3)) axis_adj_int<TM>(WX, BX, fc, n[0], coef[0], A.limiter, g, tb);
-                else axis_adj<TM>(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
-                const double h = A.abar * 0.5 * len(0);
-                abt[t] += h * ((double)tb[0] * (1 + ((eq >> 2) & 1)) + (double)tb[1] * (1 + ((eq >> 4) & 1)));
-            }
-            for (int a = 1; a < 3; ++a) {
-                if (!A.act[a]) continue;
-                const int na = a == 1 ? nx1 : nx2, pos = a == 1 ? j : k;
-                TM V[7], B[5];
-                unsigned eq = 0;
+            for (int o = -3; o <= 3; ++o) eq |= (unsigned)(amap(i + o, nx0, A.per[0]) == i) << (o + 3);
+            const TM *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
+            TM tb[2] = {TM(0), TM(0)};
+            if (eq == (1u << 3)) axis_adj_int<TM>(WX, BX, fc, n[0], coef[0], A.limiter, g, tb);
+            else axis_adj<TM>(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
+            abt += hl[0] * (tb[0] * TM(1 + ((eq >> 2) & 1)) + tb[1] * TM(1 + ((eq >> 4) & 1)));
+        }
 #pragma unroll
-                for (int o = -3; o <= 3; ++o) {
-                    const int mq = amap(pos + o, na, A.per[a]);
-                    eq |= (unsigned)(mq == pos) << (o + 3);
-                    V[o + 3] = o == 0 ? Ic : ldI(a == 1 ? cell(i, mq, k) : cell(i, j, mq));
-                }
+        for (int a = 1; a < 3; ++a) {
+            if (!A.act[a]) continue;
+            const int *rr = a == 1 ? ry : rz;
+            TM V[7], B[5];
 #pragma unroll
-                for (int o = -2; o <= 2; ++o) {
-                    const int q = pos + o, mq = amap(q, na, A.per[a]);
-                    B[o + 2] = o == 0 ? (TM)Bc
-                               : ((A.per[a] || (q >= 0 && q < na)) ? (TM)ldB(a == 1 ? cell(i, mq, k) : cell(i, j, mq)) : TM(0));
-                }
-                const int base = TXA + 3 + (a - 1) * 4 * TXA + 4 * t;
-                const TM *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
-                TM tb[2] = {TM(0), TM(0)};
-                if (eq == (1u << 3)) axis_adj_int<TM>(V, B, fc, n[a], coef[a], A.limiter, g, tb);
-                else axis_adj<TM>(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
-                const double h = A.abar * 0.5 * len(a);
-                abt[t] += h * ((double)tb[0] * (1 + ((eq >> 2) & 1)) + (double)tb[1] * (1 + ((eq >> 4) & 1)));
-            }
-            if (act) {
-                const size_t ix = c * nd + s;
-                double v = (double)g + (A.add_base ? Bc : 0.0);
-                if (A.src_acc) v += A.out_src[ix];
-                A.out_src[ix] = v;
-                if (A.base_out) A.base_out[ix] = Bc;
-            }
-            // slide the x1 window
-            if (A.act[0] && t + 1 < nc) {
+            for (int o = -3; o <= 3; ++o) V[o + 3] = o == 0 ? Ic : ldI(rr[o + 3] + ie);
 #pragma unroll
-                for (int o = 0; o < 6; ++o) WX[o] = WX[o + 1];
+            for (int o = -2; o <= 2; ++o)
+                B[o + 2] = o == 0 ? Bc : (((ina[a] >> (o + 3)) & 1u) ? ldB(rr[o + 3] + ie) : TM(0));
+            const int base = TXA + 3 + (a - 1) * 4 * TXA + 4 * t;
+            const TM *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
+            TM tb[2] = {TM(0), TM(0)};
+            const unsigned eq = eqa[a];
+            if (eq == (1u << 3)) axis_adj_int<TM>(V, B, fc, n[a], coef[a], A.limiter, g, tb);
+            else axis_adj<TM>(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
+            abt += hl[a] * (tb[0] * TM(1 + ((eq >> 2) & 1)) + tb[1] * TM(1 + ((eq >> 4) & 1)));
+        }
+        if (act) {
+            const size_t ix = (size_t)ce + s;
+            TM v = g + (A.add_base ? Bc : TM(0));
+            if (A.src_acc) v += ((TM *)A.out_src)[ix];
+            ((TM *)A.out_src)[ix] = v;
+            if (A.base_out) ((TM *)A.base_out)[ix] = Bc;
+        }
+        // opacity cotangent of this cell: warp sum now, block sum below
+        for (int o = 16; o > 0; o >>= 1) abt += __shfl_xor_sync(0xffffffffu, abt, o);
+        if (lane == 0) abw[warp][t] = (double)abt;
+        // slide the x1 window
+        if (A.act[0] && t + 1 < nc) {
 #pragma unroll
-                for (int o = 0; o < 4; ++o) BX[o] = BX[o + 1];
-                WX[6] = ldI(cell(amap(i + 4, nx0, A.per[0]), j, k));
-                const int q = i + 3;
-                BX[4] = (A.per[0] || q < nx0) ? (TM)ldB(cell(amap(q, nx0, A.per[0]), j, k)) : TM(0);
-            }
+            for (int o = 0; o < 6; ++o) WX[o] = WX[o + 1];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) BX[o] = BX[o + 1];
+            WX[6] = ldI(eo(amap(i + 4, nx0, A.per[0]), j, k));
+            const int q = i + 3;
+            BX[4] = (A.per[0] || q < nx0) ? ldB(eo(amap(q, nx0, A.per[0]), j, k)) : TM(0);
         }
     }
-    // opacity cotangent of each cell: sum over directions, then through
-    // alpha = kappa rho^m T^-p + alpha^s (T = u_g/Y) to u_g and kappa
-#pragma unroll
-    for (int t = 0; t < TXA; ++t) {
-        double v = abt[t];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) abw[warp][t] = v;
-    }
+    // through alpha = kappa rho^m T^-p + alpha^s (T = u_g/Y) to u_g and kappa
     __syncthreads();
     if (s < nc) {
         const size_t c = cell(x0 + s, j, k);
@@ -472,11 +500,17 @@ __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
         double ubv = 0.0;
         if (A.cc_on[c] && T > 0.0 && ab != 0.0) {
             const double tp = tpow_neg<double>(T, A.T_exp);
-            A.kb[c] += ab * pow(A.rho[c], A.rho_exp) * tp;
+            A.kb[c] += ab * rho_m(A.cc_au[c], A.kap[c], A.rho[c], A.rho_exp) * tp;
             ubv = ab * A.cc_au[c] * (-A.T_exp) * tp / T / Y;
         }
         A.ub[c] = A.ub_acc ? A.ub[c] + ubv : ubv;
     }
+}
+
+// element-wise type conversion (the mixed pass keeps its cotangents in FP32)
+template <typename A, typename B> __global__ void k_cvt(const A *__restrict__ x, B *__restrict__ y, size_t n) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (B)x[i];
 }
 
 }  // namespace
@@ -488,14 +522,14 @@ static rt_status adj_fail(rt_ctx *c, rt_status st, const std::string &msg) {
 }
 
 static rt_status launch_src(rt_ctx *c, bool rev, const void *I, const double *ug_in, double dtk, void *I_out,
-                            double *ug_out, const double *Ibo, const double *ubo, double *Ibi, double *ubi, int ub_acc,
+                            double *ug_out, const void *Ibo, const double *ubo, void *Ibi, double *ubi, int ub_acc,
                             double *kb, double *eb) {
     SrcArgs A{};
     const rt_config &f = c->cfg;
     A.ncell = c->ncell; A.nd = c->nd; A.source = f.source;
     A.dtk = dtk; A.sumw = c->sumw; A.T_exp = f.T_exp; A.arad = f.arad; A.rho_exp = f.rho_exp;
     A.w = c->g->w; A.I = I; A.ug_in = ug_in; A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y;
-    A.eta = c->eta; A.rho = c->rho; A.cc_on = c->cc_on;
+    A.eta = c->eta; A.rho = c->rho; A.kap = c->kap; A.cc_on = c->cc_on;
     A.I_out = I_out; A.ug_out = ug_out; A.Ibo = Ibo; A.ubo = ubo; A.Ibi = Ibi; A.ubi = ubi; A.ub_acc = ub_acc;
     A.kb = kb; A.eb = eb; A.fail = c->fail;
     unsigned nblk = (unsigned)((c->ncell + SC - 1) / SC);
@@ -512,7 +546,7 @@ static rt_status launch_src(rt_ctx *c, bool rev, const void *I, const double *ug
 }
 
 static rt_status launch_tr(rt_ctx *c, const void *I, const double *ug, const double *alpha, double dtk,
-                           const double *Ibo, double *out_src, int src_acc, int add_base, double *base_out, double *ub,
+                           const void *Ibo, void *out_src, int src_acc, int add_base, void *base_out, double *ub,
                            int ub_acc, double *kb) {
     TrArgs A{};
     const rt_config &f = c->cfg;
@@ -523,11 +557,16 @@ static rt_status launch_tr(rt_ctx *c, const void *I, const double *ug, const dou
     A.T_exp = f.T_exp; A.rho_exp = f.rho_exp;
     A.dir = c->g->dir; A.I = I; A.alpha = alpha; A.Ibo = Ibo; A.out_src = out_src; A.base_out = base_out;
     A.src_acc = src_acc; A.add_base = add_base; A.ug = ug; A.cc_au = c->cc_au; A.cc_Y = c->cc_Y; A.rho = c->rho;
+    A.kap = c->kap;
+    for (int a = 0; a < 3; ++a) {
+        A.coef[a] = dtk / f.dx[a];
+        A.hl[a] = f.abar * 0.5 * (f.tau_dt ? dtk : f.dx[a]);
+    }
     A.cc_on = c->cc_on; A.ub = ub; A.kb = kb; A.ub_acc = ub_acc;
     const int nseg = (f.nx[0] + TXA - 1) / TXA;
     unsigned nblk = (unsigned)((size_t)nseg * f.nx[1] * f.nx[2]);
-    if (c->cfg.precision == RT_FP64) k_tr_adj<double, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-    else k_tr_adj<float, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    if (c->cfg.precision == RT_FP64) k_tr_adj<double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
+    else k_tr_adj<float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }
@@ -553,6 +592,8 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
         return adj_fail(c, RT_EINVAL, "rt_step_adjoint: flat Cartesian geometry with the fluid at rest only");
     if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: FP64 or FP32 intensities only");
     if (c->nd > ADJ_NT) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: at most 192 directions");
+    if ((double)c->ncell * c->nd >= 2147483647.0)
+        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: n_cell * n_dir must be below 2^31");
     for (int a = 0; a < 3; ++a) {
         if (!c->active[a]) continue;
         int b0 = c->cfg.bc[a][0], b1 = c->cfg.bc[a][1];
@@ -570,12 +611,13 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
     const int order = c->cfg.order;
     // arena: per step I^n, (order 2: I*_t, I*), I^{n+1}_t in the storage
-    // type, u_g^n, (u_g*); reverse: two FP64 intensity cotangents and eight
-    // per-cell buffers
+    // type, u_g^n, (u_g*); reverse: intensity cotangents in the storage type
+    // (two, plus the running one for FP32) and eight per-cell FP64 buffers
     const size_t es = c->esize, per_step_i = order == 2 ? 4 : 2, per_step_c = order == 2 ? 2 : 1;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t bI = up(ni * es), bX = up(ni * 8), bC = up(nc * 8);
-    const size_t need = per_step_i * nsteps * bI + 2 * bX + (per_step_c * nsteps + 8) * bC;
+    const bool f64 = c->cfg.precision == RT_FP64;
+    const size_t bI = up(ni * es), bX = bI, bC = up(nc * 8);
+    const size_t need = per_step_i * nsteps * bI + (f64 ? 2 : 3) * bX + (per_step_c * nsteps + 8) * bC;
     if (c->adj_bytes < need) {
         if (c->adj) cudaFree(c->adj);
         c->adj = nullptr; c->adj_bytes = 0;
@@ -592,7 +634,8 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
         Ct[n] = take(bI);
     }
     for (int n = 0; n < nsteps; ++n) { un[n] = (double *)take(bC); if (order == 2) us[n] = (double *)take(bC); }
-    double *X1 = (double *)take(bX), *X2 = (double *)take(bX);
+    void *X1 = take(bX), *X2 = take(bX);
+    void *Ib = f64 ? (void *)dL_dI_in : (void *)take(bX);   // the running cotangent of I
     double *ub = (double *)take(bC), *ubn = (double *)take(bC), *ubs = (double *)take(bC), *an = (double *)take(bC);
     double *as_ = (double *)take(bC), *ug_scr = (double *)take(bC), *a_scr = (double *)take(bC);
     double *u_next = (double *)take(bC);
@@ -617,10 +660,13 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
             if ((st = launch_src(c, false, Ct[n], un[n], dt, Inext, unext, 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
         }
     }
-    // 2. reverse sweep; Ib = dL_dI_in holds the running cotangent of I
-    double *Ib = dL_dI_in;
-    if (Ib != dL_dI_out)
+    // 2. reverse sweep
+    if (!f64) {
+        k_cvt<double, float><<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>(dL_dI_out, (float *)Ib, ni);
+        RT_CUDA_TRY(c, cudaGetLastError());
+    } else if (Ib != (void *)dL_dI_out) {
         RT_CUDA_TRY(c, cudaMemcpyAsync(Ib, dL_dI_out, ni * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
     if (dL_dug_out) RT_CUDA_TRY(c, cudaMemcpyAsync(ub, dL_dug_out, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     else RT_CUDA_TRY(c, cudaMemsetAsync(ub, 0, nc * sizeof(double), c->stream));
     for (int n = nsteps - 1; n >= 0; --n) {
@@ -640,6 +686,10 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
             if ((st = launch_tr(c, In[n], un[n], an, 0.5 * dt, X1, Ib, 1, 1, nullptr, ubn, 1, dL_dkappa)) != RT_OK) return st;
         }
         std::swap(ub, ubn);
+    }
+    if (!f64) {
+        k_cvt<float, double><<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>((const float *)Ib, dL_dI_in, ni);
+        RT_CUDA_TRY(c, cudaGetLastError());
     }
     RT_CUDA_TRY(c, cudaMemcpyAsync(dL_dug_in, ub, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     return RT_OK;
