@@ -22,6 +22,14 @@ using namespace rtk;
 
 template <typename TM> struct __align__(4 * sizeof(TM)) Rec4 { TM c1, c2, c3, pad; };
 
+// asynchronous 8-byte global -> shared copy, and waiting for this thread's copies
+__device__ __forceinline__ void cp_async8(double *smem, const double *gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // half of the monotonised central slope, sign(dl) min(|dl|, |dr|, |dl + dr|/4),
 // 0 where the one-sided differences differ in sign (halving is exact, so this
 // is bit-identical to half of the MC slope)
@@ -74,6 +82,10 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
     __shared__ TM part[FS_NT / 32][4][NCELL];
     __shared__ TM cEm[NCELL], cInv[NCELL];
     __shared__ int cOn[NCELL];
+    // per-cell inputs of the interaction (Y, u_g, alpha, kappa rho^m,
+    // alpha^s, eta), copied asynchronously at the start so that their
+    // latency hides behind the transport
+    __shared__ double cIn[6][NCELL];
 
     const int nd = A.nd, NT = blockDim.x, s = threadIdx.x, lane = s & 31, warp = s >> 5;
     const bool act = s < nd;
@@ -88,6 +100,16 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
     }
     for (int t = s; t < BZ * (BY + 4); t += NT) rowY[t] = row_desc(A, j0 - 2 + t % (BY + 4), k0 + t / (BY + 4));
     for (int t = s; t < BY * (BZ + 4); t += NT) rowZ[t] = row_desc(A, j0 + t / (BZ + 4), k0 - 2 + t % (BZ + 4));
+    // local cell lc = o TXC + ii with own row o = r BY + q (lane lc of warp 0)
+    const int lc_ii = lane % TXC, lc_o = lane / TXC;
+    const size_t lc_cell = ((size_t)(k0 + lc_o / BY) * A.nx1 + j0 + lc_o % BY) * A.nx0 + i0 + lc_ii;
+    const bool lc_valid = lc_ii < nc;
+    if (warp == 0 && lc_valid) {
+        const double *srcs[6] = {A.cc_Y, A.ug_in, A.alpha_int, A.cc_au, A.cc_as, A.eta};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) cp_async8(&cIn[q][lane], srcs[q] + lc_cell);
+    }
+    cp_commit_all();
     __syncthreads();
 
     // face coefficients c1 = f e/(f+g), c2 = g e/(f+g), c3 = f g/(f+g) of the
@@ -259,14 +281,11 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
     }
 
     // ---- interaction (section 3.5.2), fluid at rest
-    // local cell lc = o TXC + ii with own row o = r BY + q
-    const int lc_ii = lane % TXC, lc_o = lane / TXC;
-    const size_t lc_cell = ((size_t)(k0 + lc_o / BY) * A.nx1 + j0 + lc_o % BY) * A.nx0 + i0 + lc_ii;
-    const bool lc_valid = lc_ii < nc;
     if (warp == 0) {
+        cp_wait_all();
         int on = 0;
         if (lc_valid) {
-            double Y = A.cc_Y[lc_cell], ug = A.ug_in[lc_cell], am = A.alpha_int[lc_cell];
+            double Y = cIn[0][lane], ug = cIn[1][lane], am = cIn[2][lane];
             on = A.source && A.cc_on[lc_cell] && am > 0.0 && Y > 0.0 && ug > 0.0;
         }
         cOn[lane] = on;
@@ -290,20 +309,23 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
         const size_t cidx = lc_cell;
         const int nw = NT / 32;
         TM ce = TM(0), ci = TM(1);
-        const double ugm = A.ug_in[cidx];
+        const double ugm = cIn[1][lane];
         if (cOn[lane]) {
-            double Em = 0.0, F[3] = {0, 0, 0};
-            for (int g = 0; g < nw; ++g) Em += (double)part[g][0][lane];
+            // warp partials summed in the math type (FP32 for the mixed path:
+            // FP64 adds and conversions are costly here), then widened once
+            TM Emt = TM(0), Ft[3] = {TM(0), TM(0), TM(0)};
+            for (int g = 0; g < nw; ++g) Emt += part[g][0][lane];
             if (WANTG)
                 for (int m = 0; m < 3; ++m)
-                    for (int g = 0; g < nw; ++g) F[m] += (double)part[g][1 + m][lane];
-            const double dt = A.dtk, adt = A.alpha_int[cidx] * dt;
+                    for (int g = 0; g < nw; ++g) Ft[m] += part[g][1 + m][lane];
+            double Em = (double)Emt, F[3] = {(double)Ft[0], (double)Ft[1], (double)Ft[2]};
+            const double dt = A.dtk, adt = cIn[2][lane] * dt;
             const double K = adt / (1.0 + adt);
-            const double Y = A.cc_Y[cidx], au = A.cc_au[cidx], as = A.cc_as[cidx];
+            const double Y = cIn[0][lane], au = cIn[3][lane], as = cIn[4][lane];
             // FP64 divisions are costly on this part: one reciprocal of Y per cell
             const double iY = 1.0 / Y, Tm = ugm * iY;
             Teq<double> q{K * Em, K * A.sumw * dt * (1.0 / FOURPI), Em + ugm, Y, Tm, Em, au, as,
-                          A.eta[cidx], A.arad, dt, A.T_exp, iY};
+                          cIn[5][lane], A.arad, dt, A.T_exp, iY};
             double X, a, c, inv, alpha_new;
             bool ok;
             if (sizeof(TM) == 4) {
@@ -343,7 +365,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             }
         } else {
             A.ug_out[cidx] = ugm;
-            A.alpha_out[cidx] = A.alpha_int[cidx];
+            A.alpha_out[cidx] = cIn[2][lane];
             if (WANTG && A.G) for (int m = 0; m < 4; ++m) A.G[4 * cidx + m] = 0.0;
         }
         cEm[lane] = ce; cInv[lane] = ci;
