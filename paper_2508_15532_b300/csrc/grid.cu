@@ -114,6 +114,26 @@ __global__ void k_grid_geometry(int nd, const double *__restrict__ dir, const in
     }
 }
 
+// reconstruction weights of the minimum-angle planes: for direction s, pair
+// (b, b+1) of its ring and edge midpoint q, the dot products of the pair's
+// gnomonic neighbour images with the midpoint's image (zero outside the ring)
+__global__ void k_mapr_dots(int nd, const int *__restrict__ nnb, const double *__restrict__ mx,
+                            const double *__restrict__ mm, double *__restrict__ md) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 36 * nd) return;
+    int s = t / 36, b = (t / 6) % 6, q = t % 6, kk = nnb[s];
+    double d0 = 0.0, d1 = 0.0;
+    if (b < kk && q < kk) {
+        int b1 = b + 1 == kk ? 0 : b + 1;
+        const double *x0 = mx + (size_t)(6 * s + b) * 3, *x1 = mx + (size_t)(6 * s + b1) * 3;
+        const double *xm = mm + (size_t)(6 * s + q) * 3;
+        d0 = x0[0] * xm[0] + x0[1] * xm[1] + x0[2] * xm[2];
+        d1 = x1[0] * xm[0] + x1[1] * xm[1] + x1[2] * xm[2];
+    }
+    md[2 * (size_t)t] = d0;
+    md[2 * (size_t)t + 1] = d1;
+}
+
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, size_t n) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -149,13 +169,17 @@ rt_status rt_grid_device_geometry(rt_grid *g, std::string &err) {
     GA(g->mxf, nullptr, sizeof(float) * 18 * nd);
     GA(g->mgf, nullptr, sizeof(float) * 18 * nd);
     GA(g->mmf, nullptr, sizeof(float) * 18 * nd);
+    GA(g->md, nullptr, sizeof(double) * 72 * nd);
+    GA(g->mdf, nullptr, sizeof(float) * 72 * nd);
 #undef GA
     if (e != cudaSuccess) { err = std::string("grid allocation: ") + cudaGetErrorString(e); return RT_ENOMEM; }
     k_grid_geometry<<<(nd + 127) / 128, 128>>>(nd, g->dir, g->nnb, g->nbr, g->ring_edge, g->w, g->emid, g->eu,
                                                g->dlam, g->mx, g->mg, g->mm);
     auto tof = [&](const double *a, float *b, size_t n) { k_to_float<<<(unsigned)((n + 255) / 256), 256>>>(a, b, n); };
     tof(g->dir, g->dirf, 3 * (size_t)nd); tof(g->w, g->wf, nd);
+    k_mapr_dots<<<(36 * nd + 255) / 256, 256>>>(nd, g->nnb, g->mx, g->mm, g->md);
     tof(g->mx, g->mxf, 18 * (size_t)nd); tof(g->mg, g->mgf, 18 * (size_t)nd); tof(g->mm, g->mmf, 18 * (size_t)nd);
+    tof(g->md, g->mdf, 72 * (size_t)nd);
     e = cudaDeviceSynchronize();
     if (e == cudaSuccess) {
         g->h_w.resize(nd);
@@ -168,7 +192,7 @@ rt_status rt_grid_device_geometry(rt_grid *g, std::string &err) {
 static void free_grid(rt_grid *g) {
     if (!g) return;
     void *ptrs[] = {g->dir, g->w, g->nnb, g->nbr, g->ring_edge, g->ring_back, g->mirror, g->edge, g->emid,
-                    g->eu, g->dlam, g->mx, g->mg, g->mm, g->dirf, g->wf, g->mxf, g->mgf, g->mmf};
+                    g->eu, g->dlam, g->mx, g->mg, g->mm, g->dirf, g->wf, g->mxf, g->mgf, g->mmf, g->md, g->mdf};
     for (void *p : ptrs) if (p) cudaFree(p);
     delete g;
 }

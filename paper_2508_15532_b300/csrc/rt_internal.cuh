@@ -31,7 +31,10 @@ struct rt_grid {
     double *mx = nullptr;        // [nd*6*3] gnomonic image of neighbour q in the tangent plane of s
     double *mg = nullptr;        // [nd*6*3] inverse Gram matrix (a, b, c) of the pair (q, q+1)
     double *mm = nullptr;        // [nd*6*3] gnomonic image of the midpoint of edge q
-    float *dirf = nullptr, *wf = nullptr, *mxf = nullptr, *mgf = nullptr, *mmf = nullptr;
+    // md[((s*6 + b)*6 + q)*2 + {0,1}] = mx(s, b).mm(s, q), mx(s, b+1).mm(s, q):
+    // the reconstruction weights of edge midpoint q for the plane of pair b
+    double *md = nullptr;        // [nd*6*6*2]
+    float *dirf = nullptr, *wf = nullptr, *mxf = nullptr, *mgf = nullptr, *mmf = nullptr, *mdf = nullptr;
 };
 
 // Per-context device state.

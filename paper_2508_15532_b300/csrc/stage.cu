@@ -183,6 +183,30 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 W0[o] = I0; W1[o] = I1; S0[o] = s0; Flo[o] = phi;
             }
         }
+        // ring of direction s: neighbours, edges, back slots, which side of
+        // each edge s is, the MAPR Gram inverses, 1/dOmega (curved geometry)
+        int rg_kk = 0, rg_nb[RT_MAXNB], rg_e[RT_MAXNB], rg_bk[RT_MAXNB];
+        unsigned rg_own = 0u;
+        TM rg_g[3 * RT_MAXNB], rg_winv = TM(0);
+#pragma unroll
+        for (int q = 0; q < RT_MAXNB; ++q) { rg_nb[q] = s; rg_e[q] = 0; rg_bk[q] = 0; }
+#pragma unroll
+        for (int q = 0; q < 3 * RT_MAXNB; ++q) rg_g[q] = TM(0);
+        if (!FLAT && act) {
+            rg_kk = __ldg(A.nnb + s);
+            rg_winv = TM(1) / ldT<TM>(A.wT, s);
+#pragma unroll
+            for (int q = 0; q < RT_MAXNB; ++q) {
+                if (q < rg_kk) {
+                    rg_nb[q] = __ldg(A.nbr + 6 * s + q);
+                    rg_e[q] = __ldg(A.ring_edge + 6 * s + q);
+                    rg_bk[q] = __ldg(A.ring_back + 6 * s + q);
+                    rg_own |= (unsigned)(__ldg(A.edge + 2 * rg_e[q]) == s) << q;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) rg_g[3 * q + m] = ldT<TM>(A.mgT, (size_t)(6 * s + q) * 3 + m);
+                }
+            }
+        }
         for (int ii = 0; ii < nc; ++ii) {
             const int i = i0 + ii;
             TM acc[NOWN], Ic[NOWN];
@@ -270,7 +294,8 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             }
             // angular flux (curved geometry): minimum-angle plane reconstruction
             // of every direction at the edge midpoints, edge fluxes with the
-            // upwind side of n_0(m) v(m).u_e (eq. angular_fluxes)
+            // upwind side of n_0(m) v(m).u_e (eq. angular_fluxes); ring data of
+            // direction s in registers (rg_*), loops over the ring unrolled
             TM ang[NOWN];
 #pragma unroll
             for (int o = 0; o < NOWN; ++o) ang[o] = TM(0);
@@ -278,59 +303,63 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 if (act)
                     for (int o = 0; o < NOWN; ++o) Icell[o * nd + s] = Ic[o];
                 __syncthreads();
-                int kk = act ? __ldg(A.nnb + s) : 0;
                 if (act) {
                     for (int o = 0; o < NOWN; ++o) {
                         TM rec[RT_MAXNB];
                         if (A.ang_recon == 1) {
-                            for (int q = 0; q < kk; ++q) rec[q] = Ic[o];
+#pragma unroll
+                            for (int q = 0; q < RT_MAXNB; ++q) rec[q] = Ic[o];
                         } else {
                             TM dI[RT_MAXNB], al[RT_MAXNB], be[RT_MAXNB], nr[RT_MAXNB];
-                            for (int q = 0; q < kk; ++q) dI[q] = Icell[o * nd + __ldg(A.nbr + 6 * s + q)] - Ic[o];
+#pragma unroll
+                            for (int q = 0; q < RT_MAXNB; ++q) dI[q] = q < rg_kk ? Icell[o * nd + rg_nb[q]] - Ic[o] : TM(0);
                             TM mn = TM(0);
-                            for (int q = 0; q < kk; ++q) {
-                                int q1 = q + 1 == kk ? 0 : q + 1;
-                                const size_t og = (size_t)(6 * s + q) * 3;
-                                TM ga = ldT<TM>(A.mgT, og), gb = ldT<TM>(A.mgT, og + 1), gc = ldT<TM>(A.mgT, og + 2);
-                                al[q] = ga * dI[q] + gb * dI[q1];
-                                be[q] = gb * dI[q] + gc * dI[q1];
-                                nr[q] = al[q] * dI[q] + be[q] * dI[q1];
-                                if (q == 0 || nr[q] < mn) mn = nr[q];
+#pragma unroll
+                            for (int q = 0; q < RT_MAXNB; ++q) {
+                                const TM d1 = q + 1 < rg_kk ? dI[q + 1] : dI[0];
+                                al[q] = rg_g[3 * q] * dI[q] + rg_g[3 * q + 1] * d1;
+                                be[q] = rg_g[3 * q + 1] * dI[q] + rg_g[3 * q + 2] * d1;
+                                nr[q] = al[q] * dI[q] + be[q] * d1;
+                                if (q < rg_kk && (q == 0 || nr[q] < mn)) mn = nr[q];
                             }
                             // near-equal norms tie (mirror-symmetric neighbourhoods); first in ring order wins
-                            int best = 0;
-                            while (best + 1 < kk && !(nr[best] <= mn + TM(1e-6) * fabs(mn))) ++best;
-                            int b1 = best + 1 == kk ? 0 : best + 1;
-                            const size_t ox0 = (size_t)(6 * s + best) * 3, ox1 = (size_t)(6 * s + b1) * 3;
-                            TM x0[3], x1[3];
-                            for (int m = 0; m < 3; ++m) { x0[m] = ldT<TM>(A.mxT, ox0 + m); x1[m] = ldT<TM>(A.mxT, ox1 + m); }
-                            for (int q = 0; q < kk; ++q) {
-                                const size_t om = (size_t)(6 * s + q) * 3;
-                                TM xm0 = ldT<TM>(A.mmT, om), xm1 = ldT<TM>(A.mmT, om + 1), xm2 = ldT<TM>(A.mmT, om + 2);
-                                rec[q] = Ic[o] + al[best] * (x0[0] * xm0 + x0[1] * xm1 + x0[2] * xm2) +
-                                         be[best] * (x1[0] * xm0 + x1[1] * xm1 + x1[2] * xm2);
-                            }
+                            const TM thr = mn + TM(1e-6) * fabs(mn);
+                            int best = rg_kk - 1;
+#pragma unroll
+                            for (int q = RT_MAXNB - 1; q >= 0; --q)
+                                if (q < rg_kk && nr[q] <= thr) best = q;
+                            TM ab = TM(0), bb = TM(0);
+#pragma unroll
+                            for (int q = 0; q < RT_MAXNB; ++q)
+                                if (q == best) { ab = al[q]; bb = be[q]; }
+                            // precomputed dot products of the plane's dual basis with the edge midpoints
+                            const size_t od = (size_t)(6 * s + best) * 12;
+#pragma unroll
+                            for (int q = 0; q < RT_MAXNB; ++q)
+                                rec[q] = Ic[o] + ab * ldT<TM>(A.mdT, od + 2 * q) + bb * ldT<TM>(A.mdT, od + 2 * q + 1);
                         }
-                        for (int q = 0; q < kk; ++q) Arec[(o * nd + s) * 6 + q] = rec[q];
+#pragma unroll
+                        for (int q = 0; q < RT_MAXNB; ++q)
+                            if (q < rg_kk) Arec[(o * nd + s) * 6 + q] = rec[q];
                     }
                 }
                 __syncthreads();
                 if (act) {
-                    TM winv = TM(1) / ldT<TM>(A.wT, s);
                     for (int o = 0; o < NOWN; ++o) {
                         const int pc = (j0 + o % BY + A.ng1) * A.gn0 + (i + A.ng0);
                         TM a = TM(0);
-                        for (int q = 0; q < kk; ++q) {
-                            int e = __ldg(A.ring_edge + 6 * s + q), t = __ldg(A.nbr + 6 * s + q);
-                            int back = __ldg(A.ring_back + 6 * s + q);
-                            bool own = __ldg(A.edge + 2 * e) == s;
-                            TM w = ldT<TM>(A.ew, (size_t)pc * A.ne + e);
-                            TM Io = Arec[(o * nd + s) * 6 + q], It2 = Arec[(o * nd + t) * 6 + back];
-                            TM IL = own ? Io : It2, IR = own ? It2 : Io;
-                            TM F = w * (w > TM(0) ? IL : IR);
-                            a += own ? F : -F;
+#pragma unroll
+                        for (int q = 0; q < RT_MAXNB; ++q) {
+                            if (q < rg_kk) {
+                                const bool own = (rg_own >> q) & 1u;
+                                TM w = ldT<TM>(A.ew, (size_t)pc * A.ne + rg_e[q]);
+                                TM Io = Arec[(o * nd + s) * 6 + q], It2 = Arec[(o * nd + rg_nb[q]) * 6 + rg_bk[q]];
+                                TM IL = own ? Io : It2, IR = own ? It2 : Io;
+                                TM F = w * (w > TM(0) ? IL : IR);
+                                a += own ? F : -F;
+                            }
                         }
-                        ang[o] = a * winv;
+                        ang[o] = a * rg_winv;
                     }
                 }
                 __syncthreads();
@@ -639,6 +668,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.mxT = dbl ? (const void *)g->mx : (const void *)g->mxf;
     A.mgT = dbl ? (const void *)g->mg : (const void *)g->mgf;
     A.mmT = dbl ? (const void *)g->mm : (const void *)g->mmf;
+    A.mdT = dbl ? (const void *)g->md : (const void *)g->mdf;
     bool flat = c->metric == RT_MINKOWSKI_CART;
     A.ng0 = c->active[0] ? 2 : 0; A.ng1 = c->active[1] ? 2 : 0; A.gn0 = c->gn[0];
     if (!flat) {

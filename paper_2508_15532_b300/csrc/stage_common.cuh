@@ -33,6 +33,7 @@ struct StageArgs {
     unsigned long long *fail;
     const int *mirror, *nnb, *nbr, *ring_edge, *ring_back, *edge;
     const void *dirT, *wT, *mxT, *mgT, *mmT;   // math-type copies of the grid tables
+    const void *mdT;                            // MAPR dual-basis dot products [nd][6][6][2]
     int gn0, ng0, ng1;
     const void *cenU, *fn, *fP, *ew;           // math-type geometry tables (curved)
     const uint8_t *mask;
