@@ -203,6 +203,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--n-cells", type=int, default=128)
     ap.add_argument("--workload", default="flat3d", choices=["flat3d", "kerr3d", "kerr2d"])
+    ap.add_argument("--kerr-dims", type=int, nargs=3, default=None, metavar=("NR", "NTH", "NPH"),
+                    help="Kerr grid other than the workload's (a smaller case for profiling)")
     ap.add_argument("--ref-cells", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -255,7 +257,11 @@ def main():
         cfg, f = W.flat3d(N=N, n_geo=4, intensity_dtype=np_dt)
         wname = "flat3d-periodic-opacity-coupling"
     else:
-        cfg, f = (W.kerr3d if args.workload == "kerr3d" else W.kerr2d)(n_geo=4)
+        if args.kerr_dims:
+            nr, nth, nph = args.kerr_dims
+            cfg, f = W.kerr(nr=nr, nth=nth, nph=nph, n_geo=4, index=3 if nph > 1 else 2)
+        else:
+            cfg, f = (W.kerr3d if args.workload == "kerr3d" else W.kerr2d)(n_geo=4)
         f["I"] = f["I"].astype(np_dt)
         wname = args.workload + "-kerr-schild-a0.9-torus"
     nd = f["I"].shape[1]
