@@ -22,7 +22,6 @@ using namespace rtk;
 namespace {
 
 constexpr int ADJ_NT = 192;   // threads of a block = directions (n_dir <= 192)
-constexpr int SC = 16;        // cells per interaction block (one lane per cell in the solve)
 constexpr int TXA = 8;        // cells per transport-adjoint block along x1
 constexpr int NFACE = 9 * TXA + 3;
 
@@ -50,10 +49,10 @@ __device__ __forceinline__ double rho_m(double au, double kap, double rho, doubl
     return kap != 0.0 ? au / kap : pow(rho, m);
 }
 
-// 16 values per lane -> lane l (and l + 16) holds the warp sum of value l & 15
-template <typename R> __device__ __forceinline__ R tsum16(R (&v)[SC], int lane) {
+// N (16 or 32) values per lane -> lane l holds the warp sum of value l % N
+template <int N, typename R> __device__ __forceinline__ R tsum(R (&v)[N], int lane) {
 #pragma unroll
-    for (int n = 8; n >= 1; n >>= 1) {
+    for (int n = N / 2; n >= 1; n >>= 1) {
         const bool hi = (lane & n) != 0;
 #pragma unroll
         for (int i = 0; i < n; ++i) {
@@ -62,8 +61,13 @@ template <typename R> __device__ __forceinline__ R tsum16(R (&v)[SC], int lane) 
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, n);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+    if (N == 16) return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+    return v[0];
 }
+
+// cells per interaction block (one lane of warp 0 per cell in the solve):
+// 32 for the FP32 pass, 16 for FP64 (register arrays of 16 doubles)
+template <typename R> struct CellsPerBlock { static constexpr int v = sizeof(R) == 4 ? 32 : 16; };
 
 // REV = false: I_out = interaction(I), u_g out.  REV = true: the reverse.
 // R is the storage and per-element arithmetic type of intensities and their
@@ -71,6 +75,7 @@ template <typename R> __device__ __forceinline__ R tsum16(R (&v)[SC], int lane) 
 // the sums over warps and the per-cell arithmetic in FP64.
 template <bool REV, typename R>
 __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
+    constexpr int SC = CellsPerBlock<R>::v;
     constexpr int NW = ADJ_NT / 32;
     __shared__ double part[NW][3][SC];
     __shared__ double sh_a[SC], sh_b[SC], sh_c[SC];
@@ -90,15 +95,15 @@ __global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
     }
 #pragma unroll
     for (int k = 0; k < SC; ++k) v[k] = Iv[k] * w;
-    R r0 = tsum16<R>(v, lane);
+    R r0 = tsum<SC, R>(v, lane);
     if (lane < SC) part[warp][0][lane] = (double)r0;
     if (REV) {
 #pragma unroll
         for (int k = 0; k < SC; ++k) v[k] = Bv[k];
-        R r1 = tsum16<R>(v, lane);
+        R r1 = tsum<SC, R>(v, lane);
 #pragma unroll
         for (int k = 0; k < SC; ++k) v[k] = Bv[k] * Iv[k];
-        R r2 = tsum16<R>(v, lane);
+        R r2 = tsum<SC, R>(v, lane);
         if (lane < SC) { part[warp][1][lane] = (double)r1; part[warp][2][lane] = (double)r2; }
     }
     __syncthreads();
@@ -237,6 +242,26 @@ template <typename TM> __device__ void face_cd(TM tau, TM *fc) {
     }
 }
 
+// the six face coefficients from a 16-byte aligned shared record, with vector loads
+__device__ __forceinline__ void ldfc6(const float *p, float (&f)[6]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    const float2 b = *reinterpret_cast<const float2 *>(p + 4);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y;
+}
+__device__ __forceinline__ void ldfc6(const double *p, double (&f)[6]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2),
+                  c = *reinterpret_cast<const double2 *>(p + 4);
+    f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y; f[4] = c.x; f[5] = c.y;
+}
+__device__ __forceinline__ void ldfc2(const float *p, float (&f)[2]) {
+    const float2 a = *reinterpret_cast<const float2 *>(p);
+    f[0] = a.x; f[1] = a.y;
+}
+__device__ __forceinline__ void ldfc2(const double *p, double (&f)[2]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    f[0] = a.x; f[1] = a.y;
+}
+
 // derivative of the limited slope in (dl, dr), branches of rtk::limiter
 template <typename TM> __device__ __forceinline__ void lim_d(int kind, TM dl, TM dr, TM &gl, TM &gr) {
     gl = TM(0); gr = TM(0);
@@ -268,7 +293,8 @@ __device__ __forceinline__ void axis_adj(const TM (&V)[7], const TM (&B)[5], uns
         const TM phib = coef * (B[m + 3] - B[m + 2]);
         if (phib == TM(0)) continue;
         const TM Ill = V[m + 2], Il = V[m + 3], Ir = V[m + 4], Irr = V[m + 5];
-        const TM *f = fc[m + 2];
+        TM f[6];
+        ldfc6(fc[m + 2], f);
         TM gla, glb, gra, grb;
         lim_d<TM>(lim, Ir - Il, Il - Ill, gla, glb);
         lim_d<TM>(lim, Irr - Ir, Ir - Il, gra, grb);
@@ -328,13 +354,15 @@ __device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5],
     const TM ph[4] = {coef * (B[1] - B[0]), coef * (B[2] - B[1]), coef * (B[3] - B[2]), coef * (B[4] - B[3])};
     // m = -2: this cell is I_{r+1}; IR = I_r - s_r/2 with s_r the slope of offset -1
     {
-        const TM *f = fc[0];
+        TM f[2];
+        ldfc2(fc[0], f);
         const TM IRb = ph[0] * n * (pos ? f[1] : f[0]);
         g += -h * IRb * ga[0];
     }
     // m = -1: this cell is I_r
     {
-        const TM *f = fc[1];
+        TM f[6];
+        ldfc6(fc[1], f);
         const TM cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
         const TM ILb = ph[1] * n * cL, IRb = ph[1] * n * cR, c3t = ph[1] * an * f[2];
         g += -c3t + h * ILb * ga[0] + IRb * (one + h * ga[1] - h * gb[1]);
@@ -344,7 +372,8 @@ __device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5],
     }
     // m = 0: this cell is I_l
     {
-        const TM *f = fc[2];
+        TM f[6];
+        ldfc6(fc[2], f);
         const TM cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
         const TM ILb = ph[2] * n * cL, IRb = ph[2] * n * cR, c3t = ph[2] * an * f[2];
         g += c3t + ILb * (one - h * ga[1] + h * gb[1]) + h * IRb * gb[2];
@@ -354,7 +383,8 @@ __device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5],
     }
     // m = 1: this cell is I_{l-1}; IL = I_l + s_l/2 with s_l the slope of offset 1
     {
-        const TM *f = fc[3];
+        TM f[2];
+        ldfc2(fc[3], f);
         const TM ILb = ph[3] * n * (pos ? f[0] : f[1]);
         g += -h * ILb * gb[2];
     }
@@ -366,7 +396,7 @@ __device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5],
 template <typename TM>
 __global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
     constexpr int NW = ADJ_NT / 32;
-    __shared__ TM fcs[NFACE][6];
+    __shared__ __align__(16) TM fcs[NFACE][8];   // c1 c2 c3 dc1 dc2 dc3 (padded for vector loads)
     __shared__ double abw[NW][TXA];
     const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
     const bool act = s < A.nd;
@@ -532,8 +562,9 @@ static rt_status launch_src(rt_ctx *c, bool rev, const void *I, const double *ug
     A.eta = c->eta; A.rho = c->rho; A.kap = c->kap; A.cc_on = c->cc_on;
     A.I_out = I_out; A.ug_out = ug_out; A.Ibo = Ibo; A.ubo = ubo; A.Ibi = Ibi; A.ubi = ubi; A.ub_acc = ub_acc;
     A.kb = kb; A.eb = eb; A.fail = c->fail;
-    unsigned nblk = (unsigned)((c->ncell + SC - 1) / SC);
     const bool f64 = c->cfg.precision == RT_FP64;
+    const int SC = f64 ? CellsPerBlock<double>::v : CellsPerBlock<float>::v;
+    unsigned nblk = (unsigned)((c->ncell + SC - 1) / SC);
     if (rev) {
         if (f64) k_src<true, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
         else k_src<true, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
