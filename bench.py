@@ -322,7 +322,8 @@ def main():
                 "traffic": (traffic * cell_angles if traffic else None),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
-                "kernel": ("k_stage_fs" if args.workload == "flat3d" else "k_stage") + " (transport + interaction, fused)"}
+                "kernel": ({"fp32": "k_stage_fp2", "bf16": "k_stage_fs", "fp64": "k_stage_fs"}[prec]
+                           if args.workload == "flat3d" else "k_stage") + " (transport + interaction, fused)"}
 
     # ---- end to end through the public API with pinned host buffers: every
     # step uploads its inputs (I, u_g), steps, and reads its results back.  Two

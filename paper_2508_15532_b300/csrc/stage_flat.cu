@@ -389,6 +389,335 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 variant of k_stage_fs: each thread owns a pair of adjacent
+// directions (2p, 2p+1) (n_dir = 10 n^2 + 2 is even) and works on both with
+// f32x2 arithmetic (add/sub/mul/fma.rn.f32x2) and 8-byte loads and stores,
+// which halves the arithmetic, load and address instructions per cell-angle.
+// FP32 storage, periodic/outflow boundaries only.  Five CTAs of 96 threads
+// per SM (128 registers, 30 KB shared memory): measured 7% faster than
+// k_stage_fs at 128^3 x 162; six CTAs spill.
+struct F2 { float x, y; };
+__device__ __forceinline__ F2 f2(float a) { return F2{a, a}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+    F2 r;
+    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; add.rn.f32x2 rc, ra, rb; mov.b64 {%0, %1}, rc; }"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    F2 r;
+    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; sub.rn.f32x2 rc, ra, rb; mov.b64 {%0, %1}, rc; }"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+    F2 r;
+    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; mul.rn.f32x2 rc, ra, rb; mov.b64 {%0, %1}, rc; }"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+// a * b + c
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("{ .reg .b64 ra, rb, rc, rd; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; mov.b64 rc, {%6, %7};"
+        " fma.rn.f32x2 rd, ra, rb, rc; mov.b64 {%0, %1}, rd; }"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+__device__ __forceinline__ F2 ld2(const float *p) { float2 v = __ldg(reinterpret_cast<const float2 *>(p)); return F2{v.x, v.y}; }
+__device__ __forceinline__ void st2(float *p, F2 v) { __stcs(reinterpret_cast<float2 *>(p), make_float2(v.x, v.y)); }
+
+// half MC slope per component (see mc_half)
+__device__ __forceinline__ F2 mc_half2(F2 dl, F2 dr) {
+    const F2 h = F2{0.25f, 0.25f} * (dl + dr), pr = dl * dr;
+    float mx = fminf(fminf(fabsf(dl.x), fabsf(dr.x)), fabsf(h.x));
+    float my = fminf(fminf(fabsf(dl.y), fabsf(dr.y)), fabsf(h.y));
+    return F2{pr.x > 0.0f ? copysignf(mx, dl.x) : 0.0f, pr.y > 0.0f ? copysignf(my, dl.y) : 0.0f};
+}
+// the face flux per component: n (cL I_L + cR I_R) - |n| c3 (I_r - I_l)
+__device__ __forceinline__ F2 phi2(F2 n, F2 an, const Rec4<float> &r, F2 IL, F2 IR, F2 Il, F2 Ir) {
+    const F2 cL = F2{n.x > 0.0f ? r.c1 : r.c2, n.y > 0.0f ? r.c1 : r.c2};
+    const F2 cR = F2{n.x > 0.0f ? r.c2 : r.c1, n.y > 0.0f ? r.c2 : r.c1};
+    const F2 t = fma2(cR, IR, cL * IL);
+    return n * t - (an * f2(r.c3)) * (Ir - Il);
+}
+
+constexpr int FP2_NT = 96;
+
+template <int BY, int BZ, bool WANTG>
+__global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
+    constexpr int TXC = NCELL / (BY * BZ), NOWN = BY * BZ, NW = FP2_NT / 32;
+    __shared__ int xmap[TXC + 4];
+    __shared__ int rowY[BZ * (BY + 4)], rowZ[BY * (BZ + 4)];
+    __shared__ Rec4<float> recX[NOWN * (TXC + 1)], recY[BZ * (BY + 1) * TXC], recZ[BY * (BZ + 1) * TXC];
+    __shared__ float part[NW][4][NCELL];
+    __shared__ float cEm[NCELL], cInv[NCELL];
+    __shared__ int cOn[NCELL];
+    __shared__ double cIn[6][NCELL];
+    __shared__ __align__(8) float sIt[NCELL][2 * FP2_NT];
+
+    const int nd = A.nd, NT = blockDim.x, p = threadIdx.x, lane = p & 31, warp = p >> 5;
+    const int d0 = 2 * p;
+    const bool act = d0 < nd;   // n_dir is even: both directions of the pair exist
+    const int nseg = (A.nx0 + TXC - 1) / TXC;
+    const int seg = blockIdx.x % nseg, rest = blockIdx.x / nseg, nyb = A.nx1 / BY;
+    const int j0 = (rest % nyb) * BY, k0 = (rest / nyb) * BZ, i0 = seg * TXC;
+    const int nc = min(TXC, A.nx0 - i0);
+
+    for (int t = p; t < TXC + 4; t += NT) {
+        int fl = 0;
+        xmap[t] = map_axis(A, 0, i0 - 2 + t, &fl, nullptr) | fl;
+    }
+    for (int t = p; t < BZ * (BY + 4); t += NT) rowY[t] = row_desc(A, j0 - 2 + t % (BY + 4), k0 + t / (BY + 4));
+    for (int t = p; t < BY * (BZ + 4); t += NT) rowZ[t] = row_desc(A, j0 + t / (BZ + 4), k0 - 2 + t % (BZ + 4));
+    const int lc_ii = lane % TXC, lc_o = lane / TXC;
+    const size_t lc_cell = ((size_t)(k0 + lc_o / BY) * A.nx1 + j0 + lc_o % BY) * A.nx0 + i0 + lc_ii;
+    const bool lc_valid = lc_ii < nc;
+    if (warp == 0 && lc_valid) {
+        const double *srcs[6] = {A.cc_Y, A.ug_in, A.alpha_int, A.cc_au, A.cc_as, A.eta};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) cp_async8(&cIn[q][lane], srcs[q] + lc_cell);
+    }
+    cp_commit_all();
+    __syncthreads();
+
+    auto coeffs = [&](int cl, int cr, double len, Rec4<float> &r) {
+        double tau = A.abar * 0.5 * (A.alpha_in[cl] + A.alpha_in[cr]) * (A.tau_dt ? A.dtk : len);
+        if (tau > 0.0) {
+            float t = (float)tau;
+            float f = sqrtf(-expm1f(-t * t)) / t, g = sqrtf(-expm1f(-t * t * t * t)) / t, e = expf(-t), fg = f + g;
+            r.c1 = f * e / fg; r.c2 = g * e / fg; r.c3 = f * g / fg;
+        } else {
+            r.c1 = 1.0f; r.c2 = 0.0f; r.c3 = 0.0f;
+        }
+        r.pad = 0.0f;
+    };
+    if (A.transport) {
+        const int nX = A.act0 ? NOWN * (nc + 1) : 0, nY = A.act1 ? BZ * (BY + 1) * nc : 0;
+        const int nZ = A.act2 ? BY * (BZ + 1) * nc : 0;
+        for (int t = p; t < nX + nY + nZ; t += NT) {
+            if (t < nX) {
+                int o = t / (nc + 1), f = t % (nc + 1);
+                int rb = rowY[(o / BY) * (BY + 4) + o % BY + 2] & F_MASK;
+                coeffs(rb + (xmap[f + 1] & F_MASK), rb + (xmap[f + 2] & F_MASK), A.dx0, recX[o * (TXC + 1) + f]);
+            } else if (t < nX + nY) {
+                int u = t - nX, ii = u % nc, v = u / nc, f = v % (BY + 1), r = v / (BY + 1);
+                coeffs((rowY[r * (BY + 4) + f + 1] & F_MASK) + i0 + ii, (rowY[r * (BY + 4) + f + 2] & F_MASK) + i0 + ii,
+                       A.dx1, recY[(r * (BY + 1) + f) * TXC + ii]);
+            } else {
+                int u = t - nX - nY, ii = u % nc, v = u / nc, f = v % (BZ + 1), q = v / (BZ + 1);
+                coeffs((rowZ[q * (BZ + 4) + f + 1] & F_MASK) + i0 + ii, (rowZ[q * (BZ + 4) + f + 2] & F_MASK) + i0 + ii,
+                       A.dx2, recZ[(q * (BZ + 1) + f) * TXC + ii]);
+            }
+        }
+    }
+    __syncthreads();
+
+    const float *Isrc = (const float *)A.Isrc;
+    F2 nh[3] = {f2(0.0f), f2(0.0f), f2(0.0f)}, w = f2(0.0f);
+    if (act) {
+        for (int m = 0; m < 3; ++m) nh[m] = F2{((const float *)A.dirT)[3 * d0 + m], ((const float *)A.dirT)[3 * d0 + 3 + m]};
+        w = ld2((const float *)A.wT + d0);
+    }
+    const F2 an[3] = {F2{fabsf(nh[0].x), fabsf(nh[0].y)}, F2{fabsf(nh[1].x), fabsf(nh[1].y)}, F2{fabsf(nh[2].x), fabsf(nh[2].y)}};
+    const float dtk = (float)A.dtk;
+    const F2 cdx[3] = {f2(dtk / (float)A.dx0), f2(dtk / (float)A.dx1), f2(dtk / (float)A.dx2)};
+    auto roff = [&](int desc) -> int { return (desc & F_MASK) * nd + d0; };
+    auto ldo = [&](int off, int i) -> F2 { return ld2(Isrc + (unsigned)(off + i * nd)); };
+    auto ldx = [&](int ownoff, int xd) -> F2 { return ld2(Isrc + (unsigned)(ownoff + (xd & F_MASK) * nd)); };
+    auto putIt = [&](int c, F2 v) { *reinterpret_cast<float2 *>(&sIt[c][d0]) = make_float2(v.x, v.y); };
+    auto getIt = [&](int c) -> F2 { float2 v = *reinterpret_cast<const float2 *>(&sIt[c][d0]); return F2{v.x, v.y}; };
+
+    if (act) {
+        int oy[BZ][BY + 4], oz[BY][BZ + 4];
+#pragma unroll
+        for (int r = 0; r < BZ; ++r)
+#pragma unroll
+            for (int q = 0; q < BY + 4; ++q) oy[r][q] = roff(rowY[r * (BY + 4) + q]);
+#pragma unroll
+        for (int q = 0; q < BY; ++q)
+#pragma unroll
+            for (int r = 0; r < BZ + 4; ++r) oz[q][r] = roff(rowZ[q * (BZ + 4) + r]);
+        const bool same_base = A.Isrc == A.Ibase;
+        if (A.transport) {
+            F2 W0[NOWN], W1[NOWN], S0[NOWN], Flo[NOWN];
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                W0[o] = W1[o] = S0[o] = Flo[o] = f2(0.0f);
+                if (A.act0) {
+                    const int q = o % BY, r = o / BY, own = oy[r][q + 2];
+                    F2 Im2 = ldx(own, xmap[0]), Im1 = ldx(own, xmap[1]);
+                    F2 I0 = ldx(own, xmap[2]), I1 = ldx(own, xmap[3]);
+                    F2 sm1 = mc_half2(I0 - Im1, Im1 - Im2), s0 = mc_half2(I1 - I0, I0 - Im1);
+                    Flo[o] = phi2(nh[0], an[0], recX[o * (TXC + 1)], Im1 + sm1, I0 - s0, Im1, I0);
+                    W0[o] = I0; W1[o] = I1; S0[o] = s0;
+                }
+            }
+#pragma unroll
+            for (int ii = 0; ii < TXC; ++ii) {
+                if (ii < nc) {
+                    const int i = i0 + ii;
+                    F2 acc[NOWN], Ic[NOWN];
+#pragma unroll
+                    for (int o = 0; o < NOWN; ++o) {
+                        acc[o] = f2(0.0f);
+                        Ic[o] = A.act0 ? W0[o] : ldo(oy[o / BY][o % BY + 2], i);
+                    }
+                    if (A.act0) {
+#pragma unroll
+                        for (int o = 0; o < NOWN; ++o) {
+                            const int q = o % BY, r = o / BY;
+                            F2 I2 = ldx(oy[r][q + 2], xmap[ii + 4]);
+                            F2 s1 = mc_half2(I2 - W1[o], W1[o] - W0[o]);
+                            F2 phi = phi2(nh[0], an[0], recX[o * (TXC + 1) + ii + 1], W0[o] + S0[o], W1[o] - s1, W0[o], W1[o]);
+                            acc[o] = fma2(cdx[0], phi - Flo[o], acc[o]);
+                            Flo[o] = phi; W0[o] = W1[o]; W1[o] = I2; S0[o] = s1;
+                        }
+                    }
+                    if (A.act1) {
+#pragma unroll
+                        for (int r = 0; r < BZ; ++r) {
+                            F2 Y[BY + 4], sy[BY + 4], F[BY + 1];
+#pragma unroll
+                            for (int q = 0; q < BY + 4; ++q) Y[q] = (q >= 2 && q < BY + 2) ? Ic[r * BY + q - 2] : ldo(oy[r][q], i);
+#pragma unroll
+                            for (int q = 1; q < BY + 3; ++q) sy[q] = mc_half2(Y[q + 1] - Y[q], Y[q] - Y[q - 1]);
+#pragma unroll
+                            for (int f = 0; f <= BY; ++f)
+                                F[f] = phi2(nh[1], an[1], recY[(r * (BY + 1) + f) * TXC + ii], Y[f + 1] + sy[f + 1],
+                                            Y[f + 2] - sy[f + 2], Y[f + 1], Y[f + 2]);
+#pragma unroll
+                            for (int q = 0; q < BY; ++q) acc[r * BY + q] = fma2(cdx[1], F[q + 1] - F[q], acc[r * BY + q]);
+                        }
+                    }
+                    if (A.act2) {
+#pragma unroll
+                        for (int q = 0; q < BY; ++q) {
+                            F2 Z[BZ + 4], sz[BZ + 4], F[BZ + 1];
+#pragma unroll
+                            for (int r = 0; r < BZ + 4; ++r) Z[r] = (r >= 2 && r < BZ + 2) ? Ic[(r - 2) * BY + q] : ldo(oz[q][r], i);
+#pragma unroll
+                            for (int r = 1; r < BZ + 3; ++r) sz[r] = mc_half2(Z[r + 1] - Z[r], Z[r] - Z[r - 1]);
+#pragma unroll
+                            for (int f = 0; f <= BZ; ++f)
+                                F[f] = phi2(nh[2], an[2], recZ[(q * (BZ + 1) + f) * TXC + ii], Z[f + 1] + sz[f + 1],
+                                            Z[f + 2] - sz[f + 2], Z[f + 1], Z[f + 2]);
+#pragma unroll
+                            for (int r = 0; r < BZ; ++r) acc[r * BY + q] = fma2(cdx[2], F[r + 1] - F[r], acc[r * BY + q]);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 0; o < NOWN; ++o) {
+                        F2 Ib = same_base ? Ic[o] : ld2((const float *)A.Ibase + (unsigned)(oy[o / BY][o % BY + 2] + i * nd));
+                        putIt(o * TXC + ii, Ib - acc[o]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o)
+#pragma unroll
+                for (int ii = 0; ii < TXC; ++ii)
+                    if (ii < nc) putIt(o * TXC + ii, ld2((const float *)A.Ibase + (unsigned)(oy[o / BY][o % BY + 2] + (i0 + ii) * nd)));
+        }
+    }
+
+    // ---- interaction (section 3.5.2), fluid at rest (as k_stage_fs, FP32 storage)
+    if (warp == 0) {
+        cp_wait_all();
+        int on = 0;
+        if (lc_valid) {
+            double Y = cIn[0][lane], ug = cIn[1][lane], am = cIn[2][lane];
+            on = A.source && A.cc_on[lc_cell] && am > 0.0 && Y > 0.0 && ug > 0.0;
+        }
+        cOn[lane] = on;
+    }
+    {
+        float v[NCELL];
+#pragma unroll
+        for (int c = 0; c < NCELL; ++c) {
+            F2 t = (act && c % TXC < nc) ? getIt(c) * w : f2(0.0f);
+            v[c] = t.x + t.y;
+        }
+        part[warp][0][lane] = transpose_sum(v, lane);
+        if (WANTG) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+#pragma unroll
+                for (int c = 0; c < NCELL; ++c) {
+                    F2 t = (act && c % TXC < nc) ? getIt(c) * w * nh[m] : f2(0.0f);
+                    v[c] = t.x + t.y;
+                }
+                part[warp][1 + m][lane] = transpose_sum(v, lane);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lc_valid) {
+        const size_t cidx = lc_cell;
+        float ce = 0.0f, ci = 1.0f;
+        const double ugm = cIn[1][lane];
+        if (cOn[lane]) {
+            float Emt = 0.0f, Ft[3] = {0.0f, 0.0f, 0.0f};
+            for (int g = 0; g < NW; ++g) Emt += part[g][0][lane];
+            if (WANTG)
+                for (int m = 0; m < 3; ++m)
+                    for (int g = 0; g < NW; ++g) Ft[m] += part[g][1 + m][lane];
+            double Em = (double)Emt, F[3] = {(double)Ft[0], (double)Ft[1], (double)Ft[2]};
+            const double dt = A.dtk, adt = cIn[2][lane] * dt;
+            const double K = adt / (1.0 + adt);
+            const double Y = cIn[0][lane], au = cIn[3][lane], as = cIn[4][lane];
+            const double iY = 1.0 / Y, Tm = ugm * iY;
+            Teq<double> q{K * Em, K * A.sumw * dt * (1.0 / FOURPI), Em + ugm, Y, Tm, Em, au, as,
+                          cIn[5][lane], A.arad, dt, A.T_exp, iY};
+            double X;
+            bool ok = solve_mixed(q, &X);
+            const float Tp = (float)(Tm + (Em - X) * iY);
+            const float aap = (float)au * tpow_neg<float>(Tp, (float)A.T_exp);
+            const float af = (aap + (float)as) * (float)dt;
+            const float cf = (float)dt * ((float)q.eta * aap * (float)A.arad * Tp * Tp * Tp * Tp + (float)as * (float)X) /
+                             (float)FOURPI;
+            const float invf = 1.0f / (1.0f + af);
+            if (!ok) atomicAdd(A.fail, 1ull);
+            ce = cf; ci = invf;
+            const double a = af, c = cf, inv = invf;
+            const double Ep = (Em + c * A.sumw) * inv;
+            const double ugp = ugm - (Ep - Em);
+            A.ug_out[cidx] = ugp;
+            const double T = ugp * iY;
+            A.alpha_out[cidx] = T > 0.0 ? (double)((float)au * tpow_neg<float>((float)T, (float)A.T_exp) + (float)as) : 0.0;
+            if (WANTG && A.G) {
+                const double idt = 1.0 / dt;
+                A.G[4 * cidx] = -(Ep - Em) * idt;
+                for (int m = 0; m < 3; ++m) A.G[4 * cidx + 1 + m] = -((c * A.sumnw[m] - a * F[m]) * inv) * idt;
+            }
+        } else {
+            A.ug_out[cidx] = ugm;
+            A.alpha_out[cidx] = cIn[2][lane];
+            if (WANTG && A.G) for (int m = 0; m < 4; ++m) A.G[4 * cidx + m] = 0.0;
+        }
+        cEm[lane] = ce; cInv[lane] = ci;
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int o = 0; o < NOWN; ++o) {
+            const int q = o % BY, r = o / BY;
+            const size_t base = ((size_t)(k0 + r) * A.nx1 + j0 + q) * A.nx0 + i0;
+#pragma unroll
+            for (int ii = 0; ii < TXC; ++ii) {
+                if (ii < nc) {
+                    const int lc = o * TXC + ii;
+                    F2 v = getIt(lc);
+                    if (cOn[lc]) v = (v + f2(cEm[lc])) * f2(cInv[lc]);
+                    st2((float *)A.Iout + (base + ii) * nd + d0, v);
+                }
+            }
+        }
+    }
+}
+
 template <typename TS, typename TM, int BY, int BZ>
 rt_status launch_fs(rt_ctx *c, const StageArgs &A, int NT) {
     constexpr int TXC = NCELL / (BY * BZ);
@@ -396,7 +725,10 @@ rt_status launch_fs(rt_ctx *c, const StageArgs &A, int NT) {
     bool simple = true;
     for (int a = 0; a < 3; ++a)
         for (int sd = 0; sd < 2; ++sd) simple = simple && (A.bc[a][sd] == RT_BC_PERIODIC || A.bc[a][sd] == RT_BC_OUTFLOW);
-    if (simple) {
+    if (simple && sizeof(TS) == 4 && sizeof(TM) == 4 && A.nd % 2 == 0 && A.nd <= 2 * FP2_NT) {
+        if (A.G) k_stage_fp2<BY, BZ, true><<<(unsigned)nblk, FP2_NT, 0, c->stream>>>(A);
+        else k_stage_fp2<BY, BZ, false><<<(unsigned)nblk, FP2_NT, 0, c->stream>>>(A);
+    } else if (simple) {
         if (A.G) k_stage_fs<TS, TM, BY, BZ, true, true><<<(unsigned)nblk, NT, 0, c->stream>>>(A);
         else k_stage_fs<TS, TM, BY, BZ, false, true><<<(unsigned)nblk, NT, 0, c->stream>>>(A);
     } else {
