@@ -42,7 +42,7 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 # DRAM bytes (read + write) per cell-angle per stage launch, averaged over the
 # two launches of a step, from an ncu capture of the 64^3 box; traffic scales
 # with the cells (each cell is read once per source array and written once)
-NCU_TRAFFIC = {("bcc076464ae9", "fp32", "flat3d"): 10.04}   # {(sha1 of the stage sources, precision, workload): B}
+NCU_TRAFFIC = {("195b76d87513", "fp32", "flat3d"): 10.00}   # {(sha1 of the stage sources, precision, workload): B}
 STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
@@ -322,7 +322,7 @@ def main():
                 "traffic": (traffic * cell_angles if traffic else None),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_per_launch,
                 "avg_launch_ms": avg_launch_s * 1e3,
-                "kernel": ({"fp32": "k_stage_fp2", "bf16": "k_stage_fs", "fp64": "k_stage_fs"}[prec]
+                "kernel": ({"fp32": "k_stage_fp2", "bf16": "k_stage_fp2", "fp64": "k_stage_fs"}[prec]
                            if args.workload == "flat3d" else "k_stage") + " (transport + interaction, fused)"}
 
     # ---- end to end through the public API with pinned host buffers: every
