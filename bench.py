@@ -206,7 +206,7 @@ def main():
     ap.add_argument("--kerr-dims", type=int, nargs=3, default=None, metavar=("NR", "NTH", "NPH"),
                     help="Kerr grid other than the workload's (a smaller case for profiling)")
     ap.add_argument("--ref-cells", type=int, default=32)
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-only", action="store_true",
@@ -326,36 +326,42 @@ def main():
                            if args.workload == "flat3d" else "k_stage") + " (transport + interaction, fused)"}
 
     # ---- end to end through the public API with pinned host buffers: every
-    # step uploads its inputs (I, u_g), steps, and reads its results back.  Two
-    # contexts on two streams take alternate steps (double buffering), so one
-    # step's copies overlap the other's compute, as a serving loop would run.
-    stream2 = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream2):
-        st2 = rt.RadiationStep(grid, cfg, precision=prec, stream=stream2.cuda_stream)
-        st2.set_fluid(*fluid_dev)
-    sts = [st, st2]
-    outs = [(torch.empty_like(I_host).pin_memory(), torch.empty_like(ug_host).pin_memory()) for _ in range(2)]
+    # step uploads its inputs (I, u_g), steps, and reads its results back.
+    # NCTX contexts on NCTX streams take steps in turn (a serving loop with
+    # NCTX batches in flight): while one context's results come back, the
+    # next one's inputs go up and a third one computes, so host->device and
+    # device->host copies and the kernels overlap.
+    NCTX = 3
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(NCTX - 1)]
+    sts = [st]
+    for q in range(1, NCTX):
+        with torch.cuda.stream(streams[q]):
+            sq = rt.RadiationStep(grid, cfg, precision=prec, stream=streams[q].cuda_stream)
+            sq.set_fluid(*fluid_dev)
+        sts.append(sq)
+    outs = [(torch.empty_like(I_host).pin_memory(), torch.empty_like(ug_host).pin_memory()) for _ in range(NCTX)]
     out_I, out_ug = outs[0]
-    for q in range(2):
+    for q in range(NCTX):
         sts[q].set_intensity(I_host); sts[q].set_ugas(ug_host); sts[q].step(dt, 1)
         sts[q].get_intensity(outs[q][0]); sts[q].get_ugas(outs[q][1])
     torch.cuda.synchronize(dev)
     barrier()
-    E = max(2, args.e2e_steps)
+    E = max(NCTX, args.e2e_steps)
     t0 = time.perf_counter()
-    for k in range(E + 1):
+    for k in range(E + NCTX - 1):
         if k < E:
-            q = k % 2
+            q = k % NCTX
             sts[q].set_intensity(I_host)
             sts[q].set_ugas(ug_host)
             sts[q].step(dt, 1)
-        if k >= 1:
-            q = (k - 1) % 2
+        kr = k - (NCTX - 1)
+        if kr >= 0:
+            q = kr % NCTX
             sts[q].get_intensity(outs[q][0])   # host buffer: waits for that context's stream
             sts[q].get_ugas(outs[q][1])
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    del st2
+    del sts[1:]
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -390,7 +396,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "steps": E, "mode": "pinned host buffers; 2 contexts on 2 streams take alternate steps"},
+                    "steps": E, "mode": "pinned host buffers; %d contexts on %d streams take steps in turn" % (NCTX, NCTX)},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
