@@ -42,7 +42,7 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 # DRAM bytes (read + write) per cell-angle per stage launch, averaged over the
 # two launches of a step, from an ncu capture of the 64^3 box; traffic scales
 # with the cells (each cell is read once per source array and written once)
-NCU_TRAFFIC = {("195b76d87513", "fp32", "flat3d"): 10.00}   # {(sha1 of the stage sources, precision, workload): B}
+NCU_TRAFFIC = {("70b1281b85a6", "fp32", "flat3d"): 9.99}   # {(sha1 of the stage sources, precision, workload): B}
 STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
@@ -124,6 +124,16 @@ def cpu_oracle_rate(n_cells, n_geo, steps):
     el = time.perf_counter() - t0
     nd = 10 * n_geo * n_geo + 2
     return n_cells ** 3 * nd * steps / el, el
+
+
+def max_over_ranks(x, dist=None):
+    """The slowest rank's time (replicas: the job ends when the last rank does)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def run_reference(args, world, rank):
@@ -301,10 +311,7 @@ def main():
     stage_ms, launches = st.get_timing()
     st.set_timing(False)
     barrier()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     ms_per_step = ms / args.steps
     cell_angles = ncell * nd
     value = world * cell_angles * args.steps / (ms * 1e-3)
@@ -362,10 +369,7 @@ def main():
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     del sts[1:]
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     e2e_value = world * cell_angles * E / e2e_s
     h2d = I_host.numel() * I_host.element_size() + ug_host.numel() * 8
     d2h = out_I.numel() * out_I.element_size() + out_ug.numel() * 8

@@ -463,6 +463,10 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
     __shared__ int cOn[NCELL];
     __shared__ double cIn[6][NCELL];
     __shared__ __align__(8) float sIt[NCELL][2 * FP2_NT];
+    // one x1 position ahead: the own rows' next values and, for the corrector,
+    // the base intensities (both first reads from HBM), copied asynchronously
+    constexpr bool PFX = sizeof(TS) == 4;
+    __shared__ __align__(8) float pfb[2][2 * NOWN][PFX ? 2 * FP2_NT : 2];
 
     const int nd = A.nd, NT = blockDim.x, p = threadIdx.x, lane = p & 31, warp = p >> 5;
     const int d0 = 2 * p;
@@ -547,6 +551,21 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
 #pragma unroll
             for (int r = 0; r < BZ + 4; ++r) oz[q][r] = roff(rowZ[q * (BZ + 4) + r]);
         const bool same_base = A.Isrc == A.Ibase;
+        auto cp8 = [&](float *dst, const TS *src) {
+            unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+        };
+        auto pf_issue = [&](int ii) {
+            if constexpr (PFX) {
+                const int st = ii & 1, i = i0 + ii;
+#pragma unroll
+                for (int o = 0; o < NOWN; ++o) {
+                    if (A.act0) cp8(&pfb[st][o][d0], Isrc + (unsigned)(oy[o / BY][o % BY + 2] + (xmap[ii + 4] & F_MASK) * nd));
+                    if (!same_base) cp8(&pfb[st][NOWN + o][d0], (const TS *)A.Ibase + (unsigned)(oy[o / BY][o % BY + 2] + i * nd));
+                }
+            }
+        };
+        auto pf_get = [&](int st, int k) -> F2 { return F2{pfb[st][k][d0], pfb[st][k][d0 + 1]}; };
         if (A.transport) {
             F2 W0[NOWN], W1[NOWN], S0[NOWN], Flo[NOWN];
 #pragma unroll
@@ -561,10 +580,17 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
                     W0[o] = I0; W1[o] = I1; S0[o] = s0;
                 }
             }
+            if (PFX) { pf_issue(0); cp_commit_all(); }
 #pragma unroll
             for (int ii = 0; ii < TXC; ++ii) {
                 if (ii < nc) {
                     const int i = i0 + ii;
+                    const int pst = ii & 1;
+                    if (PFX) {
+                        if (ii + 1 < nc) pf_issue(ii + 1);
+                        cp_commit_all();
+                        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+                    }
                     F2 acc[NOWN], Ic[NOWN];
 #pragma unroll
                     for (int o = 0; o < NOWN; ++o) {
@@ -575,7 +601,7 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
 #pragma unroll
                         for (int o = 0; o < NOWN; ++o) {
                             const int q = o % BY, r = o / BY;
-                            F2 I2 = ldx(oy[r][q + 2], xmap[ii + 4]);
+                            F2 I2 = PFX ? pf_get(pst, o) : ldx(oy[r][q + 2], xmap[ii + 4]);
                             F2 s1 = mc_half2(I2 - W1[o], W1[o] - W0[o]);
                             F2 phi = phi2(nh[0], an[0], recX[o * (TXC + 1) + ii + 1], W0[o] + S0[o], W1[o] - s1, W0[o], W1[o]);
                             acc[o] = fma2(cdx[0], phi - Flo[o], acc[o]);
@@ -616,7 +642,8 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
                     }
 #pragma unroll
                     for (int o = 0; o < NOWN; ++o) {
-                        F2 Ib = same_base ? Ic[o] : ld2((const TS *)A.Ibase + (unsigned)(oy[o / BY][o % BY + 2] + i * nd));
+                        F2 Ib = same_base ? Ic[o]
+                                : (PFX ? pf_get(pst, NOWN + o) : ld2((const TS *)A.Ibase + (unsigned)(oy[o / BY][o % BY + 2] + i * nd)));
                         putIt(o * TXC + ii, Ib - acc[o]);
                     }
                 }
