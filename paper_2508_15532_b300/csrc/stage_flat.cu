@@ -466,6 +466,9 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
     // one x1 position ahead: the own rows' next values and, for the corrector,
     // the base intensities (both first reads from HBM), copied asynchronously
     constexpr bool PFX = sizeof(TS) == 4;
+    // unrolling of the x1 loop; measured at 128^3 x 162: FP32 storage runs
+    // 13% faster unrolled by 4 than fully, BF16 storage 10% slower
+    constexpr int XUNROLL = PFX ? 4 : TXC;
     __shared__ __align__(8) float pfb[2][2 * NOWN][PFX ? 2 * FP2_NT : 2];
 
     const int nd = A.nd, NT = blockDim.x, p = threadIdx.x, lane = p & 31, warp = p >> 5;
@@ -581,7 +584,7 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
                 }
             }
             if (PFX) { pf_issue(0); cp_commit_all(); }
-#pragma unroll
+#pragma unroll XUNROLL
             for (int ii = 0; ii < TXC; ++ii) {
                 if (ii < nc) {
                     const int i = i0 + ii;
