@@ -161,13 +161,16 @@ rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G);
  * reverse of section 3.6's predictor-corrector, eq. radiative_transfer_discrete
  * with eqs. rad_speeds / flux_Jiang, and method 3 of section 3.5.2 (implicit
  * function theorem at the temperature root).  The forward is recomputed from
- * the checkpoint into a library-owned arena of about (4 nsteps + 2) intensity
- * arrays (order 2; 2 nsteps + 2 for order 1), kept for the next call.  With
- * FP64 intensities the reverse pass is FP64 throughout; with FP32 intensities
- * (I_ckpt in FP32) the recompute is stored in FP32 and the per-element reverse
- * arithmetic is FP32, while per-cell sums and every cotangent stay FP64.
+ * the checkpoint by the stage kernels of rt_step into a library-owned arena of
+ * (2 nsteps + 3) intensity arrays (order 2; nsteps + 3 for order 1) plus a few
+ * per-cell arrays per stage, kept for the next call; the reverse then takes
+ * one kernel per stage.  With FP64 intensities the reverse pass is FP64
+ * throughout; with FP32 intensities (I_ckpt in FP32) the recompute is stored
+ * in FP32 and the per-element reverse arithmetic and intensity cotangents are
+ * FP32, while per-cell sums and per-cell cotangents stay FP64.
  * Scope: flat Cartesian geometry, fluid at rest, FP64 or FP32 intensities,
- * periodic (>= 4 cells) or outflow boundaries; anything else is RT_EINVAL.
+ * at most 192 directions, periodic (>= 4 cells) or outflow boundaries;
+ * anything else is RT_EINVAL.
  * All pointers are device pointers; dL_dI_in may alias dL_dI_out.
  * Stream-ordered. */
 rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,

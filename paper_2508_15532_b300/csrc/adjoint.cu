@@ -5,43 +5,142 @@
 // section 3.5.2).
 //
 // One call reverses nsteps steps from a checkpoint (I^0, u_g^0):
-//  1. forward recompute: every stage's transported intensities (the stage
-//     kernel with the interaction switched off) and the interaction applied to
-//     them, all kept in a library-owned arena;
-//  2. reverse sweep, per stage from the last: the interaction adjoint (the
-//     explicit pieces in reverse and the implicit function theorem at the
-//     temperature root), then the transport adjoint, a gather over the faces
-//     whose fluxes read each cell, with the limiter branches of the forward
-//     state and the optical-depth dependence of the face coefficients, which
-//     carries gradient into kappa and u_g through the opacity.
+//  1. forward recompute with the ordinary stage kernels, which also save each
+//     cell's E-bar_- and temperature root X; every stage's input intensities,
+//     gas energies and opacities are kept in a library-owned arena;
+//  2. reverse sweep, one kernel per stage (k_rev): the transport adjoint of
+//     the stage, computed face by face (each face's flux derivatives once,
+//     each cell's limited slope and its derivatives once), fused with the
+//     interaction adjoint of the stage before it, whose output is this
+//     stage's input.  The interaction adjoint is written in terms of its
+//     output I_+ = (I_* + c)/(1 + a), so I_* is never stored, and its root
+//     enters through the implicit function theorem.
 #include "stage_common.cuh"
+#include "f32x2.cuh"
 #include <algorithm>
 
 using namespace rtk;
 
 namespace {
 
-constexpr int ADJ_NT = 192;   // threads of a block = directions (n_dir <= 192)
-constexpr int TXA = 8;        // cells per transport-adjoint block along x1
-constexpr int NFACE = 9 * TXA + 3;
+// ------------------------------------------------------------ lane types
+// FP32 pass: a thread owns two adjacent directions (n_dir is even) and works
+// on both with f32x2 arithmetic.  FP64 pass: one direction per thread.
+__device__ __forceinline__ double fma2(double a, double b, double c) { return fma(a, b, c); }
 
-// ------------------------------------------------------------ interaction
-struct SrcArgs {
-    int ncell, nd, source;
-    double dtk, sumw, T_exp, arad, rho_exp;
-    const double *w, *ug_in, *cc_au, *cc_as, *cc_Y, *eta, *rho, *kap;
-    const void *I;                           // storage type of the context
-    const uint8_t *cc_on;
-    void *I_out;                             // forward (storage type)
-    double *ug_out;
-    const void *Ibo;                         // reverse: cotangent of the output intensities (type R)
-    const double *ubo;                       // cotangent of the output u_g
-    void *Ibi;                               // cotangent of I (written, type R)
-    double *ubi;                             // cotangent of u_g entering (ub_acc: added)
-    int ub_acc;
-    double *kb, *eb;                         // added
-    unsigned long long *fail;
+struct LaneF {
+    using S = float;
+    using V = F2;
+    static constexpr int L = 2, NT = 96, MINB = 4;
+    __device__ static V splat(float a) { return f2(a); }
+    __device__ static V ld(const float *p) { float2 v = __ldg(reinterpret_cast<const float2 *>(p)); return F2{v.x, v.y}; }
+    __device__ static void st(float *p, V v) { *reinterpret_cast<float2 *>(p) = make_float2(v.x, v.y); }
+    __device__ static void st64(double *p, V v) { *reinterpret_cast<double2 *>(p) = make_double2(v.x, v.y); }
+    __device__ static float hsum(V v) { return v.x + v.y; }
+    __device__ static V vabs(V v) { return F2{fabsf(v.x), fabsf(v.y)}; }
+    __device__ static V dirv(const double *dir, int d, int a) { return F2{(float)dir[3 * d + a], (float)dir[3 * d + 3 + a]}; }
+    __device__ static V wv(const double *w, int d) { return F2{(float)w[d], (float)w[d + 1]}; }
 };
+struct LaneD {
+    using S = double;
+    using V = double;
+    static constexpr int L = 1, NT = 192, MINB = 2;
+    __device__ static V splat(double a) { return a; }
+    __device__ static V ld(const double *p) { return __ldg(p); }
+    __device__ static void st(double *p, V v) { *p = v; }
+    __device__ static void st64(double *p, V v) { *p = v; }
+    __device__ static double hsum(V v) { return v; }
+    __device__ static V vabs(V v) { return fabs(v); }
+    __device__ static V dirv(const double *dir, int d, int a) { return dir[3 * d + a]; }
+    __device__ static V wv(const double *w, int d) { return w[d]; }
+};
+
+// Half of the limited slope, hs = s/2 (the reconstruction offset of eq.
+// radiative_transfer_discrete's face states), and its derivatives in the
+// forward difference dl = I_{p+1} - I_p and the backward difference
+// dr = I_p - I_{p-1}.  Values as rtk::limiter / 2 (halving is exact).  The
+// branch taken at ties follows the MC rule of the forward scan: 2|dl| first,
+// 2|dr| only when strictly smaller, (dl + dr)/2 only when strictly below both.
+// Every kind has zero derivatives where dl dr <= 0 (in particular where one
+// difference is zero), which the outflow ghost folding below relies on.
+template <typename S> __device__ __forceinline__ void lim_half(int kind, S dl, S dr, S &hs, S &gl, S &gr) {
+    const S al = fabs(dl), ar = fabs(dr);
+    const bool ok = dl * dr > S(0);
+    if (kind == RT_LIM_MC) {
+        const S q = S(0.25) * fabs(dl + dr);
+        const bool w1 = ar < al;                    // |dr| strictly smaller
+        const S m1 = w1 ? ar : al;
+        const bool w2 = q < m1;
+        const S m = w2 ? q : m1;
+        hs = ok ? copysign(m, dl) : S(0);
+        gl = ok ? (w2 ? S(0.25) : (w1 ? S(0) : S(1))) : S(0);
+        gr = ok ? (w2 ? S(0.25) : (w1 ? S(1) : S(0))) : S(0);
+    } else if (kind == RT_LIM_MINMOD) {
+        const bool wl = al < ar;
+        hs = ok ? copysign(S(0.5) * (wl ? al : ar), dl) : S(0);
+        gl = (ok && wl) ? S(0.5) : S(0);
+        gr = (ok && !wl) ? S(0.5) : S(0);
+    } else {
+        hs = S(0); gl = S(0); gr = S(0);
+    }
+}
+__device__ __forceinline__ void limv(int kind, F2 dl, F2 dr, F2 &hs, F2 &gl, F2 &gr) {
+    lim_half<float>(kind, dl.x, dr.x, hs.x, gl.x, gr.x);
+    lim_half<float>(kind, dl.y, dr.y, hs.y, gl.y, gr.y);
+}
+__device__ __forceinline__ void limv(int kind, double dl, double dr, double &hs, double &gl, double &gr) {
+    lim_half<double>(kind, dl, dr, hs, gl, gr);
+}
+
+// Face record of the exponentially cut flux (eqs. rad_speeds, flux_Jiang):
+// with (cL, cR) = (c1, c2) for n > 0 and (c2, c1) for n < 0,
+//   n cL = n P + |n| D,  n cR = n P - |n| D,  P = (c1 + c2)/2, D = (c1 - c2)/2,
+// and the same for the derivatives in tau.  Stored: P, D, -D, c3, dP, dD, -dc3.
+template <typename S> __device__ void face_record(S tau, S *r) {
+    S c1, c2, c3, d1, d2, d3;
+    if (tau > S(0)) {
+        const S t2 = tau * tau, t4 = t2 * t2;
+        const S F = -expm1(-t2), G = -expm1(-t4);
+        const S f = sqrt(F) / tau, g = sqrt(G) / tau, e = exp(-tau), Sg = f + g;
+        const S fp = exp(-t2) / sqrt(F) - f / tau;
+        const S gp = G > S(0) ? S(2) * t2 * exp(-t4) / sqrt(G) - g / tau : S(1);
+        const S ep = -e, Sp = fp + gp, iS2 = S(1) / (Sg * Sg);
+        c1 = f * e / Sg; c2 = g * e / Sg; c3 = f * g / Sg;
+        d1 = ((fp * e + f * ep) * Sg - f * e * Sp) * iS2;
+        d2 = ((gp * e + g * ep) * Sg - g * e * Sp) * iS2;
+        d3 = ((fp * g + f * gp) * Sg - f * g * Sp) * iS2;
+    } else {
+        c1 = S(1); c2 = S(0); c3 = S(0);
+        d1 = S(-2); d2 = S(1); d3 = S(1);
+    }
+    r[0] = S(0.5) * (c1 + c2); r[1] = S(0.5) * (c1 - c2); r[2] = -r[1]; r[3] = c3;
+    r[4] = S(0.5) * (d1 + d2); r[5] = S(0.5) * (d1 - d2); r[6] = -d3; r[7] = S(0);
+}
+
+// cotangents of a face's states from the cotangent phib of its flux:
+// ILb = phib n cL, IRb = phib n cR, c3t = phib |n| c3
+template <typename V> struct FaceCot { V ILb, IRb, c3t; };
+template <class LT>
+__device__ __forceinline__ FaceCot<typename LT::V> face_cot(typename LT::V phib, typename LT::V n, typename LT::V an,
+                                                           const typename LT::S *r) {
+    using V = typename LT::V;
+    const V nP = n * LT::splat(r[0]);
+    const V ncL = fma2(an, LT::splat(r[1]), nP), ncR = fma2(an, LT::splat(r[2]), nP);
+    return FaceCot<V>{phib * ncL, phib * ncR, phib * (an * LT::splat(r[3]))};
+}
+// d flux / d tau times phib, for face states IL, IR and cells Il, Ir:
+// phib (n dcL IL + n dcR IR - |n| dc3 (Ir - Il))
+template <class LT>
+__device__ __forceinline__ typename LT::V face_tau(typename LT::V phib, typename LT::V n, typename LT::V an,
+                                                   typename LT::V IL, typename LT::V IR, typename LT::V dI,
+                                                   const typename LT::S *r) {
+    using V = typename LT::V;
+    V u = LT::splat(r[5]) * (IL - IR);
+    u = fma2(LT::splat(r[6]), dI, u);
+    V v = an * u;
+    v = fma2(n * LT::splat(r[4]), IL + IR, v);
+    return phib * v;
+}
 
 // rho^m = (kappa rho^m) / kappa, the derivative of alpha^a's prefactor in
 // kappa, without an FP64 pow where kappa is nonzero
@@ -49,568 +148,506 @@ __device__ __forceinline__ double rho_m(double au, double kap, double rho, doubl
     return kap != 0.0 ? au / kap : pow(rho, m);
 }
 
-// N (16 or 32) values per lane -> lane l holds the warp sum of value l % N
-template <int N, typename R> __device__ __forceinline__ R tsum(R (&v)[N], int lane) {
+// Reverse of the interaction of section 3.5.2 (method 3) in one cell at rest,
+// from its output: I_+ = (I_* + c)/A in every direction, A = 1 + a,
+// E-bar_+ = sum w I_+, u_g+ = u_g- - (E-bar_+ - E-bar_-), with a = alpha(T_+) dt,
+// c = dt (eta alpha^a(T_+) a_R T_+^4 + alpha^s X)/(4 pi), T_+ = T_- + (E-bar_- - X)/Y
+// and X the root of h(X; B1, B2, T_-, E-bar_-) = 0 (B1 = K E-bar_-,
+// B2 = K sum w dt/(4 pi), K = alpha(T_-) dt / (1 + alpha(T_-) dt)).
+// Given P = sum Ibo, Q = sum Ibo I_+ (Ibo: cotangent of I_+) and ub (cotangent
+// of u_g+), the cotangent of I_* in direction s is (Ibo_s - ub w_s) inv + Emb w_s.
+struct SrcRev { double inv, ub, Emb, ugb, kb, eb; };
+__device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, double eta, double kap, double rho,
+                          double Em, double X, double P, double Q, double ub, double dt, double S, double p,
+                          double ar, double rho_exp) {
+    SrcRev o{1.0, 0.0, 0.0, ub, 0.0, 0.0};
+    if (!on) return o;
+    constexpr double i4pi = 1.0 / FOURPI;
+    const double iY = 1.0 / Y, Tm = ugm * iY;
+    const double tm = tpow_neg<double>(Tm, p), am = au * tm + as;
+    const double adt = am * dt, i1a = 1.0 / (1.0 + adt), K = adt * i1a, B2 = K * S * dt * i4pi;
+    const double Tp = Tm + (Em - X) * iY;
+    const double tp = tpow_neg<double>(Tp, p), aap = au * tp;
+    const double Tp4 = Tp * Tp * Tp * Tp;
+    const double a = (aap + as) * dt;
+    const double cc = dt * (eta * aap * ar * Tp4 + as * X) * i4pi;
+    const double inv = 1.0 / (1.0 + a);
+    const double Ep = (Em + cc * S) * inv;
+    const double sIpb = P - ub * S;                 // sum_s Ipb_s, Ipb_s = Ibo_s - ub w_s
+    const double ccb = sIpb * inv;
+    const double Ab = -(Q - ub * Ep) * inv;         // d/dA of sum_s Ipb_s I_+s = -sum_s Ipb_s I_+s / A
+    double aapb = Ab * dt;
+    // 1/T without a division for p = 3.5: T^2 sqrt(T) T^-3.5
+    const double iTp = p == 3.5 ? Tp * Tp * sqrt(Tp) * tp : 1.0 / Tp;
+    const double ccbd = ccb * dt * i4pi;
+    double etab = ccbd * aap * ar * Tp4;
+    aapb += ccbd * eta * ar * Tp4;
+    double Tpb = ccbd * eta * aap * ar * 4.0 * Tp * Tp * Tp;
+    double Xb = ccbd * as;
+    double aub = aapb * tp;
+    Tpb += aapb * (-p) * aap * iTp;
+    double Tmb = Tpb, Emb = ub + Tpb * iY;
+    Xb -= Tpb * iY;
+    // the root: h(X) = (alpha(T_+) dt - B2 alpha^s) X - B1 - B2 eta alpha^a(T_+) a_R T_+^4
+    const double lin = (aap + as) * dt - B2 * as;
+    const double hT = -p * aap * iTp * dt * X - B2 * eta * ar * (4.0 - p) * aap * Tp * Tp * Tp;
+    const double hX = lin - hT * iY;
+    const double lam = -Xb / hX;
+    const double B1b = -lam;
+    const double B2b = lam * (-as * X - eta * ar * aap * Tp4);
+    Tmb += lam * hT;
+    Emb += lam * hT * iY;
+    aub += lam * (tp * dt * X - B2 * eta * ar * tp * Tp4);
+    etab += lam * (-B2 * ar * aap * Tp4);
+    const double Kb = B2b * S * dt * i4pi + B1b * Em;
+    Emb += B1b * K;
+    const double amb = Kb * dt * i1a * i1a;
+    aub += amb * tm;
+    Tmb += amb * (-p) * au * tm * (p == 3.5 ? Tm * Tm * tm * sqrt(Tm) : 1.0 / Tm);
+    o.inv = inv; o.ub = ub; o.Emb = Emb;
+    o.ugb = ub + Tmb * iY;
+    o.kb = aub * rho_m(au, kap, rho, rho_exp);
+    o.eb = etab;
+    return o;
+}
+
+// N values per lane -> every lane l holds the warp sum of value l % N
+// (N a power of two <= 32; N - 1 + 5 - log2 N shuffles)
+template <int N, typename R> __device__ __forceinline__ R tsum_n(R (&v)[N], int lane) {
 #pragma unroll
     for (int n = N / 2; n >= 1; n >>= 1) {
         const bool hi = (lane & n) != 0;
 #pragma unroll
         for (int i = 0; i < n; ++i) {
-            R keep = hi ? v[i + n] : v[i];
-            R send = hi ? v[i] : v[i + n];
+            const R keep = hi ? v[i + n] : v[i], send = hi ? v[i] : v[i + n];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, n);
         }
     }
-    if (N == 16) return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+#pragma unroll
+    for (int m = N; m < 32; m <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
     return v[0];
 }
 
-// cells per interaction block (one lane of warp 0 per cell in the solve):
-// 32 for the FP32 pass, 16 for FP64 (register arrays of 16 doubles)
-template <typename R> struct CellsPerBlock { static constexpr int v = sizeof(R) == 4 ? 32 : 16; };
+// ------------------------------------------------------ reverse stage kernel
+constexpr int RNC = 32;                        // cells per CTA: a TXC x BY x BZ brick
+constexpr int F_OUT = 1 << 30, F_IDX = F_OUT - 1;   // index flag: ghost beyond an outflow boundary
 
-// REV = false: I_out = interaction(I), u_g out.  REV = true: the reverse.
-// R is the storage and per-element arithmetic type of intensities and their
-// cotangents (FP64, or FP32 for the mixed pass); warp partial sums are in R,
-// the sums over warps and the per-cell arithmetic in FP64.
-template <bool REV, typename R>
-__global__ void __launch_bounds__(ADJ_NT) k_src(const SrcArgs A) {
-    constexpr int SC = CellsPerBlock<R>::v;
-    constexpr int NW = ADJ_NT / 32;
-    __shared__ double part[NW][3][SC];
-    __shared__ double sh_a[SC], sh_b[SC], sh_c[SC];
-    __shared__ int sh_on[SC];
-    const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
-    const bool act = s < A.nd;
-    const size_t c0 = (size_t)blockIdx.x * SC;
-    const int nc = (int)min((size_t)SC, (size_t)A.ncell - c0);
-    const R w = act ? (R)A.w[s] : R(0);
-    const R *Isrc = (const R *)A.I, *Bsrc = (const R *)A.Ibo;
-    R Iv[SC], Bv[SC], v[SC];
-#pragma unroll
-    for (int k = 0; k < SC; ++k) Iv[k] = (act && k < nc) ? __ldg(Isrc + (c0 + k) * A.nd + s) : R(0);
-    if (REV) {
-#pragma unroll
-        for (int k = 0; k < SC; ++k) Bv[k] = (act && k < nc) ? __ldg(Bsrc + (c0 + k) * A.nd + s) : R(0);
-    }
-#pragma unroll
-    for (int k = 0; k < SC; ++k) v[k] = Iv[k] * w;
-    R r0 = tsum<SC, R>(v, lane);
-    if (lane < SC) part[warp][0][lane] = (double)r0;
-    if (REV) {
-#pragma unroll
-        for (int k = 0; k < SC; ++k) v[k] = Bv[k];
-        R r1 = tsum<SC, R>(v, lane);
-#pragma unroll
-        for (int k = 0; k < SC; ++k) v[k] = Bv[k] * Iv[k];
-        R r2 = tsum<SC, R>(v, lane);
-        if (lane < SC) { part[warp][1][lane] = (double)r1; part[warp][2][lane] = (double)r2; }
-    }
-    __syncthreads();
-    if (warp == 0 && lane < SC) {
-        int on = 0;
-        double a0 = 0.0, b0 = 0.0, cc0 = 0.0;
-        if (lane < nc) {
-            const size_t c = c0 + lane;
-            const double Y = A.cc_Y[c], ugm = A.ug_in[c], au = A.cc_au[c], as = A.cc_as[c];
-            // FP64 divisions are costly on this part: reciprocals once per cell
-            const double iY = Y > 0.0 ? 1.0 / Y : 0.0, Tm = ugm * iY;
-            const double tm = Tm > 0.0 ? tpow_neg<double>(Tm, A.T_exp) : 0.0;
-            const double am = (A.cc_on[c] && Tm > 0.0) ? au * tm + as : 0.0;
-            on = A.source && A.cc_on[c] && am > 0.0 && Y > 0.0 && ugm > 0.0;
-            const double ub = (REV && A.ubo) ? A.ubo[c] : 0.0;
-            if (on) {
-                double Em = 0.0, P = 0.0, Q = 0.0;
-                for (int g = 0; g < NW; ++g) Em += part[g][0][lane];
-                if (REV)
-                    for (int g = 0; g < NW; ++g) { P += part[g][1][lane]; Q += part[g][2][lane]; }
-                constexpr double i4pi = 1.0 / FOURPI;
-                const double dt = A.dtk, adt = am * dt, i1a = 1.0 / (1.0 + adt), K = adt * i1a, S = A.sumw;
-                const double eta = A.eta[c], p = A.T_exp, ar = A.arad;
-                Teq<double> q{K * Em, K * S * dt * i4pi, Em + ugm, Y, Tm, Em, au, as, eta, ar, dt, p, iY};
-                double X, lo = 0.0, hi = q.W;
-                bool ok;
-                if constexpr (sizeof(R) == 4) ok = solve_mixed(q, &X);   // as the FP32 forward solves it
-                else ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
-                if (!ok && A.fail) atomicAdd(A.fail, 1ull);
-                const double Tp = Tm + (Em - X) * iY;
-                const double tp = tpow_neg<double>(Tp, p), aap = au * tp;
-                const double Tp4 = Tp * Tp * Tp * Tp;
-                const double a = (aap + as) * dt;
-                const double cc = dt * (eta * aap * ar * Tp4 + as * X) * i4pi;
-                const double inv = 1.0 / (1.0 + a);
-                if (!REV) {
-                    const double Ep = (Em + cc * S) * inv;
-                    A.ug_out[c] = ugm - (Ep - Em);
-                    a0 = cc; b0 = inv;
-                } else {
-                    // I_+ = (I + cc)/A, E_+ = sum w I_+, u_g+ = u_g - (E_+ - E_-)
-                    const double sIpb = P - ub * S;                 // sum_s Ipb_s, Ipb_s = Ibo_s - ub w_s
-                    const double sIpbI = Q - ub * Em;               // sum_s Ipb_s I_s
-                    const double ccb = sIpb * inv;
-                    const double Ab = -(sIpbI + cc * sIpb) * inv * inv;
-                    double aapb = Ab * dt;
-                    // 1/Tp without a division for p = 3.5: Tp^2 sqrt(Tp) Tp^-3.5
-                    const double iTpx = p == 3.5 ? Tp * Tp * sqrt(Tp) * tp : 1.0 / Tp;
-                    const double ccbd = ccb * dt * i4pi;
-                    double etab = ccbd * aap * ar * Tp4;
-                    aapb += ccbd * eta * ar * Tp4;
-                    double Tpb = ccbd * eta * aap * ar * 4.0 * Tp * Tp * Tp;
-                    double Xb = ccbd * as;
-                    double aub = aapb * tp;
-                    Tpb += aapb * (-p) * aap * iTpx;
-                    double Tmb = Tpb, Emb = ub + Tpb * iY;
-                    Xb -= Tpb * iY;
-                    // root of h(X; B1, B2, T_-, E_-, au, eta) = 0
-                    const double lin = (aap + as) * dt - q.B2 * as;
-                    const double hT = -p * aap * iTpx * dt * X - q.B2 * eta * ar * (4.0 - p) * aap * Tp * Tp * Tp;
-                    const double hX = lin - hT * iY;
-                    const double lam = -Xb / hX;
-                    const double B1b = -lam;
-                    const double B2b = lam * (-as * X - eta * ar * aap * Tp4);
-                    Tmb += lam * hT;
-                    Emb += lam * hT * iY;
-                    aub += lam * (tp * dt * X - q.B2 * eta * ar * tp * Tp4);
-                    etab += lam * (-q.B2 * ar * aap * Tp4);
-                    const double Kb = B2b * S * dt * i4pi + B1b * Em;
-                    Emb += B1b * K;
-                    const double amb = Kb * dt * i1a * i1a;
-                    aub += amb * tm;
-                    Tmb += amb * (-p) * au * tm * (p == 3.5 ? Tm * Tm * tm * sqrt(Tm) : 1.0 / Tm);
-                    const double ugb = ub + Tmb * iY;
-                    A.ubi[c] = A.ub_acc ? A.ubi[c] + ugb : ugb;
-                    A.kb[c] += aub * rho_m(au, A.kap[c], A.rho[c], A.rho_exp);
-                    A.eb[c] += etab;
-                    a0 = inv; b0 = ub; cc0 = Emb;
-                }
-            } else {
-                if (!REV) A.ug_out[c] = ugm;
-                else A.ubi[c] = A.ub_acc ? A.ubi[c] + ub : ub;
-            }
-        }
-        sh_on[lane] = on; sh_a[lane] = a0; sh_b[lane] = b0; sh_c[lane] = cc0;
-    }
-    __syncthreads();
-    if (!act) return;
-#pragma unroll
-    for (int k = 0; k < SC; ++k) {
-        if (k >= nc) break;
-        const size_t i = (c0 + k) * A.nd + s;
-        if (!REV) ((R *)A.I_out)[i] = sh_on[k] ? (Iv[k] + (R)sh_a[k]) * (R)sh_b[k] : Iv[k];
-        else ((R *)A.Ibi)[i] = sh_on[k] ? (Bv[k] - (R)sh_b[k] * w) * (R)sh_a[k] + (R)sh_c[k] * w : Bv[k];
-    }
-}
-
-// --------------------------------------------------------------- transport
-struct TrArgs {
-    int nx[3], act[3], per[3], nd, limiter, tau_dt;
-    double dx[3], abar, dtk, T_exp, rho_exp;
-    double coef[3], hl[3];                   // dtk/dx_a, and d tau/d alpha of one side of an a-face
-    const double *dir, *alpha;
-    const void *I;                           // intensities (type R)
-    const void *Ibo;                         // cotangent of the stage output (type R)
-    void *out_src, *base_out;                // cotangents written (type R)
-    int src_acc, add_base;
-    const double *ug, *cc_au, *cc_Y, *rho, *kap;
+// One stage of the reverse sweep.  The stage maps its input I to
+// base - dtk div F(I) (eq. radiative_transfer_discrete; base = I for the
+// predictor and for first-order steps, I^n for the corrector); Zg is the
+// cotangent of that transported state.  The kernel forms, per own element,
+//   Ibar = sum over faces of Zg's flux cotangents through dF/dI  (+ Zg if the
+//          base is the input) (+ Zown),
+// and the opacity cotangent of every own cell (the face coefficients depend
+// on tau = abar alpha len).  FUSE: the stage before this one ended with an
+// interaction whose output is I; its reverse (src_rev) turns Ibar into the
+// cotangent of that interaction's input, written to Zout.  Otherwise Ibar is
+// written to Zout.  Cotangents of the gas energies and of kappa and eta go
+// to per-cell arrays.
+struct RevArgs {
+    int nx[3], act[3], per[3], nd, limiter, transport, source;
+    int add_base;                 // the stage's base intensities are its input
+    int out_f64;                  // !FUSE: Zout is FP64 whatever the storage type
+    int ub_dst_acc;               // FUSE: add to ub_dst instead of writing it
+    double coef[3];               // dtk / dx_a
+    double hl[3];                 // d tau / d alpha of one side of an a-face: abar len_a / 2
+    double taulen[3];             // the length in tau: dtk (tau_dt) or dx_a
+    double abar, dts, sumw, T_exp, arad, rho_exp;
+    const double *dir, *w;        // [3 nd], [nd]
+    const void *I;                // stage input (storage type)
+    const void *Zg;               // cotangent of the transported state (storage type)
+    const void *Zown;             // extra cotangent of I at own elements, or null
+    void *Zout;
+    const double *alpha;          // opacity of the stage's faces
+    const double *ug_a;           // the gas energy that alpha belongs to
+    const double *ubA;            // cotangent of ug_a gathered so far, or null
+    double *ubA_out;              // !FUSE: the complete cotangent of ug_a, or null
+    const double *ugm, *Em, *X;   // FUSE: the interaction's gas energy in, saved E-bar_- and root
+    double *ub_dst;               // FUSE: cotangent of ugm
+    double *kb, *eb;              // added
+    const double *cc_au, *cc_as, *cc_Y, *kap, *rho, *eta;
     const uint8_t *cc_on;
-    double *ub, *kb;
-    int ub_acc;
 };
 
-__device__ __forceinline__ int amap(int q, int n, int per) {
-    if (q >= 0 && q < n) return q;
-    if (per) return ((q % n) + n) % n;
-    return q < 0 ? 0 : n - 1;
-}
+template <class LT, int BY, int BZ, bool FUSE>
+__global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
+    using S = typename LT::S;
+    using V = typename LT::V;
+    constexpr int NT = LT::NT, L = LT::L, NW = NT / 32;
+    constexpr int TXC = RNC / (BY * BZ), NOWN = BY * BZ;
+    constexpr int NRED = FUSE ? 2 * NOWN : NOWN;   // per x position: alpha-bar (and Q) of the own cells
+    __shared__ int xmap[TXC + 4];                  // x1 window: positions i0 - 2 .. i0 + TXC + 1
+    __shared__ int rowY[BZ * (BY + 4)], rowZ[BY * (BZ + 4)];
+    __shared__ __align__(16) S recX[NOWN][TXC + 3][8];   // x1 faces between window positions f, f + 1
+    __shared__ __align__(16) S recY[BZ][BY + 3][TXC][8];
+    __shared__ __align__(16) S recZ[BY][BZ + 3][TXC][8];
+    __shared__ S part[NW][NRED][TXC];
+    __shared__ S partP[NW][RNC];
+    __shared__ double cInv[RNC], cUb[RNC], cEmb[RNC];
+    extern __shared__ __align__(16) unsigned char dsm[];   // FUSE: cotangents of I_+ [RNC][NT L]
+    S *sIt = reinterpret_cast<S *>(dsm);
 
-// c1, c2, c3 of the face and their derivatives in tau (in the pass's type)
-template <typename TM> __device__ void face_cd(TM tau, TM *fc) {
-    if (tau > TM(0)) {
-        TM t2 = tau * tau, t4 = t2 * t2;
-        TM F = -expm1(-t2), G = -expm1(-t4);
-        TM f = sqrt(F) / tau, g = sqrt(G) / tau, e = exp(-tau), S = f + g;
-        TM fp = exp(-t2) / sqrt(F) - f / tau;
-        TM gp = G > TM(0) ? TM(2) * t2 * exp(-t4) / sqrt(G) - g / tau : TM(1);
-        TM ep = -e, Sp = fp + gp, iS2 = TM(1) / (S * S);
-        fc[0] = f * e / S; fc[1] = g * e / S; fc[2] = f * g / S;
-        fc[3] = ((fp * e + f * ep) * S - f * e * Sp) * iS2;
-        fc[4] = ((gp * e + g * ep) * S - g * e * Sp) * iS2;
-        fc[5] = ((fp * g + f * gp) * S - f * g * Sp) * iS2;
-    } else {
-        fc[0] = TM(1); fc[1] = TM(0); fc[2] = TM(0);
-        fc[3] = TM(-2); fc[4] = TM(1); fc[5] = TM(1);
-    }
-}
-
-// the six face coefficients from a 16-byte aligned shared record, with vector loads
-__device__ __forceinline__ void ldfc6(const float *p, float (&f)[6]) {
-    const float4 a = *reinterpret_cast<const float4 *>(p);
-    const float2 b = *reinterpret_cast<const float2 *>(p + 4);
-    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y;
-}
-__device__ __forceinline__ void ldfc6(const double *p, double (&f)[6]) {
-    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2),
-                  c = *reinterpret_cast<const double2 *>(p + 4);
-    f[0] = a.x; f[1] = a.y; f[2] = b.x; f[3] = b.y; f[4] = c.x; f[5] = c.y;
-}
-__device__ __forceinline__ void ldfc2(const float *p, float (&f)[2]) {
-    const float2 a = *reinterpret_cast<const float2 *>(p);
-    f[0] = a.x; f[1] = a.y;
-}
-__device__ __forceinline__ void ldfc2(const double *p, double (&f)[2]) {
-    const double2 a = *reinterpret_cast<const double2 *>(p);
-    f[0] = a.x; f[1] = a.y;
-}
-
-// derivative of the limited slope in (dl, dr), branches of rtk::limiter
-template <typename TM> __device__ __forceinline__ void lim_d(int kind, TM dl, TM dr, TM &gl, TM &gr) {
-    gl = TM(0); gr = TM(0);
-    if (kind == RT_LIM_DONOR || dl * dr <= TM(0)) return;
-    const TM al = fabs(dl), ar = fabs(dr);
-    if (kind == RT_LIM_MINMOD) { if (al < ar) gl = TM(1); else gr = TM(1); return; }
-    TM m = TM(2) * al;
-    int which = 0;
-    if (TM(2) * ar < m) { m = TM(2) * ar; which = 1; }
-    if (TM(0.5) * fabs(dl + dr) < m) which = 2;
-    if (which == 0) gl = TM(2);
-    else if (which == 1) gr = TM(2);
-    else { gl = TM(0.5); gr = TM(0.5); }
-}
-
-// One axis of the gather for one (cell, direction).  V: intensities at
-// offsets -3..3 along the axis (index o + 3), B: output cotangents at -2..2
-// (index o + 2, zero outside an outflow boundary), eq: bit o + 3 set when
-// offset o maps to this cell, fc[m + 2]: coefficients of the face between
-// offsets m and m + 1 (m = -2..1).  Adds the cotangent of this cell's
-// intensity to g and the cotangent of tau of the two adjacent faces to tb.
-template <typename TM>
-__device__ __forceinline__ void axis_adj(const TM (&V)[7], const TM (&B)[5], unsigned eq, const TM *const (&fc)[4],
-                                         TM n, TM coef, int lim, TM &g, TM (&tb)[2]) {
-    if (n == TM(0)) return;
-    const TM an = fabs(n), h = TM(0.5), one = TM(1);
-#pragma unroll
-    for (int m = -2; m <= 1; ++m) {
-        const TM phib = coef * (B[m + 3] - B[m + 2]);
-        if (phib == TM(0)) continue;
-        const TM Ill = V[m + 2], Il = V[m + 3], Ir = V[m + 4], Irr = V[m + 5];
-        TM f[6];
-        ldfc6(fc[m + 2], f);
-        TM gla, glb, gra, grb;
-        lim_d<TM>(lim, Ir - Il, Il - Ill, gla, glb);
-        lim_d<TM>(lim, Irr - Ir, Ir - Il, gra, grb);
-        const TM cL = n > TM(0) ? f[0] : f[1], cR = n > TM(0) ? f[1] : f[0];
-        const TM ILb = phib * n * cL, IRb = phib * n * cR;
-        const TM c3t = phib * an * f[2];
-        const TM dIll = -h * ILb * glb;
-        const TM dIl = c3t + ILb * (one - h * gla + h * glb) + h * IRb * grb;
-        const TM dIr = -c3t + h * ILb * gla + IRb * (one + h * gra - h * grb);
-        const TM dIrr = -h * IRb * gra;
-        if (eq & (1u << (m + 2))) g += dIll;
-        if (eq & (1u << (m + 3))) g += dIl;
-        if (eq & (1u << (m + 4))) g += dIr;
-        if (eq & (1u << (m + 5))) g += dIrr;
-        if (m == -1 || m == 0) {
-            TM sl = limiter<TM>(lim, Ir - Il, Il - Ill), sr = limiter<TM>(lim, Irr - Ir, Ir - Il);
-            const TM IL = Il + h * sl, IR = Ir - h * sr;
-            const TM cLb = phib * n * IL, cRb = phib * n * IR;
-            const TM c1b = n > TM(0) ? cLb : cRb, c2b = n > TM(0) ? cRb : cLb;
-            const TM c3b = -phib * an * (Ir - Il);
-            tb[m + 1] += c1b * f[3] + c2b * f[4] + c3b * f[5];
-        }
-    }
-}
-
-// limited slope of a cell and its derivatives in (dl, dr); the MC case with
-// selects only (same branches as lim_d: 0.5|dl+dr| wins when it is below
-// both 2|dl| and 2|dr|, 2|dr| wins over 2|dl| when strictly smaller)
-template <typename TM> __device__ __forceinline__ TM lim_dv(int kind, TM dl, TM dr, TM &gl, TM &gr) {
-    if (kind == RT_LIM_MC) {
-        const TM a2l = TM(2) * fabs(dl), a2r = TM(2) * fabs(dr), ah = TM(0.5) * fabs(dl + dr);
-        const bool ok = dl * dr > TM(0);
-        const TM mlr = fmin(a2l, a2r);
-        const bool w2 = ah < mlr, w1 = !w2 && a2r < a2l;
-        gl = ok ? (w2 ? TM(0.5) : (w1 ? TM(0) : TM(2))) : TM(0);
-        gr = ok ? (w2 ? TM(0.5) : (w1 ? TM(2) : TM(0))) : TM(0);
-        return ok ? copysign(fmin(mlr, ah), dl) : TM(0);
-    }
-    lim_d<TM>(kind, dl, dr, gl, gr);
-    return limiter<TM>(kind, dl, dr);
-}
-
-// axis_adj for a cell whose stencil maps to seven distinct cells (every
-// interior cell, and every cell of a periodic axis): only offset 0 is this
-// cell, so face m needs only the derivative at its own stencil position 0 -
-// the right neighbour's slope for m = -2, the full pair for m = -1 and 0, the
-// left cell's slope for m = 1 - and the slopes of offsets -1, 0, 1.
-template <typename TM>
-__device__ __forceinline__ void axis_adj_int(const TM (&V)[7], const TM (&B)[5], const TM *const (&fc)[4], TM n, TM coef,
-                                             int lim, TM &g, TM (&tb)[2]) {
-    if (n == TM(0)) return;
-    const TM an = fabs(n), h = TM(0.5), one = TM(1);
-    const bool pos = n > TM(0);
-    TM ga[3], gb[3], sv[3];
-#pragma unroll
-    for (int q = -1; q <= 1; ++q) sv[q + 1] = lim_dv<TM>(lim, V[q + 4] - V[q + 3], V[q + 3] - V[q + 2], ga[q + 1], gb[q + 1]);
-    const TM ph[4] = {coef * (B[1] - B[0]), coef * (B[2] - B[1]), coef * (B[3] - B[2]), coef * (B[4] - B[3])};
-    // m = -2: this cell is I_{r+1}; IR = I_r - s_r/2 with s_r the slope of offset -1
-    {
-        TM f[2];
-        ldfc2(fc[0], f);
-        const TM IRb = ph[0] * n * (pos ? f[1] : f[0]);
-        g += -h * IRb * ga[0];
-    }
-    // m = -1: this cell is I_r
-    {
-        TM f[6];
-        ldfc6(fc[1], f);
-        const TM cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
-        const TM ILb = ph[1] * n * cL, IRb = ph[1] * n * cR, c3t = ph[1] * an * f[2];
-        g += -c3t + h * ILb * ga[0] + IRb * (one + h * ga[1] - h * gb[1]);
-        const TM IL = V[2] + h * sv[0], IR = V[3] - h * sv[1];
-        const TM cLb = ph[1] * n * IL, cRb = ph[1] * n * IR;
-        tb[0] += (pos ? cLb : cRb) * f[3] + (pos ? cRb : cLb) * f[4] - ph[1] * an * (V[3] - V[2]) * f[5];
-    }
-    // m = 0: this cell is I_l
-    {
-        TM f[6];
-        ldfc6(fc[2], f);
-        const TM cL = pos ? f[0] : f[1], cR = pos ? f[1] : f[0];
-        const TM ILb = ph[2] * n * cL, IRb = ph[2] * n * cR, c3t = ph[2] * an * f[2];
-        g += c3t + ILb * (one - h * ga[1] + h * gb[1]) + h * IRb * gb[2];
-        const TM IL = V[3] + h * sv[1], IR = V[4] - h * sv[2];
-        const TM cLb = ph[2] * n * IL, cRb = ph[2] * n * IR;
-        tb[1] += (pos ? cLb : cRb) * f[3] + (pos ? cRb : cLb) * f[4] - ph[2] * an * (V[4] - V[3]) * f[5];
-    }
-    // m = 1: this cell is I_{l-1}; IL = I_l + s_l/2 with s_l the slope of offset 1
-    {
-        TM f[2];
-        ldfc2(fc[3], f);
-        const TM ILb = ph[3] * n * (pos ? f[0] : f[1]);
-        g += -h * ILb * gb[2];
-    }
-}
-
-// TM: storage and per-element arithmetic of intensities and their cotangents
-// (FP64, or FP32 for the mixed pass); the opacity cotangents are summed over
-// warps and chained to u_g and kappa in FP64
-template <typename TM>
-__global__ void __launch_bounds__(ADJ_NT) k_tr_adj(const TrArgs A) {
-    constexpr int NW = ADJ_NT / 32;
-    __shared__ __align__(16) TM fcs[NFACE][8];   // c1 c2 c3 dc1 dc2 dc3 (padded for vector loads)
-    __shared__ double abw[NW][TXA];
-    const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
-    const bool act = s < A.nd;
-    const int nx0 = A.nx[0], nx1 = A.nx[1], nx2 = A.nx[2];
-    const int nseg = (nx0 + TXA - 1) / TXA;
-    const int seg = blockIdx.x % nseg, row = blockIdx.x / nseg;
-    const int j = row % nx1, k = row / nx1, x0 = seg * TXA;
-    const int nc = min(TXA, nx0 - x0);
-    auto cell = [&](int i, int jj, int kk) { return ((size_t)kk * nx1 + jj) * nx0 + i; };
-    auto len = [&](int a) { return A.tau_dt ? A.dtk : A.dx[a]; };
-
-    // face coefficients: x1 faces with left cell x0 + m, m = -2..TXA (slot m + 2);
-    // x2 / x3 faces of cell t with left offset m = -2..1 (slot TXA + 3 + (axis - 1) 4 TXA + 4 t + m + 2)
-    for (int f = s; f < NFACE; f += ADJ_NT) {
-        int a, t, m;
-        if (f < TXA + 3) { a = 0; t = 0; m = f - 2; }
-        else { int u = f - (TXA + 3); a = 1 + u / (4 * TXA); t = (u % (4 * TXA)) / 4; m = u % 4 - 2; }
-        if (!A.act[a] || (a > 0 && t >= nc)) continue;
-        size_t cl, cr;
-        if (a == 0) {
-            cl = cell(amap(x0 + m, nx0, A.per[0]), j, k); cr = cell(amap(x0 + m + 1, nx0, A.per[0]), j, k);
-        } else if (a == 1) {
-            cl = cell(x0 + t, amap(j + m, nx1, A.per[1]), k); cr = cell(x0 + t, amap(j + m + 1, nx1, A.per[1]), k);
-        } else {
-            cl = cell(x0 + t, j, amap(k + m, nx2, A.per[2])); cr = cell(x0 + t, j, amap(k + m + 1, nx2, A.per[2]));
-        }
-        face_cd<TM>(TM(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len(a)), fcs[f]);
-    }
-    __syncthreads();
-
-    TM n[3] = {TM(0), TM(0), TM(0)};
-    if (act) for (int a = 0; a < 3; ++a) n[a] = (TM)A.dir[3 * s + a];
-    // (host-computed: FP64 divisions per thread would cost more than the cell's work)
-    const TM coef[3] = {TM(A.coef[0]), TM(A.coef[1]), TM(A.coef[2])};
-    const TM hl[3] = {TM(A.hl[0]), TM(A.hl[1]), TM(A.hl[2])};
+    const int p = threadIdx.x, lane = p & 31, warp = p >> 5;
     const int nd = A.nd;
-    // 32-bit element offsets (the host checks n_cell * n_dir < 2^31)
-    const TM *Ip = (const TM *)A.I + s, *Bp = (const TM *)A.Ibo + s;
-    auto ldI = [&](int off) -> TM { return act ? __ldg(Ip + off) : TM(0); };
-    auto ldB = [&](int off) -> TM { return act ? __ldg(Bp + off) : TM(0); };
-    auto eo = [&](int i, int jj, int kk) -> int { return ((kk * nx1 + jj) * nx0 + i) * nd; };
-
-    // x2 / x3 stencils of the block's row (j, k): mapped indices, which
-    // offsets are this cell, and which cotangent positions exist
-    int ry[7], rz[7];   // element offsets of the stencil rows at x1 = 0
-    unsigned eqa[3] = {0u, 0u, 0u}, ina[3] = {0u, 0u, 0u};
-#pragma unroll
-    for (int o = -3; o <= 3; ++o) {
-        const int my = amap(j + o, nx1, A.per[1]), mz = amap(k + o, nx2, A.per[2]);
-        ry[o + 3] = eo(0, my, k);
-        rz[o + 3] = eo(0, j, mz);
-        eqa[1] |= (unsigned)(my == j) << (o + 3);
-        eqa[2] |= (unsigned)(mz == k) << (o + 3);
-        ina[1] |= (unsigned)(A.per[1] || (j + o >= 0 && j + o < nx1)) << (o + 3);
-        ina[2] |= (unsigned)(A.per[2] || (k + o >= 0 && k + o < nx2)) << (o + 3);
+    const bool act = L * p < nd;
+    const int d0 = act ? L * p : 0;        // idle lanes shadow direction 0; their results are dropped
+    const int nx0 = A.nx[0], nx1 = A.nx[1], nx2 = A.nx[2];
+    const int nseg = (nx0 + TXC - 1) / TXC;
+    const int seg = blockIdx.x % nseg, rest = blockIdx.x / nseg, nyb = nx1 / BY;
+    const int j0 = (rest % nyb) * BY, k0 = (rest / nyb) * BZ, i0 = seg * TXC;
+    const int nc = min(TXC, nx0 - i0);
+    auto mapq = [](int q, int n, int per) -> int {
+        if (q >= 0 && q < n) return q;
+        if (per) return ((q % n) + n) % n;
+        return (q < 0 ? 0 : n - 1) | F_OUT;
+    };
+    for (int t = p; t < TXC + 4; t += NT) xmap[t] = mapq(i0 - 2 + t, nx0, A.per[0]);
+    for (int t = p; t < BZ * (BY + 4); t += NT) {
+        const int q = t % (BY + 4), r = t / (BY + 4);
+        const int my = mapq(j0 - 2 + q, nx1, A.per[1]);
+        rowY[t] = (((k0 + r) * nx1 + (my & F_IDX)) * nx0) | (my & F_OUT);
     }
-
-    // sliding x1 window
-    TM WX[7], BX[5];
-    if (A.act[0]) {
-#pragma unroll
-        for (int o = -3; o <= 3; ++o) WX[o + 3] = ldI(eo(amap(x0 + o, nx0, A.per[0]), j, k));
-#pragma unroll
-        for (int o = -2; o <= 2; ++o) {
-            int q = x0 + o;
-            BX[o + 2] = (A.per[0] || (q >= 0 && q < nx0)) ? ldB(eo(amap(q, nx0, A.per[0]), j, k)) : TM(0);
-        }
+    for (int t = p; t < BY * (BZ + 4); t += NT) {
+        const int r = t % (BZ + 4), q = t / (BZ + 4);
+        const int mz = mapq(k0 - 2 + r, nx2, A.per[2]);
+        rowZ[t] = (((mz & F_IDX) * nx1 + j0 + q) * nx0) | (mz & F_OUT);
     }
-#pragma unroll 1
-    for (int t = 0; t < nc; ++t) {
-        const int i = x0 + t;
-        const int ce = eo(i, j, k), ie = i * nd;
-        const TM Ic = ldI(ce), Bc = ldB(ce);
-        TM g = TM(0), abt = TM(0);
-        if (A.act[0]) {
-            unsigned eq = 0;
-#pragma unroll
-            for (int o = -3; o <= 3; ++o) eq |= (unsigned)(amap(i + o, nx0, A.per[0]) == i) << (o + 3);
-            const TM *fc[4] = {fcs[t], fcs[t + 1], fcs[t + 2], fcs[t + 3]};
-            TM tb[2] = {TM(0), TM(0)};
-            if (eq == (1u << 3)) axis_adj_int<TM>(WX, BX, fc, n[0], coef[0], A.limiter, g, tb);
-            else axis_adj<TM>(WX, BX, eq, fc, n[0], coef[0], A.limiter, g, tb);
-            abt += hl[0] * (tb[0] * TM(1 + ((eq >> 2) & 1)) + tb[1] * TM(1 + ((eq >> 4) & 1)));
-        }
-#pragma unroll
-        for (int a = 1; a < 3; ++a) {
-            if (!A.act[a]) continue;
-            const int *rr = a == 1 ? ry : rz;
-            TM V[7], B[5];
-#pragma unroll
-            for (int o = -3; o <= 3; ++o) V[o + 3] = o == 0 ? Ic : ldI(rr[o + 3] + ie);
-#pragma unroll
-            for (int o = -2; o <= 2; ++o)
-                B[o + 2] = o == 0 ? Bc : (((ina[a] >> (o + 3)) & 1u) ? ldB(rr[o + 3] + ie) : TM(0));
-            const int base = TXA + 3 + (a - 1) * 4 * TXA + 4 * t;
-            const TM *fc[4] = {fcs[base], fcs[base + 1], fcs[base + 2], fcs[base + 3]};
-            TM tb[2] = {TM(0), TM(0)};
-            const unsigned eq = eqa[a];
-            if (eq == (1u << 3)) axis_adj_int<TM>(V, B, fc, n[a], coef[a], A.limiter, g, tb);
-            else axis_adj<TM>(V, B, eq, fc, n[a], coef[a], A.limiter, g, tb);
-            abt += hl[a] * (tb[0] * TM(1 + ((eq >> 2) & 1)) + tb[1] * TM(1 + ((eq >> 4) & 1)));
-        }
-        if (act) {
-            const size_t ix = (size_t)ce + s;
-            TM v = g + (A.add_base ? Bc : TM(0));
-            if (A.src_acc) v += ((TM *)A.out_src)[ix];
-            ((TM *)A.out_src)[ix] = v;
-            if (A.base_out) ((TM *)A.base_out)[ix] = Bc;
-        }
-        // opacity cotangent of this cell: warp sum now, block sum below
-        for (int o = 16; o > 0; o >>= 1) abt += __shfl_xor_sync(0xffffffffu, abt, o);
-        if (lane == 0) abw[warp][t] = (double)abt;
-        // slide the x1 window
-        if (A.act[0] && t + 1 < nc) {
-#pragma unroll
-            for (int o = 0; o < 6; ++o) WX[o] = WX[o + 1];
-#pragma unroll
-            for (int o = 0; o < 4; ++o) BX[o] = BX[o + 1];
-            WX[6] = ldI(eo(amap(i + 4, nx0, A.per[0]), j, k));
-            const int q = i + 3;
-            BX[4] = (A.per[0] || q < nx0) ? ldB(eo(amap(q, nx0, A.per[0]), j, k)) : TM(0);
-        }
-    }
-    // through alpha = kappa rho^m T^-p + alpha^s (T = u_g/Y) to u_g and kappa
     __syncthreads();
-    if (s < nc) {
-        const size_t c = cell(x0 + s, j, k);
-        double ab = 0.0;
-        for (int g = 0; g < NW; ++g) ab += abw[g][s];
-        const double Y = A.cc_Y[c], T = Y > 0.0 ? A.ug[c] / Y : 0.0;
-        double ubv = 0.0;
-        if (A.cc_on[c] && T > 0.0 && ab != 0.0) {
-            const double tp = tpow_neg<double>(T, A.T_exp);
-            A.kb[c] += ab * rho_m(A.cc_au[c], A.kap[c], A.rho[c], A.rho_exp) * tp;
-            ubv = ab * A.cc_au[c] * (-A.T_exp) * tp / T / Y;
+    if (A.transport) {
+        const int nX = A.act[0] ? NOWN * (nc + 3) : 0;
+        const int nY = A.act[1] ? BZ * (BY + 3) * nc : 0;
+        const int nZ = A.act[2] ? BY * (BZ + 3) * nc : 0;
+        for (int t = p; t < nX + nY + nZ; t += NT) {
+            int cl, cr;
+            S *dst;
+            double len;
+            if (t < nX) {
+                const int o = t / (nc + 3), f = t % (nc + 3);
+                const int rb = rowY[(o / BY) * (BY + 4) + o % BY + 2] & F_IDX;
+                cl = rb + (xmap[f] & F_IDX); cr = rb + (xmap[f + 1] & F_IDX);
+                dst = recX[o][f]; len = A.taulen[0];
+            } else if (t < nX + nY) {
+                const int u = t - nX, ii = u % nc, v = u / nc, f = v % (BY + 3), r = v / (BY + 3);
+                cl = (rowY[r * (BY + 4) + f] & F_IDX) + i0 + ii;
+                cr = (rowY[r * (BY + 4) + f + 1] & F_IDX) + i0 + ii;
+                dst = recY[r][f][ii]; len = A.taulen[1];
+            } else {
+                const int u = t - nX - nY, ii = u % nc, v = u / nc, f = v % (BZ + 3), q = v / (BZ + 3);
+                cl = (rowZ[q * (BZ + 4) + f] & F_IDX) + i0 + ii;
+                cr = (rowZ[q * (BZ + 4) + f + 1] & F_IDX) + i0 + ii;
+                dst = recZ[q][f][ii]; len = A.taulen[2];
+            }
+            face_record<S>((S)(A.abar * 0.5 * (A.alpha[cl] + A.alpha[cr]) * len), dst);
         }
-        A.ub[c] = A.ub_acc ? A.ub[c] + ubv : ubv;
+    }
+    __syncthreads();
+
+    V n[3], an[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { n[a] = LT::dirv(A.dir, d0, a); an[a] = LT::vabs(n[a]); }
+    const V cf[3] = {LT::splat((S)A.coef[0]), LT::splat((S)A.coef[1]), LT::splat((S)A.coef[2])};
+    const V hv[3] = {LT::splat((S)A.hl[0]), LT::splat((S)A.hl[1]), LT::splat((S)A.hl[2])};
+    const V zero = LT::splat(S(0));
+    const int lim = A.limiter;
+    const S *Ip = (const S *)A.I, *Zp = (const S *)A.Zg, *Zo = (const S *)A.Zown;
+    auto ldI = [&](int off) -> V { return LT::ld(Ip + off); };
+    auto ldZ = [&](int off) -> V { return LT::ld(Zp + off); };
+    // element offsets (32 bits: the host checks n_cell n_dir < 2^31) of the
+    // stencil rows at x1 = 0, and which of them lie beyond an outflow boundary
+    int oy[BZ][BY + 4], oz[BY][BZ + 4];
+    unsigned outY[BZ], outZ[BY];
+#pragma unroll
+    for (int r = 0; r < BZ; ++r) {
+        outY[r] = 0u;
+#pragma unroll
+        for (int k = 0; k < BY + 4; ++k) {
+            const int d = rowY[r * (BY + 4) + k];
+            oy[r][k] = (d & F_IDX) * nd + d0;
+            outY[r] |= (unsigned)((d & F_OUT) != 0) << k;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < BY; ++q) {
+        outZ[q] = 0u;
+#pragma unroll
+        for (int k = 0; k < BZ + 4; ++k) {
+            const int d = rowZ[q * (BZ + 4) + k];
+            oz[q][k] = (d & F_IDX) * nd + d0;
+            outZ[q] |= (unsigned)((d & F_OUT) != 0) << k;
+        }
+    }
+    auto own = [&](int o) -> int { return oy[o / BY][o % BY + 2]; };
+
+    // x1 pipeline per own row, at own position p: xE = the part of p's
+    // cotangent known before face p + 3/2 (faces p -+ 1/2 and the slope terms
+    // of p - 1 and p), xCa = S~_p gl_p, xIRb / xR1 / xPh = IRb, IRb - c3t and
+    // phib of face p + 1/2, xI0 / xI1 = I_p / I_{p+1}, xH0 = hs_p,
+    // xB0 / xB1 = Zg_p / Zg_{p+1}, xAb = alpha-bar share of face p - 1/2.
+    // (S~_p = ILb_{p+1/2} - IRb_{p-1/2}; the cotangent of I_p along one axis is
+    //  ILb_{p+1/2} + c3t_{p+1/2} + IRb_{p-1/2} - c3t_{p-1/2}
+    //  + S~_p (gr_p - gl_p) + S~_{p-1} gl_{p-1} - S~_{p+1} gr_{p+1},
+    //  with gl, gr the derivatives of the half slopes.)
+    const bool xon = A.transport && A.act[0];
+    const bool lowX = xon && i0 == 0 && !A.per[0];
+    V xE[NOWN], xCa[NOWN], xIRb[NOWN], xR1[NOWN], xPh[NOWN], xI0[NOWN], xI1[NOWN], xH0[NOWN], xB0[NOWN], xB1[NOWN],
+        xAb[NOWN];
+    if (xon) {
+#pragma unroll
+        for (int o = 0; o < NOWN; ++o) {
+            const int ob = own(o);
+            V Iw[4], Zw[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int xd = xmap[u], off = ob + (xd & F_IDX) * nd;
+                Iw[u] = ldI(off);
+                Zw[u] = (xd & F_OUT) ? zero : ldZ(off);
+            }
+            const V d01 = Iw[1] - Iw[0], d12 = Iw[2] - Iw[1], d23 = Iw[3] - Iw[2];
+            V hs1, gl1, gr1, hs2, gl2, gr2;
+            limv(lim, d12, d01, hs1, gl1, gr1);
+            limv(lim, d23, d12, hs2, gl2, gr2);
+            const V ph0 = cf[0] * (Zw[1] - Zw[0]), ph1 = cf[0] * (Zw[2] - Zw[1]), ph2 = cf[0] * (Zw[3] - Zw[2]);
+            const FaceCot<V> f0 = face_cot<LT>(ph0, n[0], an[0], recX[o][0]);
+            const FaceCot<V> f1 = face_cot<LT>(ph1, n[0], an[0], recX[o][1]);
+            const FaceCot<V> f2c = face_cot<LT>(ph2, n[0], an[0], recX[o][2]);
+            const V St1 = f1.ILb - f0.IRb, St2 = f2c.ILb - f1.IRb;
+            const V tb1 = face_tau<LT>(ph1, n[0], an[0], Iw[1] + hs1, Iw[2] - hs2, d12, recX[o][1]) * hv[0];
+            V e = St2 * (gr2 - gl2) + St1 * gl1 + (f2c.ILb + f2c.c3t) + (f1.IRb - f1.c3t);
+            if (lowX) e = e + (f1.ILb + f1.c3t);            // ghost I_{-1} is I_0
+            xE[o] = e; xCa[o] = St2 * gl2;
+            xIRb[o] = f2c.IRb; xR1[o] = f2c.IRb - f2c.c3t; xPh[o] = ph2;
+            xI0[o] = Iw[2]; xI1[o] = Iw[3]; xH0[o] = hs2; xB0[o] = Zw[2]; xB1[o] = Zw[3];
+            xAb[o] = lowX ? tb1 + tb1 : tb1;                  // tau of face -1/2 is 2 x (alpha_0 abar len / 2)
+        }
+    }
+
+    const V wdir = LT::wv(A.w, d0);
+    (void)wdir;
+#pragma unroll 1
+    for (int ii = 0; ii < nc; ++ii) {
+        const int i = i0 + ii, ie = i * nd;
+        V Ic[NOWN], Zc[NOWN], acc[NOWN], ab[NOWN];
+        if (xon) {
+            const int xd = xmap[ii + 4];
+            const bool hiE = !A.per[0] && i == nx0 - 1;
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                const int off = own(o) + (xd & F_IDX) * nd;
+                const V I2 = ldI(off), Z2 = (xd & F_OUT) ? zero : ldZ(off);
+                const V dr = xI1[o] - xI0[o], dl = I2 - xI1[o];
+                V hsN, glN, grN;
+                limv(lim, dl, dr, hsN, glN, grN);
+                const V phN = cf[0] * (Z2 - xB1[o]);
+                const FaceCot<V> fN = face_cot<LT>(phN, n[0], an[0], recX[o][ii + 3]);
+                const V StN = fN.ILb - xIRb[o];
+                V g = xE[o] - StN * grN;
+                const V tb = face_tau<LT>(xPh[o], n[0], an[0], xI0[o] + xH0[o], xI1[o] - hsN, dr, recX[o][ii + 2]) * hv[0];
+                if (hiE) g = g + xR1[o];                        // ghost I_{n} is I_{n-1}
+                acc[o] = g;
+                ab[o] = xAb[o] + (hiE ? tb + tb : tb);
+                Ic[o] = xI0[o]; Zc[o] = xB0[o];
+                xE[o] = StN * (grN - glN) + xCa[o] + (fN.ILb + fN.c3t) + xR1[o];
+                xCa[o] = StN * glN; xIRb[o] = fN.IRb; xR1[o] = fN.IRb - fN.c3t; xPh[o] = phN;
+                xI0[o] = xI1[o]; xI1[o] = I2; xH0[o] = hsN; xB0[o] = xB1[o]; xB1[o] = Z2; xAb[o] = tb;
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                Ic[o] = ldI(own(o) + ie); Zc[o] = ldZ(own(o) + ie);
+                acc[o] = zero; ab[o] = zero;
+            }
+        }
+        // one column of NB own cells along x2 or x3 (window rows k = 0 .. NB + 3,
+        // own rows k = 2 .. NB + 1)
+        auto column = [&](auto NBc, const int *ofs, unsigned out, int ax, auto ownidx, auto recp) {
+            constexpr int NB = decltype(NBc)::value;
+            V Yv[NB + 4], Bv[NB + 4];
+#pragma unroll
+            for (int k = 0; k < NB + 4; ++k) {
+                if (k >= 2 && k < NB + 2) { Yv[k] = Ic[ownidx(k - 2)]; Bv[k] = Zc[ownidx(k - 2)]; }
+                else {
+                    Yv[k] = ldI(ofs[k] + ie);
+                    Bv[k] = ((out >> k) & 1u) ? zero : ldZ(ofs[k] + ie);
+                }
+            }
+            V dI[NB + 3];
+#pragma unroll
+            for (int k = 0; k < NB + 3; ++k) dI[k] = Yv[k + 1] - Yv[k];
+            V hs[NB + 4], gl[NB + 4], gr[NB + 4];
+#pragma unroll
+            for (int k = 1; k < NB + 3; ++k) limv(lim, dI[k], dI[k - 1], hs[k], gl[k], gr[k]);
+            V ph[NB + 3];
+            FaceCot<V> fc[NB + 3];
+#pragma unroll
+            for (int f = 0; f < NB + 3; ++f) {
+                ph[f] = cf[ax] * (Bv[f + 1] - Bv[f]);
+                fc[f] = face_cot<LT>(ph[f], n[ax], an[ax], recp(f));
+            }
+            V St[NB + 4];
+#pragma unroll
+            for (int k = 1; k < NB + 3; ++k) St[k] = fc[k].ILb - fc[k - 1].IRb;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                const int k = q + 2, o = ownidx(q);
+                const bool loE = (out >> (k - 1)) & 1u, hiE = (out >> (k + 1)) & 1u;
+                V g = (fc[k].ILb + fc[k].c3t) + (fc[k - 1].IRb - fc[k - 1].c3t) + St[k] * (gr[k] - gl[k]) +
+                      St[k - 1] * gl[k - 1] - St[k + 1] * gr[k + 1];
+                if (loE) g = g + (fc[k - 1].ILb + fc[k - 1].c3t);
+                if (hiE) g = g + (fc[k].IRb - fc[k].c3t);
+                acc[o] = acc[o] + g;
+                const V tl = face_tau<LT>(ph[k - 1], n[ax], an[ax], Yv[k - 1] + hs[k - 1], Yv[k] - hs[k], dI[k - 1], recp(k - 1)) * hv[ax];
+                const V tr = face_tau<LT>(ph[k], n[ax], an[ax], Yv[k] + hs[k], Yv[k + 1] - hs[k + 1], dI[k], recp(k)) * hv[ax];
+                ab[o] = ab[o] + (loE ? tl + tl : tl) + (hiE ? tr + tr : tr);
+            }
+        };
+        if (A.transport && A.act[1]) {
+#pragma unroll
+            for (int r = 0; r < BZ; ++r)
+                column(std::integral_constant<int, BY>{}, oy[r], outY[r], 1, [&](int q) { return r * BY + q; },
+                       [&](int f) -> const S * { return recY[r][f][ii]; });
+        }
+        if (A.transport && A.act[2]) {
+#pragma unroll
+            for (int q = 0; q < BY; ++q)
+                column(std::integral_constant<int, BZ>{}, oz[q], outZ[q], 2, [&](int r) { return r * BY + q; },
+                       [&](int f) -> const S * { return recZ[q][f][ii]; });
+        }
+        S red[NRED];
+#pragma unroll
+        for (int o = 0; o < NOWN; ++o) {
+            V ib = acc[o];
+            if (A.add_base) ib = ib + Zc[o];
+            if (Zo) ib = ib + LT::ld(Zo + own(o) + ie);
+            red[o] = act ? LT::hsum(ab[o]) : S(0);
+            if constexpr (FUSE) {
+                if (act) LT::st(sIt + (o * TXC + ii) * (NT * L) + d0, ib);
+                red[NOWN + o] = act ? LT::hsum(ib * Ic[o]) : S(0);
+            } else if (act) {
+                if (A.out_f64) LT::st64((double *)A.Zout + own(o) + ie, ib);
+                else LT::st((S *)A.Zout + own(o) + ie, ib);
+            }
+        }
+        const S rs = tsum_n<NRED, S>(red, lane);
+        if (lane < NRED) part[warp][lane][ii] = rs;
+    }
+    __syncthreads();
+    if constexpr (FUSE) {
+        // P = sum over directions of the cotangent of I_+, per own cell
+        S v[RNC];
+#pragma unroll
+        for (int c = 0; c < RNC; ++c) {
+            S t = S(0);
+            if (act && c % TXC < nc) {
+                if constexpr (L == 2) {
+                    const float2 x = *reinterpret_cast<const float2 *>(sIt + c * (NT * L) + d0);
+                    t = x.x + x.y;
+                } else {
+                    t = sIt[c * (NT * L) + d0];
+                }
+            }
+            v[c] = t;
+        }
+        const S ps = tsum_n<RNC, S>(v, lane);
+        partP[warp][lane] = ps;
+        __syncthreads();
+    }
+    // one lane of warp 0 per own cell: the opacity chain and the interaction
+    if (warp == 0) {
+        const int lc = lane, o = lc / TXC, ii = lc % TXC;
+        if (ii < nc) {
+            const int c = ((k0 + o / BY) * nx1 + j0 + o % BY) * nx0 + i0 + ii;
+            double abar = 0.0;
+            for (int g = 0; g < NW; ++g) abar += (double)part[g][o][ii];
+            const double Y = A.cc_Y[c], au = A.cc_au[c];
+            double t = A.ubA ? A.ubA[c] : 0.0, kbv = 0.0;
+            // alpha = kappa rho^m T^-p + alpha^s with T = u_g / Y
+            if (A.transport && A.cc_on[c] && abar != 0.0) {
+                const double Ta = Y > 0.0 ? A.ug_a[c] / Y : 0.0;
+                if (Ta > 0.0) {
+                    const double tp = tpow_neg<double>(Ta, A.T_exp);
+                    kbv = abar * rho_m(au, A.kap[c], A.rho[c], A.rho_exp) * tp;
+                    t += abar * au * (-A.T_exp) * tp / Ta / Y;
+                }
+            }
+            if constexpr (!FUSE) {
+                if (A.ubA_out) A.ubA_out[c] = t;
+                A.kb[c] += kbv;
+            } else {
+                const double ugm = A.ugm[c], as = A.cc_as[c];
+                const double Tm = Y > 0.0 ? ugm / Y : 0.0;
+                const double am = (A.cc_on[c] && Tm > 0.0) ? au * tpow_neg<double>(Tm, A.T_exp) + as : 0.0;
+                const bool on = A.source && A.cc_on[c] && am > 0.0 && Y > 0.0 && ugm > 0.0;
+                double P = 0.0, Q = 0.0;
+                for (int g = 0; g < NW; ++g) { P += (double)partP[g][lc]; Q += (double)part[g][NOWN + o][ii]; }
+                const SrcRev r = src_rev(on, Y, ugm, au, as, A.eta[c], A.kap[c], A.rho[c], on ? A.Em[c] : 0.0,
+                                         on ? A.X[c] : 0.0, P, Q, t, A.dts, A.sumw, A.T_exp, A.arad, A.rho_exp);
+                A.ub_dst[c] = (A.ub_dst_acc ? A.ub_dst[c] : 0.0) + r.ugb;
+                A.kb[c] += kbv + r.kb;
+                A.eb[c] += r.eb;
+                cInv[lc] = r.inv; cUb[lc] = r.ub; cEmb[lc] = r.Emb;
+            }
+        }
+    }
+    if constexpr (FUSE) {
+        __syncthreads();
+        if (act) {
+            const V wv = LT::wv(A.w, d0);
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+#pragma unroll 4
+                for (int ii = 0; ii < TXC; ++ii) {
+                    if (ii >= nc) break;
+                    const int lc = o * TXC + ii;
+                    V ib;
+                    if constexpr (L == 2) {
+                        const float2 x = *reinterpret_cast<const float2 *>(sIt + lc * (NT * L) + d0);
+                        ib = F2{x.x, x.y};
+                    } else {
+                        ib = sIt[lc * (NT * L) + d0];
+                    }
+                    const V out = (ib - LT::splat((S)cUb[lc]) * wv) * LT::splat((S)cInv[lc]) + LT::splat((S)cEmb[lc]) * wv;
+                    LT::st((S *)A.Zout + own(o) + (i0 + ii) * nd, out);
+                }
+            }
+        }
     }
 }
 
-// element-wise type conversion (the mixed pass keeps its cotangents in FP32)
+// element-wise type conversion (the FP32 pass keeps its cotangents in FP32)
 template <typename A, typename B> __global__ void k_cvt(const A *__restrict__ x, B *__restrict__ y, size_t n) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = (B)x[i];
 }
 
-}  // namespace
-
-// ----------------------------------------------------------------- host side
 static rt_status adj_fail(rt_ctx *c, rt_status st, const std::string &msg) {
     c->err = msg;
     return st;
 }
 
-static rt_status launch_src(rt_ctx *c, bool rev, const void *I, const double *ug_in, double dtk, void *I_out,
-                            double *ug_out, const void *Ibo, const double *ubo, void *Ibi, double *ubi, int ub_acc,
-                            double *kb, double *eb) {
-    SrcArgs A{};
-    const rt_config &f = c->cfg;
-    A.ncell = c->ncell; A.nd = c->nd; A.source = f.source;
-    A.dtk = dtk; A.sumw = c->sumw; A.T_exp = f.T_exp; A.arad = f.arad; A.rho_exp = f.rho_exp;
-    A.w = c->g->w; A.I = I; A.ug_in = ug_in; A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y;
-    A.eta = c->eta; A.rho = c->rho; A.kap = c->kap; A.cc_on = c->cc_on;
-    A.I_out = I_out; A.ug_out = ug_out; A.Ibo = Ibo; A.ubo = ubo; A.Ibi = Ibi; A.ubi = ubi; A.ub_acc = ub_acc;
-    A.kb = kb; A.eb = eb; A.fail = c->fail;
-    const bool f64 = c->cfg.precision == RT_FP64;
-    const int SC = f64 ? CellsPerBlock<double>::v : CellsPerBlock<float>::v;
-    unsigned nblk = (unsigned)((c->ncell + SC - 1) / SC);
-    if (rev) {
-        if (f64) k_src<true, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-        else k_src<true, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-    } else {
-        if (f64) k_src<false, double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-        else k_src<false, float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-    }
+template <class LT, int BY, int BZ, bool FUSE>
+rt_status launch_rev_t(rt_ctx *c, const RevArgs &A) {
+    constexpr int TXC = RNC / (BY * BZ);
+    const size_t nblk = (size_t)((A.nx[0] + TXC - 1) / TXC) * (A.nx[1] / BY) * (A.nx[2] / BZ);
+    const int dyn = FUSE ? (int)(RNC * LT::NT * LT::L * sizeof(typename LT::S)) : 0;
+    auto kern = k_rev<LT, BY, BZ, FUSE>;
+    RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    kern<<<(unsigned)nblk, LT::NT, dyn, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }
-
-static rt_status launch_tr(rt_ctx *c, const void *I, const double *ug, const double *alpha, double dtk,
-                           const void *Ibo, void *out_src, int src_acc, int add_base, void *base_out, double *ub,
-                           int ub_acc, double *kb) {
-    TrArgs A{};
-    const rt_config &f = c->cfg;
-    for (int a = 0; a < 3; ++a) {
-        A.nx[a] = f.nx[a]; A.act[a] = c->active[a]; A.per[a] = f.bc[a][0] == RT_BC_PERIODIC; A.dx[a] = f.dx[a];
-    }
-    A.nd = c->nd; A.limiter = f.limiter; A.tau_dt = f.tau_dt; A.abar = f.abar; A.dtk = dtk;
-    A.T_exp = f.T_exp; A.rho_exp = f.rho_exp;
-    A.dir = c->g->dir; A.I = I; A.alpha = alpha; A.Ibo = Ibo; A.out_src = out_src; A.base_out = base_out;
-    A.src_acc = src_acc; A.add_base = add_base; A.ug = ug; A.cc_au = c->cc_au; A.cc_Y = c->cc_Y; A.rho = c->rho;
-    A.kap = c->kap;
-    for (int a = 0; a < 3; ++a) {
-        A.coef[a] = dtk / f.dx[a];
-        A.hl[a] = f.abar * 0.5 * (f.tau_dt ? dtk : f.dx[a]);
-    }
-    A.cc_on = c->cc_on; A.ub = ub; A.kb = kb; A.ub_acc = ub_acc;
-    const int nseg = (f.nx[0] + TXA - 1) / TXA;
-    unsigned nblk = (unsigned)((size_t)nseg * f.nx[1] * f.nx[2]);
-    if (c->cfg.precision == RT_FP64) k_tr_adj<double><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-    else k_tr_adj<float><<<nblk, ADJ_NT, 0, c->stream>>>(A);
-    RT_CUDA_TRY(c, cudaGetLastError());
-    return RT_OK;
+template <class LT, bool FUSE> rt_status launch_rev_b(rt_ctx *c, const RevArgs &A) {
+    // brick shapes as the forward stage kernel picks them
+    const bool by = A.act[1] && A.nx[1] % 2 == 0, bz = A.act[2] && A.nx[2] % 2 == 0;
+    if (by && bz) return launch_rev_t<LT, 2, 2, FUSE>(c, A);
+    if (by) return launch_rev_t<LT, 2, 1, FUSE>(c, A);
+    return launch_rev_t<LT, 1, 1, FUSE>(c, A);
+}
+static rt_status launch_rev(rt_ctx *c, const RevArgs &A, bool fuse) {
+    if (c->cfg.precision == RT_FP64) return fuse ? launch_rev_b<LaneD, true>(c, A) : launch_rev_b<LaneD, false>(c, A);
+    return fuse ? launch_rev_b<LaneF, true>(c, A) : launch_rev_b<LaneF, false>(c, A);
 }
 
-// transport-only stage through the forward stage kernel (interaction off)
-static rt_status transport_only(rt_ctx *c, const void *Isrc, const void *Ibase, void *Iout, const double *ug,
-                                const double *alpha, double dtk, double *ug_scr, double *a_scr) {
-    const int src = c->cfg.source;
-    c->cfg.source = 0;
-    rt_status st = rt_launch_stage(c, Isrc, Ibase, Iout, ug, ug_scr, alpha, alpha, a_scr, dtk, nullptr);
-    c->cfg.source = src;
-    return st;
-}
+}  // namespace
 
 extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,
                                      const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,
@@ -622,7 +659,7 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     if (c->metric != RT_MINKOWSKI_CART || !c->static_fluid)
         return adj_fail(c, RT_EINVAL, "rt_step_adjoint: flat Cartesian geometry with the fluid at rest only");
     if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: FP64 or FP32 intensities only");
-    if (c->nd > ADJ_NT) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: at most 192 directions");
+    if (c->nd > LaneD::NT || c->nd % 2) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: at most 192 directions");
     if ((double)c->ncell * c->nd >= 2147483647.0)
         return adj_fail(c, RT_EINVAL, "rt_step_adjoint: n_cell * n_dir must be below 2^31");
     for (int a = 0; a < 3; ++a) {
@@ -639,16 +676,19 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
         }
         dt = c->dt_cfl;
     }
-    const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
-    const int order = c->cfg.order;
-    // arena: per step I^n, (order 2: I*_t, I*), I^{n+1}_t in the storage
-    // type, u_g^n, (u_g*); reverse: intensity cotangents in the storage type
-    // (two, plus the running one for FP32) and eight per-cell FP64 buffers
-    const size_t es = c->esize, per_step_i = order == 2 ? 4 : 2, per_step_c = order == 2 ? 2 : 1;
+    const rt_config &f = c->cfg;
+    const size_t nc = (size_t)c->ncell, ni = nc * c->nd, es = c->esize;
+    const int order = f.order, ns = order == 2 ? 2 : 1;   // stages per step
+    const int N = nsteps;
+    // arena: the stage inputs I^0..I^N (and the predictor outputs I*), two
+    // cotangent buffers in the storage type, and per-cell FP64 arrays: u_g^0..u_g^N
+    // (and u_g*), the stages' face opacities, the saved E-bar_- and roots, two
+    // gas-energy cotangents
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const bool f64 = c->cfg.precision == RT_FP64;
-    const size_t bI = up(ni * es), bX = bI, bC = up(nc * 8);
-    const size_t need = per_step_i * nsteps * bI + (f64 ? 2 : 3) * bX + (per_step_c * nsteps + 8) * bC;
+    const size_t bI = up(ni * es), bC = up(nc * 8);
+    const size_t nI = (size_t)(N + 1) + (order == 2 ? N : 0) + 2;
+    const size_t nCell = (size_t)(N + 1) * 2 + (order == 2 ? 2 * (size_t)N : 0) + 2 * (size_t)N * ns + 2;
+    const size_t need = nI * bI + nCell * bC;
     if (c->adj_bytes < need) {
         if (c->adj) cudaFree(c->adj);
         c->adj = nullptr; c->adj_bytes = 0;
@@ -657,71 +697,114 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     }
     char *p = (char *)c->adj;
     auto take = [&](size_t b) { char *r = p; p += b; return r; };
-    std::vector<void *> In(nsteps), At(nsteps), Bs(nsteps), Ct(nsteps);
-    std::vector<double *> un(nsteps), us(nsteps);
-    for (int n = 0; n < nsteps; ++n) {
-        In[n] = take(bI);
-        if (order == 2) { At[n] = take(bI); Bs[n] = take(bI); }
-        Ct[n] = take(bI);
-    }
-    for (int n = 0; n < nsteps; ++n) { un[n] = (double *)take(bC); if (order == 2) us[n] = (double *)take(bC); }
-    void *X1 = take(bX), *X2 = take(bX);
-    void *Ib = f64 ? (void *)dL_dI_in : (void *)take(bX);   // the running cotangent of I
-    double *ub = (double *)take(bC), *ubn = (double *)take(bC), *ubs = (double *)take(bC), *an = (double *)take(bC);
-    double *as_ = (double *)take(bC), *ug_scr = (double *)take(bC), *a_scr = (double *)take(bC);
-    double *u_next = (double *)take(bC);
-    void *I_last = X2;   // the recompute's final state is never read: any buffer of ni * es bytes
+    std::vector<void *> In(N + 1), Bs(N);
+    std::vector<double *> un(N + 1), us(N), aln(N + 1), als(N), sE(N * ns), sX(N * ns);
+    for (int n = 0; n <= N; ++n) In[n] = take(bI);
+    if (order == 2) for (int n = 0; n < N; ++n) Bs[n] = take(bI);
+    void *Z[2] = {take(bI), take(bI)};
+    for (int n = 0; n <= N; ++n) { un[n] = (double *)take(bC); aln[n] = (double *)take(bC); }
+    if (order == 2) for (int n = 0; n < N; ++n) { us[n] = (double *)take(bC); als[n] = (double *)take(bC); }
+    for (int s = 0; s < N * ns; ++s) { sE[s] = (double *)take(bC); sX[s] = (double *)take(bC); }
+    double *ubc = (double *)take(bC), *ubp = (double *)take(bC);
 
-    // 1. forward recompute from the checkpoint
+    // 1. forward recompute from the checkpoint with the stage kernels
+    struct SaveGuard {
+        rt_ctx *c;
+        ~SaveGuard() { c->sv_Em = nullptr; c->sv_X = nullptr; }
+    } guard{c};
     RT_CUDA_TRY(c, cudaMemcpyAsync(In[0], I_ckpt, ni * es, cudaMemcpyDeviceToDevice, c->stream));
     RT_CUDA_TRY(c, cudaMemcpyAsync(un[0], ug_ckpt, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     rt_status st;
-    for (int n = 0; n < nsteps; ++n) {
-        void *Inext = n + 1 < nsteps ? In[n + 1] : I_last;
-        double *unext = n + 1 < nsteps ? un[n + 1] : u_next;
-        if ((st = rt_launch_alpha(c, un[n], an)) != RT_OK) return st;
-        if (order == 1) {
-            if ((st = transport_only(c, In[n], In[n], Ct[n], un[n], an, dt, ug_scr, a_scr)) != RT_OK) return st;
-            if ((st = launch_src(c, false, Ct[n], un[n], dt, Inext, unext, 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
+    if ((st = rt_launch_alpha(c, un[0], aln[0])) != RT_OK) return st;
+    for (int n = 0; n < N; ++n) {
+        if (order == 2) {
+            c->sv_Em = sE[2 * n]; c->sv_X = sX[2 * n];
+            st = rt_launch_stage(c, In[n], In[n], Bs[n], un[n], us[n], aln[n], aln[n], als[n], 0.5 * dt, nullptr);
+            if (st != RT_OK) return st;
+            c->sv_Em = sE[2 * n + 1]; c->sv_X = sX[2 * n + 1];
+            st = rt_launch_stage(c, Bs[n], In[n], In[n + 1], un[n], un[n + 1], als[n], aln[n], aln[n + 1], dt, nullptr);
         } else {
-            if ((st = transport_only(c, In[n], In[n], At[n], un[n], an, 0.5 * dt, ug_scr, a_scr)) != RT_OK) return st;
-            if ((st = launch_src(c, false, At[n], un[n], 0.5 * dt, Bs[n], us[n], 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
-            if ((st = rt_launch_alpha(c, us[n], as_)) != RT_OK) return st;
-            if ((st = transport_only(c, Bs[n], In[n], Ct[n], us[n], as_, dt, ug_scr, a_scr)) != RT_OK) return st;
-            if ((st = launch_src(c, false, Ct[n], un[n], dt, Inext, unext, 0, 0, 0, 0, 0, 0, 0)) != RT_OK) return st;
+            c->sv_Em = sE[n]; c->sv_X = sX[n];
+            st = rt_launch_stage(c, In[n], In[n], In[n + 1], un[n], un[n + 1], aln[n], aln[n], aln[n + 1], dt, nullptr);
         }
+        if (st != RT_OK) return st;
     }
+    c->sv_Em = nullptr; c->sv_X = nullptr;
+
     // 2. reverse sweep
-    if (!f64) {
-        k_cvt<double, float><<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>(dL_dI_out, (float *)Ib, ni);
-        RT_CUDA_TRY(c, cudaGetLastError());
-    } else if (Ib != (void *)dL_dI_out) {
-        RT_CUDA_TRY(c, cudaMemcpyAsync(Ib, dL_dI_out, ni * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    RevArgs B{};
+    for (int a = 0; a < 3; ++a) {
+        B.nx[a] = f.nx[a]; B.act[a] = c->active[a]; B.per[a] = f.bc[a][0] == RT_BC_PERIODIC;
     }
-    if (dL_dug_out) RT_CUDA_TRY(c, cudaMemcpyAsync(ub, dL_dug_out, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    else RT_CUDA_TRY(c, cudaMemsetAsync(ub, 0, nc * sizeof(double), c->stream));
-    for (int n = nsteps - 1; n >= 0; --n) {
-        if ((st = rt_launch_alpha(c, un[n], an)) != RT_OK) return st;
-        if (order == 1) {
-            // interaction over dt, then transport over dt from I^n
-            if ((st = launch_src(c, true, Ct[n], un[n], dt, 0, 0, Ib, ub, X1, ubn, 0, dL_dkappa, dL_deta)) != RT_OK) return st;
-            if ((st = launch_tr(c, In[n], un[n], an, dt, X1, Ib, 0, 1, nullptr, ubn, 1, dL_dkappa)) != RT_OK) return st;
-        } else {
-            if ((st = rt_launch_alpha(c, us[n], as_)) != RT_OK) return st;
-            // corrector interaction (gas from u_g^n) and transport (fluxes of I*, opacity of u_g*)
-            if ((st = launch_src(c, true, Ct[n], un[n], dt, 0, 0, Ib, ub, X1, ubn, 0, dL_dkappa, dL_deta)) != RT_OK) return st;
-            // (Ib, read by the interaction above, now receives the corrector's base cotangent)
-            if ((st = launch_tr(c, Bs[n], us[n], as_, dt, X1, X2, 0, 0, Ib, ubs, 0, dL_dkappa)) != RT_OK) return st;
-            // predictor interaction and transport (both from I^n)
-            if ((st = launch_src(c, true, At[n], un[n], 0.5 * dt, 0, 0, X2, ubs, X1, ubn, 1, dL_dkappa, dL_deta)) != RT_OK) return st;
-            if ((st = launch_tr(c, In[n], un[n], an, 0.5 * dt, X1, Ib, 1, 1, nullptr, ubn, 1, dL_dkappa)) != RT_OK) return st;
+    B.nd = c->nd; B.limiter = f.limiter; B.source = f.source; B.abar = f.abar; B.sumw = c->sumw;
+    B.T_exp = f.T_exp; B.arad = f.arad; B.rho_exp = f.rho_exp;
+    B.dir = c->g->dir; B.w = c->g->w;
+    B.cc_au = c->cc_au; B.cc_as = c->cc_as; B.cc_Y = c->cc_Y; B.kap = c->kap; B.rho = c->rho; B.eta = c->eta;
+    B.cc_on = c->cc_on; B.kb = dL_dkappa; B.eb = dL_deta;
+    auto stage_args = [&](double dtk) {
+        RevArgs A = B;
+        A.transport = f.transport;
+        for (int a = 0; a < 3; ++a) {
+            A.coef[a] = dtk / f.dx[a];
+            A.taulen[a] = f.tau_dt ? dtk : f.dx[a];
+            A.hl[a] = f.abar * 0.5 * A.taulen[a];
         }
-        std::swap(ub, ubn);
-    }
+        return A;
+    };
+    const bool f64 = f.precision == RT_FP64;
+    const void *Zin = dL_dI_out;
     if (!f64) {
-        k_cvt<float, double><<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>((const float *)Ib, dL_dI_in, ni);
+        k_cvt<double, float><<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>(dL_dI_out, (float *)Z[1], ni);
         RT_CUDA_TRY(c, cudaGetLastError());
+        Zin = Z[1];
     }
-    RT_CUDA_TRY(c, cudaMemcpyAsync(dL_dug_in, ub, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    {   // the interaction that ends the last step, alone
+        RevArgs A = B;
+        A.transport = 0; A.add_base = 1;
+        A.I = In[N]; A.Zg = Zin; A.ubA = dL_dug_out;
+        A.dts = dt; A.ugm = un[N - 1]; A.Em = sE[N * ns - 1]; A.X = sX[N * ns - 1];
+        A.ub_dst = ubc; A.ub_dst_acc = 0; A.Zout = Z[0];
+        if ((st = launch_rev(c, A, true)) != RT_OK) return st;
+    }
+    int zr = 0;   // Z[zr]: cotangent of the current stage's transported state
+    for (int n = N - 1; n >= 0; --n) {
+        if (order == 2) {
+            // corrector: fluxes of I* (faces from u_g*), base I^n; fused with the
+            // predictor's interaction (gas u_g^n -> u_g*, over dt/2)
+            RevArgs A = stage_args(dt);
+            A.I = Bs[n]; A.Zg = Z[0]; A.Zown = nullptr; A.add_base = 0;
+            A.alpha = als[n]; A.ug_a = us[n]; A.ubA = nullptr;
+            A.dts = 0.5 * dt; A.ugm = un[n]; A.Em = sE[2 * n]; A.X = sX[2 * n];
+            A.ub_dst = ubc; A.ub_dst_acc = 1; A.Zout = Z[1];
+            if ((st = launch_rev(c, A, true)) != RT_OK) return st;
+            // predictor: fluxes of I^n, base I^n; the corrector's base cotangent Z[0] adds
+            RevArgs P = stage_args(0.5 * dt);
+            P.I = In[n]; P.Zg = Z[1]; P.Zown = Z[0]; P.add_base = 1;
+            P.alpha = aln[n]; P.ug_a = un[n]; P.ubA = ubc;
+            if (n > 0) {
+                P.dts = dt; P.ugm = un[n - 1]; P.Em = sE[2 * n - 1]; P.X = sX[2 * n - 1];
+                P.ub_dst = ubp; P.ub_dst_acc = 0; P.Zout = Z[0];   // Z[0] is read at own elements only
+                if ((st = launch_rev(c, P, true)) != RT_OK) return st;
+                std::swap(ubc, ubp);
+            } else {
+                P.ubA_out = dL_dug_in; P.Zout = dL_dI_in; P.out_f64 = 1;
+                if ((st = launch_rev(c, P, false)) != RT_OK) return st;
+            }
+        } else {
+            RevArgs A = stage_args(dt);
+            A.I = In[n]; A.Zg = Z[zr]; A.Zown = nullptr; A.add_base = 1;
+            A.alpha = aln[n]; A.ug_a = un[n]; A.ubA = ubc;
+            if (n > 0) {
+                A.dts = dt; A.ugm = un[n - 1]; A.Em = sE[n - 1]; A.X = sX[n - 1];
+                A.ub_dst = ubp; A.ub_dst_acc = 0; A.Zout = Z[1 - zr];
+                if ((st = launch_rev(c, A, true)) != RT_OK) return st;
+                zr ^= 1;
+                std::swap(ubc, ubp);
+            } else {
+                A.ubA_out = dL_dug_in; A.Zout = dL_dI_in; A.out_f64 = 1;
+                if ((st = launch_rev(c, A, false)) != RT_OK) return st;
+            }
+        }
+    }
     return RT_OK;
 }

@@ -84,6 +84,9 @@ struct rt_ctx {
     // arena of the reverse pass (rt_step_adjoint), grown on demand
     double *adj = nullptr;
     size_t adj_bytes = 0;
+    // set during the reverse pass's recompute: the stage kernels save each
+    // cell's E-bar_- and temperature-solve root X there (null otherwise)
+    double *sv_Em = nullptr, *sv_X = nullptr;
     // optional per-launch timing of the stage kernel
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;

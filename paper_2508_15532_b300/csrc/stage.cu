@@ -486,6 +486,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 ok = newton_E<double>(q, Em, lo, hi, 200, 4.0 * 2.220446049250313e-16, &X);
             }
             if (!ok) atomicAdd(A.fail, 1ull);
+            if (A.sv_X) { A.sv_Em[cidx] = Em; A.sv_X[cidx] = X; }
             const double Tp = Tm + (Em - X) / Y;
             const double aap = A.cc_au[cidx] * tpow_neg<double>(Tp, A.T_exp), atp = aap + A.cc_as[cidx];
             const double em = A.eta[cidx] * aap * A.arad * Tp * Tp * Tp * Tp + A.cc_as[cidx] * X;
@@ -660,6 +661,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.alpha_in = alpha_in; A.alpha_int = alpha_int; A.alpha_out = alpha_out;
     A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y; A.cc_on = c->cc_on;
     A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.G = G; A.fail = c->fail;
+    A.sv_Em = c->sv_Em; A.sv_X = c->sv_X;
     A.mirror = g->mirror; A.nnb = g->nnb; A.nbr = g->nbr; A.ring_edge = g->ring_edge; A.ring_back = g->ring_back;
     A.edge = g->edge;
     bool dbl = f.precision == RT_FP64;

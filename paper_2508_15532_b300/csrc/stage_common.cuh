@@ -31,6 +31,7 @@ struct StageArgs {
     const uint8_t *cc_on;
     double *G;
     unsigned long long *fail;
+    double *sv_Em, *sv_X;      // optional per-cell E-bar_- and root X of the interaction (reverse-pass recompute)
     const int *mirror, *nnb, *nbr, *ring_edge, *ring_back, *edge;
     const void *dirT, *wT, *mxT, *mgT, *mmT;   // math-type copies of the grid tables
     const void *mdT;                            // MAPR dual-basis dot products [nd][6][6][2]

@@ -16,6 +16,7 @@
 //    with a = alpha(T_+) dt, c = dt j(T_+) / (4 pi) (eq. fluid_interaction_discrete);
 //  - MC limiter and face records of three coefficients (no fluid advection).
 #include "stage_common.cuh"
+#include "f32x2.cuh"
 
 namespace {
 using namespace rtk;
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
                 inv = 1.0 / (1.0 + a);
             }
             if (!ok) atomicAdd(A.fail, 1ull);
+            if (A.sv_X) { A.sv_Em[cidx] = Em; A.sv_X[cidx] = X; }
             ce = (TM)c; ci = (TM)inv;
             // exchange ledger in closed form (I_+ = (I + c)/(1 + a) in every direction)
             const double Ep = (Em + c * A.sumw) * inv;
@@ -397,34 +399,6 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
 // FP32 or BF16 storage, periodic/outflow boundaries only.  Five CTAs of 96 threads
 // per SM (128 registers, 30 KB shared memory): measured 7% faster than
 // k_stage_fs at 128^3 x 162; six CTAs spill.
-struct F2 { float x, y; };
-__device__ __forceinline__ F2 f2(float a) { return F2{a, a}; }
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
-    F2 r;
-    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; add.rn.f32x2 rc, ra, rb; mov.b64 {%0, %1}, rc; }"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return r;
-}
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
-    F2 r;
-    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; sub.rn.f32x2 rc, ra, rb; mov.b64 {%0, %1}, rc; }"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return r;
-}
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
-    F2 r;
-    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; mul.rn.f32x2 rc, ra, rb; mov.b64 {%0, %1}, rc; }"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return r;
-}
-// a * b + c
-__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
-    F2 r;
-    asm("{ .reg .b64 ra, rb, rc, rd; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; mov.b64 rc, {%6, %7};"
-        " fma.rn.f32x2 rd, ra, rb, rc; mov.b64 {%0, %1}, rd; }"
-        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return r;
-}
 __device__ __forceinline__ F2 ld2(const float *p) { float2 v = __ldg(reinterpret_cast<const float2 *>(p)); return F2{v.x, v.y}; }
 __device__ __forceinline__ F2 ld2(const __nv_bfloat16 *p) {
     float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
@@ -717,6 +691,7 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
                              (float)FOURPI;
             const float invf = 1.0f / (1.0f + af);
             if (!ok) atomicAdd(A.fail, 1ull);
+            if (A.sv_X) { A.sv_Em[cidx] = Em; A.sv_X[cidx] = X; }
             ce = cf; ci = invf;
             const double a = af, c = cf, inv = invf;
             const double Ep = (Em + c * A.sumw) * inv;
