@@ -31,7 +31,10 @@ __device__ __forceinline__ double fma2(double a, double b, double c) { return fm
 struct LaneF {
     using S = float;
     using V = F2;
-    static constexpr int L = 2, NT = 96, MINB = 4;
+    // five CTAs per SM (128 registers), measured 5% faster than four; bricks of
+    // 2 x 1 cells across x2/x3 (the 2 x 2 brick spills even at four CTAs)
+    static constexpr int L = 2, NT = 96, MINB = 5;
+    static constexpr bool BRICK22 = false;
     __device__ static V splat(float a) { return f2(a); }
     __device__ static V ld(const float *p) { float2 v = __ldg(reinterpret_cast<const float2 *>(p)); return F2{v.x, v.y}; }
     __device__ static void st(float *p, V v) { *reinterpret_cast<float2 *>(p) = make_float2(v.x, v.y); }
@@ -45,6 +48,7 @@ struct LaneD {
     using S = double;
     using V = double;
     static constexpr int L = 1, NT = 192, MINB = 2;
+    static constexpr bool BRICK22 = true;     // measured 7% faster than 2 x 1 (FP64-pipe bound)
     __device__ static V splat(double a) { return a; }
     __device__ static V ld(const double *p) { return __ldg(p); }
     __device__ static void st(double *p, V v) { *p = v; }
@@ -63,7 +67,7 @@ struct LaneD {
 // 2|dr| only when strictly smaller, (dl + dr)/2 only when strictly below both.
 // Every kind has zero derivatives where dl dr <= 0 (in particular where one
 // difference is zero), which the outflow ghost folding below relies on.
-template <typename S> __device__ __forceinline__ void lim_half(int kind, S dl, S dr, S &hs, S &gl, S &gr) {
+template <typename S> __device__ __forceinline__ void lim_half(int kind, S dl, S dr, S &hs, S &gl, S &gr, S &gd) {
     const S al = fabs(dl), ar = fabs(dr);
     const bool ok = dl * dr > S(0);
     if (kind == RT_LIM_MC) {
@@ -75,21 +79,56 @@ template <typename S> __device__ __forceinline__ void lim_half(int kind, S dl, S
         hs = ok ? copysign(m, dl) : S(0);
         gl = ok ? (w2 ? S(0.25) : (w1 ? S(0) : S(1))) : S(0);
         gr = ok ? (w2 ? S(0.25) : (w1 ? S(1) : S(0))) : S(0);
+        gd = ok ? (w2 ? S(0) : (w1 ? S(1) : S(-1))) : S(0);
     } else if (kind == RT_LIM_MINMOD) {
         const bool wl = al < ar;
         hs = ok ? copysign(S(0.5) * (wl ? al : ar), dl) : S(0);
         gl = (ok && wl) ? S(0.5) : S(0);
         gr = (ok && !wl) ? S(0.5) : S(0);
+        gd = ok ? (wl ? S(-0.5) : S(0.5)) : S(0);
     } else {
-        hs = S(0); gl = S(0); gr = S(0);
+        hs = S(0); gl = S(0); gr = S(0); gd = S(0);
     }
 }
-__device__ __forceinline__ void limv(int kind, F2 dl, F2 dr, F2 &hs, F2 &gl, F2 &gr) {
-    lim_half<float>(kind, dl.x, dr.x, hs.x, gl.x, gr.x);
-    lim_half<float>(kind, dl.y, dr.y, hs.y, gl.y, gr.y);
+// FP64: the magnitude comparisons and minima on the integer pipe (the bit
+// patterns of non-negative doubles order as their values), which leaves the
+// FP64 pipe - 1/64 of the FP32 rate on this part - the sign test, dl + dr and
+// its quarter.  Same values and branches as the generic form.
+template <> __device__ __forceinline__ void lim_half<double>(int kind, double dl, double dr, double &hs, double &gl,
+                                                            double &gr, double &gd) {
+    constexpr long long MAG = 0x7fffffffffffffffLL;
+    const long long sl = __double_as_longlong(dl), al = sl & MAG, ar = __double_as_longlong(dr) & MAG;
+    const bool ok = dl * dr > 0.0;
+    if (kind == RT_LIM_MC) {
+        const long long q = __double_as_longlong(0.25 * fabs(dl + dr));
+        const bool w1 = ar < al;
+        const long long m1 = w1 ? ar : al;
+        const bool w2 = q < m1;
+        const long long m = w2 ? q : m1;
+        hs = ok ? __longlong_as_double(m | (sl & ~MAG)) : 0.0;
+        gl = ok ? (w2 ? 0.25 : (w1 ? 0.0 : 1.0)) : 0.0;
+        gr = ok ? (w2 ? 0.25 : (w1 ? 1.0 : 0.0)) : 0.0;
+        gd = ok ? (w2 ? 0.0 : (w1 ? 1.0 : -1.0)) : 0.0;
+    } else if (kind == RT_LIM_MINMOD) {
+        const bool wl = al < ar;
+        hs = ok ? 0.5 * __longlong_as_double((wl ? al : ar) | (sl & ~MAG)) : 0.0;
+        gl = (ok && wl) ? 0.5 : 0.0;
+        gr = (ok && !wl) ? 0.5 : 0.0;
+        gd = ok ? (wl ? -0.5 : 0.5) : 0.0;
+    } else {
+        hs = 0.0; gl = 0.0; gr = 0.0; gd = 0.0;
+    }
 }
-__device__ __forceinline__ void limv(int kind, double dl, double dr, double &hs, double &gl, double &gr) {
-    lim_half<double>(kind, dl, dr, hs, gl, gr);
+// per lane type, with gd = gr - gl: one packed subtraction for FP32 pairs;
+// selects for FP64, which keeps the subtraction off the FP64 pipe
+__device__ __forceinline__ void limv(int kind, F2 dl, F2 dr, F2 &hs, F2 &gl, F2 &gr, F2 &gd) {
+    float ux, uy;   // (the scalar differences are dropped: one packed subtraction is cheaper)
+    lim_half<float>(kind, dl.x, dr.x, hs.x, gl.x, gr.x, ux);
+    lim_half<float>(kind, dl.y, dr.y, hs.y, gl.y, gr.y, uy);
+    gd = gr - gl;
+}
+__device__ __forceinline__ void limv(int kind, double dl, double dr, double &hs, double &gl, double &gr, double &gd) {
+    lim_half<double>(kind, dl, dr, hs, gl, gr, gd);
 }
 
 // Face record of the exponentially cut flux (eqs. rad_speeds, flux_Jiang):
@@ -345,8 +384,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     V n[3], an[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) { n[a] = LT::dirv(A.dir, d0, a); an[a] = LT::vabs(n[a]); }
-    const V cf[3] = {LT::splat((S)A.coef[0]), LT::splat((S)A.coef[1]), LT::splat((S)A.coef[2])};
-    const V hv[3] = {LT::splat((S)A.hl[0]), LT::splat((S)A.hl[1]), LT::splat((S)A.hl[2])};
+    const S cfs[3] = {(S)A.coef[0], (S)A.coef[1], (S)A.coef[2]};
+    const S hvs[3] = {(S)A.hl[0], (S)A.hl[1], (S)A.hl[2]};
+    auto cf = [&](int a) { return LT::splat(cfs[a]); };
+    auto hv = [&](int a) { return LT::splat(hvs[a]); };
     const V zero = LT::splat(S(0));
     const int lim = A.limiter;
     const S *Ip = (const S *)A.I, *Zp = (const S *)A.Zg, *Zo = (const S *)A.Zown;
@@ -354,29 +395,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     auto ldZ = [&](int off) -> V { return LT::ld(Zp + off); };
     // element offsets (32 bits: the host checks n_cell n_dir < 2^31) of the
     // stencil rows at x1 = 0, and which of them lie beyond an outflow boundary
-    int oy[BZ][BY + 4], oz[BY][BZ + 4];
-    unsigned outY[BZ], outZ[BY];
-#pragma unroll
-    for (int r = 0; r < BZ; ++r) {
-        outY[r] = 0u;
-#pragma unroll
-        for (int k = 0; k < BY + 4; ++k) {
-            const int d = rowY[r * (BY + 4) + k];
-            oy[r][k] = (d & F_IDX) * nd + d0;
-            outY[r] |= (unsigned)((d & F_OUT) != 0) << k;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < BY; ++q) {
-        outZ[q] = 0u;
-#pragma unroll
-        for (int k = 0; k < BZ + 4; ++k) {
-            const int d = rowZ[q * (BZ + 4) + k];
-            oz[q][k] = (d & F_IDX) * nd + d0;
-            outZ[q] |= (unsigned)((d & F_OUT) != 0) << k;
-        }
-    }
-    auto own = [&](int o) -> int { return oy[o / BY][o % BY + 2]; };
+    auto own = [&](int o) -> int { return (rowY[(o / BY) * (BY + 4) + o % BY + 2] & F_IDX) * nd + d0; };
 
     // x1 pipeline per own row, at own position p: xE = the part of p's
     // cotangent known before face p + 3/2 (faces p -+ 1/2 and the slope terms
@@ -403,16 +422,16 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 Zw[u] = (xd & F_OUT) ? zero : ldZ(off);
             }
             const V d01 = Iw[1] - Iw[0], d12 = Iw[2] - Iw[1], d23 = Iw[3] - Iw[2];
-            V hs1, gl1, gr1, hs2, gl2, gr2;
-            limv(lim, d12, d01, hs1, gl1, gr1);
-            limv(lim, d23, d12, hs2, gl2, gr2);
-            const V ph0 = cf[0] * (Zw[1] - Zw[0]), ph1 = cf[0] * (Zw[2] - Zw[1]), ph2 = cf[0] * (Zw[3] - Zw[2]);
+            V hs1, gl1, gr1, gd1, hs2, gl2, gr2, gd2;
+            limv(lim, d12, d01, hs1, gl1, gr1, gd1);
+            limv(lim, d23, d12, hs2, gl2, gr2, gd2);
+            const V ph0 = cf(0) * (Zw[1] - Zw[0]), ph1 = cf(0) * (Zw[2] - Zw[1]), ph2 = cf(0) * (Zw[3] - Zw[2]);
             const FaceCot<V> f0 = face_cot<LT>(ph0, n[0], an[0], recX[o][0]);
             const FaceCot<V> f1 = face_cot<LT>(ph1, n[0], an[0], recX[o][1]);
             const FaceCot<V> f2c = face_cot<LT>(ph2, n[0], an[0], recX[o][2]);
             const V St1 = f1.ILb - f0.IRb, St2 = f2c.ILb - f1.IRb;
-            const V tb1 = face_tau<LT>(ph1, n[0], an[0], Iw[1] + hs1, Iw[2] - hs2, d12, recX[o][1]) * hv[0];
-            V e = St2 * (gr2 - gl2) + St1 * gl1 + (f2c.ILb + f2c.c3t) + (f1.IRb - f1.c3t);
+            const V tb1 = face_tau<LT>(ph1, n[0], an[0], Iw[1] + hs1, Iw[2] - hs2, d12, recX[o][1]) * hv(0);
+            V e = St2 * gd2 + St1 * gl1 + (f2c.ILb + f2c.c3t) + (f1.IRb - f1.c3t);
             if (lowX) e = e + (f1.ILb + f1.c3t);            // ghost I_{-1} is I_0
             xE[o] = e; xCa[o] = St2 * gl2;
             xIRb[o] = f2c.IRb; xR1[o] = f2c.IRb - f2c.c3t; xPh[o] = ph2;
@@ -435,18 +454,18 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 const int off = own(o) + (xd & F_IDX) * nd;
                 const V I2 = ldI(off), Z2 = (xd & F_OUT) ? zero : ldZ(off);
                 const V dr = xI1[o] - xI0[o], dl = I2 - xI1[o];
-                V hsN, glN, grN;
-                limv(lim, dl, dr, hsN, glN, grN);
-                const V phN = cf[0] * (Z2 - xB1[o]);
+                V hsN, glN, grN, gdN;
+                limv(lim, dl, dr, hsN, glN, grN, gdN);
+                const V phN = cf(0) * (Z2 - xB1[o]);
                 const FaceCot<V> fN = face_cot<LT>(phN, n[0], an[0], recX[o][ii + 3]);
                 const V StN = fN.ILb - xIRb[o];
                 V g = xE[o] - StN * grN;
-                const V tb = face_tau<LT>(xPh[o], n[0], an[0], xI0[o] + xH0[o], xI1[o] - hsN, dr, recX[o][ii + 2]) * hv[0];
+                const V tb = face_tau<LT>(xPh[o], n[0], an[0], xI0[o] + xH0[o], xI1[o] - hsN, dr, recX[o][ii + 2]) * hv(0);
                 if (hiE) g = g + xR1[o];                        // ghost I_{n} is I_{n-1}
                 acc[o] = g;
                 ab[o] = xAb[o] + (hiE ? tb + tb : tb);
                 Ic[o] = xI0[o]; Zc[o] = xB0[o];
-                xE[o] = StN * (grN - glN) + xCa[o] + (fN.ILb + fN.c3t) + xR1[o];
+                xE[o] = StN * gdN + xCa[o] + (fN.ILb + fN.c3t) + xR1[o];
                 xCa[o] = StN * glN; xIRb[o] = fN.IRb; xR1[o] = fN.IRb - fN.c3t; xPh[o] = phN;
                 xI0[o] = xI1[o]; xI1[o] = I2; xH0[o] = hsN; xB0[o] = xB1[o]; xB1[o] = Z2; xAb[o] = tb;
             }
@@ -459,57 +478,64 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         }
         // one column of NB own cells along x2 or x3 (window rows k = 0 .. NB + 3,
         // own rows k = 2 .. NB + 1)
-        auto column = [&](auto NBc, const int *ofs, unsigned out, int ax, auto ownidx, auto recp) {
+        auto column = [&](auto NBc, const int *rows, int ax, auto ownidx, auto recp) {
             constexpr int NB = decltype(NBc)::value;
             V Yv[NB + 4], Bv[NB + 4];
+            unsigned out = 0u;
 #pragma unroll
             for (int k = 0; k < NB + 4; ++k) {
+                const int d = rows[k];
+                out |= (unsigned)((d & F_OUT) != 0) << k;
                 if (k >= 2 && k < NB + 2) { Yv[k] = Ic[ownidx(k - 2)]; Bv[k] = Zc[ownidx(k - 2)]; }
                 else {
-                    Yv[k] = ldI(ofs[k] + ie);
-                    Bv[k] = ((out >> k) & 1u) ? zero : ldZ(ofs[k] + ie);
+                    const int off = (d & F_IDX) * nd + d0 + ie;
+                    Yv[k] = ldI(off);
+                    Bv[k] = (d & F_OUT) ? zero : ldZ(off);
                 }
             }
             V dI[NB + 3];
 #pragma unroll
             for (int k = 0; k < NB + 3; ++k) dI[k] = Yv[k + 1] - Yv[k];
-            V hs[NB + 4], gl[NB + 4], gr[NB + 4];
+            V hs[NB + 4], gl[NB + 4], gr[NB + 4], gd[NB + 4];
 #pragma unroll
-            for (int k = 1; k < NB + 3; ++k) limv(lim, dI[k], dI[k - 1], hs[k], gl[k], gr[k]);
+            for (int k = 1; k < NB + 3; ++k) limv(lim, dI[k], dI[k - 1], hs[k], gl[k], gr[k], gd[k]);
             V ph[NB + 3];
             FaceCot<V> fc[NB + 3];
 #pragma unroll
             for (int f = 0; f < NB + 3; ++f) {
-                ph[f] = cf[ax] * (Bv[f + 1] - Bv[f]);
+                ph[f] = cf(ax) * (Bv[f + 1] - Bv[f]);
                 fc[f] = face_cot<LT>(ph[f], n[ax], an[ax], recp(f));
             }
             V St[NB + 4];
 #pragma unroll
             for (int k = 1; k < NB + 3; ++k) St[k] = fc[k].ILb - fc[k - 1].IRb;
+            V tb[NB + 2];   // d flux / d tau of the faces next to own cells (f = 1 .. NB + 1)
+#pragma unroll
+            for (int f = 1; f <= NB + 1; ++f)
+                tb[f] = face_tau<LT>(ph[f], n[ax], an[ax], Yv[f] + hs[f], Yv[f + 1] - hs[f + 1], dI[f], recp(f));
 #pragma unroll
             for (int q = 0; q < NB; ++q) {
                 const int k = q + 2, o = ownidx(q);
                 const bool loE = (out >> (k - 1)) & 1u, hiE = (out >> (k + 1)) & 1u;
-                V g = (fc[k].ILb + fc[k].c3t) + (fc[k - 1].IRb - fc[k - 1].c3t) + St[k] * (gr[k] - gl[k]) +
+                V g = (fc[k].ILb + fc[k].c3t) + (fc[k - 1].IRb - fc[k - 1].c3t) + St[k] * gd[k] +
                       St[k - 1] * gl[k - 1] - St[k + 1] * gr[k + 1];
                 if (loE) g = g + (fc[k - 1].ILb + fc[k - 1].c3t);
                 if (hiE) g = g + (fc[k].IRb - fc[k].c3t);
                 acc[o] = acc[o] + g;
-                const V tl = face_tau<LT>(ph[k - 1], n[ax], an[ax], Yv[k - 1] + hs[k - 1], Yv[k] - hs[k], dI[k - 1], recp(k - 1)) * hv[ax];
-                const V tr = face_tau<LT>(ph[k], n[ax], an[ax], Yv[k] + hs[k], Yv[k + 1] - hs[k + 1], dI[k], recp(k)) * hv[ax];
-                ab[o] = ab[o] + (loE ? tl + tl : tl) + (hiE ? tr + tr : tr);
+                const V tl = tb[k - 1], tr = tb[k];
+                ab[o] = fma2(hv(ax), (loE ? tl + tl : tl) + (hiE ? tr + tr : tr), ab[o]);
             }
         };
         if (A.transport && A.act[1]) {
 #pragma unroll
             for (int r = 0; r < BZ; ++r)
-                column(std::integral_constant<int, BY>{}, oy[r], outY[r], 1, [&](int q) { return r * BY + q; },
+                column(std::integral_constant<int, BY>{}, rowY + r * (BY + 4), 1, [&](int q) { return r * BY + q; },
                        [&](int f) -> const S * { return recY[r][f][ii]; });
         }
         if (A.transport && A.act[2]) {
 #pragma unroll
             for (int q = 0; q < BY; ++q)
-                column(std::integral_constant<int, BZ>{}, oz[q], outZ[q], 2, [&](int r) { return r * BY + q; },
+                column(std::integral_constant<int, BZ>{}, rowZ + q * (BZ + 4), 2, [&](int r) { return r * BY + q; },
                        [&](int f) -> const S * { return recZ[q][f][ii]; });
         }
         S red[NRED];
@@ -636,9 +662,12 @@ rt_status launch_rev_t(rt_ctx *c, const RevArgs &A) {
     return RT_OK;
 }
 template <class LT, bool FUSE> rt_status launch_rev_b(rt_ctx *c, const RevArgs &A) {
-    // brick shapes as the forward stage kernel picks them
+    // brick shapes as the forward stage kernel picks them (2 x 1 in place of 2 x 2 where the lane type asks)
     const bool by = A.act[1] && A.nx[1] % 2 == 0, bz = A.act[2] && A.nx[2] % 2 == 0;
-    if (by && bz) return launch_rev_t<LT, 2, 2, FUSE>(c, A);
+    (void)bz;
+    if constexpr (LT::BRICK22) {
+        if (by && bz) return launch_rev_t<LT, 2, 2, FUSE>(c, A);
+    }
     if (by) return launch_rev_t<LT, 2, 1, FUSE>(c, A);
     return launch_rev_t<LT, 1, 1, FUSE>(c, A);
 }
