@@ -181,10 +181,38 @@ __device__ __forceinline__ typename LT::V face_tau(typename LT::V phib, typename
     return phib * v;
 }
 
+// Per-cell FP64 arithmetic without FP64 divisions or square roots, which are
+// long instruction sequences on this part's FP64 pipe (1/64 of the FP32 rate):
+// an FP32 estimate refined by two FP64 Newton steps (relative error at the
+// FP64 rounding level), with the exact operation outside the FP32 range.
+__device__ __forceinline__ double rcp_nr(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {   // x > 0
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    const double h = 0.5 * x;
+    y = y * fma(-h * y, y, 1.5);
+    return y * fma(-h * y, y, 1.5);
+}
+// T^-p and 1/T (T > 0); for p = 3.5 both from r = T^-1/2: T^-3.5 = r^7, 1/T = r^2
+__device__ __forceinline__ void tpow_inv(double T, double p, double &tp, double &iT) {
+    if (p == 3.5) {
+        const double r = rsqrt_nr(T), r2 = r * r, r6 = r2 * r2 * r2;
+        tp = r6 * r; iT = r2;
+    } else {
+        tp = tpow_neg<double>(T, p); iT = rcp_nr(T);
+    }
+}
+
 // rho^m = (kappa rho^m) / kappa, the derivative of alpha^a's prefactor in
 // kappa, without an FP64 pow where kappa is nonzero
 __device__ __forceinline__ double rho_m(double au, double kap, double rho, double m) {
-    return kap != 0.0 ? au / kap : pow(rho, m);
+    return kap != 0.0 ? au * rcp_nr(kap) : pow(rho, m);
 }
 
 // Reverse of the interaction of section 3.5.2 (method 3) in one cell at rest,
@@ -202,22 +230,23 @@ __device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, d
     SrcRev o{1.0, 0.0, 0.0, ub, 0.0, 0.0};
     if (!on) return o;
     constexpr double i4pi = 1.0 / FOURPI;
-    const double iY = 1.0 / Y, Tm = ugm * iY;
-    const double tm = tpow_neg<double>(Tm, p), am = au * tm + as;
-    const double adt = am * dt, i1a = 1.0 / (1.0 + adt), K = adt * i1a, B2 = K * S * dt * i4pi;
+    const double iY = rcp_nr(Y), Tm = ugm * iY;
+    double tm, iTm, tp, iTp;
+    tpow_inv(Tm, p, tm, iTm);
+    const double am = au * tm + as;
+    const double adt = am * dt, i1a = rcp_nr(1.0 + adt), K = adt * i1a, B2 = K * S * dt * i4pi;
     const double Tp = Tm + (Em - X) * iY;
-    const double tp = tpow_neg<double>(Tp, p), aap = au * tp;
+    tpow_inv(Tp, p, tp, iTp);
+    const double aap = au * tp;
     const double Tp4 = Tp * Tp * Tp * Tp;
     const double a = (aap + as) * dt;
     const double cc = dt * (eta * aap * ar * Tp4 + as * X) * i4pi;
-    const double inv = 1.0 / (1.0 + a);
+    const double inv = rcp_nr(1.0 + a);
     const double Ep = (Em + cc * S) * inv;
     const double sIpb = P - ub * S;                 // sum_s Ipb_s, Ipb_s = Ibo_s - ub w_s
     const double ccb = sIpb * inv;
     const double Ab = -(Q - ub * Ep) * inv;         // d/dA of sum_s Ipb_s I_+s = -sum_s Ipb_s I_+s / A
     double aapb = Ab * dt;
-    // 1/T without a division for p = 3.5: T^2 sqrt(T) T^-3.5
-    const double iTp = p == 3.5 ? Tp * Tp * sqrt(Tp) * tp : 1.0 / Tp;
     const double ccbd = ccb * dt * i4pi;
     double etab = ccbd * aap * ar * Tp4;
     aapb += ccbd * eta * ar * Tp4;
@@ -231,7 +260,7 @@ __device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, d
     const double lin = (aap + as) * dt - B2 * as;
     const double hT = -p * aap * iTp * dt * X - B2 * eta * ar * (4.0 - p) * aap * Tp * Tp * Tp;
     const double hX = lin - hT * iY;
-    const double lam = -Xb / hX;
+    const double lam = -Xb * rcp_nr(hX);
     const double B1b = -lam;
     const double B2b = lam * (-as * X - eta * ar * aap * Tp4);
     Tmb += lam * hT;
@@ -242,7 +271,7 @@ __device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, d
     Emb += B1b * K;
     const double amb = Kb * dt * i1a * i1a;
     aub += amb * tm;
-    Tmb += amb * (-p) * au * tm * (p == 3.5 ? Tm * Tm * tm * sqrt(Tm) : 1.0 / Tm);
+    Tmb += amb * (-p) * au * tm * iTm;
     o.inv = inv; o.ub = ub; o.Emb = Emb;
     o.ugb = ub + Tmb * iY;
     o.kb = aub * rho_m(au, kap, rho, rho_exp);
@@ -588,11 +617,12 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
             double t = A.ubA ? A.ubA[c] : 0.0, kbv = 0.0;
             // alpha = kappa rho^m T^-p + alpha^s with T = u_g / Y
             if (A.transport && A.cc_on[c] && abar != 0.0) {
-                const double Ta = Y > 0.0 ? A.ug_a[c] / Y : 0.0;
+                const double iY = Y > 0.0 ? rcp_nr(Y) : 0.0, Ta = A.ug_a[c] * iY;
                 if (Ta > 0.0) {
-                    const double tp = tpow_neg<double>(Ta, A.T_exp);
+                    double tp, iTa;
+                    tpow_inv(Ta, A.T_exp, tp, iTa);
                     kbv = abar * rho_m(au, A.kap[c], A.rho[c], A.rho_exp) * tp;
-                    t += abar * au * (-A.T_exp) * tp / Ta / Y;
+                    t += abar * au * (-A.T_exp) * tp * iTa * iY;
                 }
             }
             if constexpr (!FUSE) {
@@ -600,8 +630,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 A.kb[c] += kbv;
             } else {
                 const double ugm = A.ugm[c], as = A.cc_as[c];
-                const double Tm = Y > 0.0 ? ugm / Y : 0.0;
-                const double am = (A.cc_on[c] && Tm > 0.0) ? au * tpow_neg<double>(Tm, A.T_exp) + as : 0.0;
+                const double Tm = Y > 0.0 ? ugm * rcp_nr(Y) : 0.0;
+                double tmv = 0.0, iTmv = 0.0;
+                if (Tm > 0.0) tpow_inv(Tm, A.T_exp, tmv, iTmv);
+                const double am = (A.cc_on[c] && Tm > 0.0) ? au * tmv + as : 0.0;
                 const bool on = A.source && A.cc_on[c] && am > 0.0 && Y > 0.0 && ugm > 0.0;
                 double P = 0.0, Q = 0.0;
                 for (int g = 0; g < NW; ++g) { P += (double)partP[g][lc]; Q += (double)part[g][NOWN + o][ii]; }
