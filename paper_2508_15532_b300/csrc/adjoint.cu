@@ -121,10 +121,32 @@ template <> __device__ __forceinline__ void lim_half<double>(int kind, double dl
 }
 // per lane type, with gd = gr - gl: one packed subtraction for FP32 pairs;
 // selects for FP64, which keeps the subtraction off the FP64 pipe
+// FP32 pairs: dl dr and (dl + dr)/4 as packed operations, the rest per lane
+__device__ __forceinline__ void lim_pre(int kind, float dl, float dr, float prod, float q4, float &hs, float &gl, float &gr) {
+    const float al = fabsf(dl), ar = fabsf(dr);
+    const bool ok = prod > 0.0f;
+    if (kind == RT_LIM_MC) {
+        const float q = fabsf(q4);
+        const bool w1 = ar < al;
+        const float m1 = w1 ? ar : al;
+        const bool w2 = q < m1;
+        const float m = w2 ? q : m1;
+        hs = ok ? copysignf(m, dl) : 0.0f;
+        gl = ok ? (w2 ? 0.25f : (w1 ? 0.0f : 1.0f)) : 0.0f;
+        gr = ok ? (w2 ? 0.25f : (w1 ? 1.0f : 0.0f)) : 0.0f;
+    } else if (kind == RT_LIM_MINMOD) {
+        const bool wl = al < ar;
+        hs = ok ? copysignf(0.5f * (wl ? al : ar), dl) : 0.0f;
+        gl = (ok && wl) ? 0.5f : 0.0f;
+        gr = (ok && !wl) ? 0.5f : 0.0f;
+    } else {
+        hs = 0.0f; gl = 0.0f; gr = 0.0f;
+    }
+}
 __device__ __forceinline__ void limv(int kind, F2 dl, F2 dr, F2 &hs, F2 &gl, F2 &gr, F2 &gd) {
-    float ux, uy;   // (the scalar differences are dropped: one packed subtraction is cheaper)
-    lim_half<float>(kind, dl.x, dr.x, hs.x, gl.x, gr.x, ux);
-    lim_half<float>(kind, dl.y, dr.y, hs.y, gl.y, gr.y, uy);
+    const F2 prod = dl * dr, q4 = f2(0.25f) * (dl + dr);
+    lim_pre(kind, dl.x, dr.x, prod.x, q4.x, hs.x, gl.x, gr.x);
+    lim_pre(kind, dl.y, dr.y, prod.y, q4.y, hs.y, gl.y, gr.y);
     gd = gr - gl;
 }
 __device__ __forceinline__ void limv(int kind, double dl, double dr, double &hs, double &gl, double &gr, double &gd) {
@@ -279,6 +301,14 @@ __device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, d
     return o;
 }
 
+// asynchronous 8-byte global -> shared copy; waiting for all but the newest group
+__device__ __forceinline__ void cp_async8f(float *smem, const float *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // N values per lane -> every lane l holds the warp sum of value l % N
 // (N a power of two <= 32; N - 1 + 5 - log2 N shuffles)
 template <int N, typename R> __device__ __forceinline__ R tsum_n(R (&v)[N], int lane) {
@@ -352,6 +382,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     __shared__ S part[NW][NRED][TXC];
     __shared__ S partP[NW][RNC];
     __shared__ double cInv[RNC], cUb[RNC], cEmb[RNC];
+    // FP32 pass: the x1 pipeline's next own-row values (I and Zg at x1 = i + 3)
+    // are copied one position ahead with cp.async (double-buffered)
+    constexpr bool PFX = L == 2;
+    __shared__ __align__(16) S pfb[2][2 * NOWN][PFX ? NT * L : 2];
     extern __shared__ __align__(16) unsigned char dsm[];   // FUSE: cotangents of I_+ [RNC][NT L]
     S *sIt = reinterpret_cast<S *>(dsm);
 
@@ -471,6 +505,22 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
 
     const V wdir = LT::wv(A.w, d0);
     (void)wdir;
+    // copies of position ii + 2 of the window (x1 = i0 + ii + 2) into stage ii & 1
+    auto pf_issue = [&](int ii) {
+        if constexpr (PFX) {
+            if (!act) return;
+            const int xd = xmap[ii + 4], st = ii & 1;
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                const int off = own(o) + (xd & F_IDX) * nd;
+                cp_async8f(&pfb[st][o][d0], (const float *)Ip + off);
+                if (!(xd & F_OUT)) cp_async8f(&pfb[st][NOWN + o][d0], (const float *)Zp + off);
+            }
+        }
+    };
+    if constexpr (PFX) {
+        if (xon) { pf_issue(0); cp_commit(); }
+    }
 #pragma unroll 1
     for (int ii = 0; ii < nc; ++ii) {
         const int i = i0 + ii, ie = i * nd;
@@ -478,10 +528,24 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         if (xon) {
             const int xd = xmap[ii + 4];
             const bool hiE = !A.per[0] && i == nx0 - 1;
+            if constexpr (PFX) {
+                if (ii + 1 < nc) pf_issue(ii + 1);
+                cp_commit();
+                cp_wait1();
+            }
 #pragma unroll
             for (int o = 0; o < NOWN; ++o) {
                 const int off = own(o) + (xd & F_IDX) * nd;
-                const V I2 = ldI(off), Z2 = (xd & F_OUT) ? zero : ldZ(off);
+                V I2, Z2;
+                if constexpr (PFX) {
+                    const float2 a = *reinterpret_cast<const float2 *>(&pfb[ii & 1][o][d0]);
+                    const float2 b = *reinterpret_cast<const float2 *>(&pfb[ii & 1][NOWN + o][d0]);
+                    I2 = LT::splat(0); Z2 = zero;
+                    if constexpr (L == 2) { I2 = F2{a.x, a.y}; if (!(xd & F_OUT)) Z2 = F2{b.x, b.y}; }
+                    (void)off;
+                } else {
+                    I2 = ldI(off); Z2 = (xd & F_OUT) ? zero : ldZ(off);
+                }
                 const V dr = xI1[o] - xI0[o], dl = I2 - xI1[o];
                 V hsN, glN, grN, gdN;
                 limv(lim, dl, dr, hsN, glN, grN, gdN);
