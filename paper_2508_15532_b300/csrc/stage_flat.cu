@@ -416,12 +416,14 @@ __device__ __forceinline__ F2 mc_half2(F2 dl, F2 dr) {
     float my = fminf(fminf(fabsf(dl.y), fabsf(dr.y)), fabsf(h.y));
     return F2{pr.x > 0.0f ? copysignf(mx, dl.x) : 0.0f, pr.y > 0.0f ? copysignf(my, dl.y) : 0.0f};
 }
-// the face flux per component: n (cL I_L + cR I_R) - |n| c3 (I_r - I_l)
+// the face flux per component, n (cL I_L + cR I_R) - |n| c3 (I_r - I_l) with
+// (cL, cR) = (c1, c2) for n > 0 and (c2, c1) for n < 0, written without
+// selects: n cL = n P + |n| D, n cR = n P - |n| D (P = (c1 + c2)/2,
+// D = (c1 - c2)/2), so the flux is n P (I_L + I_R) + |n| (D (I_L - I_R) - c3 (I_r - I_l));
+// the record holds (P, D, -c3)
 __device__ __forceinline__ F2 phi2(F2 n, F2 an, const Rec4<float> &r, F2 IL, F2 IR, F2 Il, F2 Ir) {
-    const F2 cL = F2{n.x > 0.0f ? r.c1 : r.c2, n.y > 0.0f ? r.c1 : r.c2};
-    const F2 cR = F2{n.x > 0.0f ? r.c2 : r.c1, n.y > 0.0f ? r.c2 : r.c1};
-    const F2 t = fma2(cR, IR, cL * IL);
-    return n * t - (an * f2(r.c3)) * (Ir - Il);
+    const F2 u = fma2(f2(r.c3), Ir - Il, f2(r.c2) * (IL - IR));
+    return fma2(n * f2(r.c1), IL + IR, an * u);
 }
 
 constexpr int FP2_NT = 96;
@@ -475,9 +477,10 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
         if (tau > 0.0) {
             float t = (float)tau;
             float f = sqrtf(-expm1f(-t * t)) / t, g = sqrtf(-expm1f(-t * t * t * t)) / t, e = expf(-t), fg = f + g;
-            r.c1 = f * e / fg; r.c2 = g * e / fg; r.c3 = f * g / fg;
+            const float c1 = f * e / fg, c2 = g * e / fg;
+            r.c1 = 0.5f * (c1 + c2); r.c2 = 0.5f * (c1 - c2); r.c3 = -(f * g / fg);
         } else {
-            r.c1 = 1.0f; r.c2 = 0.0f; r.c3 = 0.0f;
+            r.c1 = 0.5f; r.c2 = 0.5f; r.c3 = 0.0f;
         }
         r.pad = 0.0f;
     };
