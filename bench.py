@@ -40,9 +40,12 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 # DRAM traffic of one stage-kernel launch from an ncu capture (bytes per
 # cell-angle), valid only for the stage-kernel source it was measured on.
 # DRAM bytes (read + write) per cell-angle per stage launch, averaged over the
-# two launches of a step, from an ncu capture of the 64^3 box; traffic scales
-# with the cells (each cell is read once per source array and written once)
-NCU_TRAFFIC = {("d10c995995fd", "fp32", "flat3d"): 9.97}   # {(sha1 of the stage sources, precision, workload): B}
+# two launches of a step, from an ncu capture of a 64^3 box (kerr3d: 64^3 cells
+# of the torus recipe); traffic scales with the cells (each cell is read once
+# per source array and written once; the Kerr-Schild tables are per (r, theta)
+# point and are mostly served from L1/L2)
+NCU_TRAFFIC = {("210af1ad0ab8", "fp32", "flat3d"): 9.99,
+               ("210af1ad0ab8", "fp32", "kerr3d"): 13.09}   # {(sha1 of the stage sources, precision, workload): B}
 STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
