@@ -192,3 +192,35 @@ def test_full_box_fp32_sampled_against_oracle():
         assert rel_err(Ig, Ir, 1e-3).max() < 1e-4, st
         ur = ref["ug"].reshape(n, n, n)[c, c, c]
         assert rel_err(u3[sel][c, c, c], ur).max() < 1e-4, st
+
+
+def test_flat_fp32_100_steps_against_fp64_oracle():
+    """The FP32 path over the 100 steps its bars are stated for: every
+    intensity within 1e-4 (floor 1e-3 of the largest) and the comoving energy
+    density within 2e-5 of the FP64 oracle."""
+    cfg, f = small_flat(nx=(16, 12, 8), n_geo=4, index=27)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 100)
+    out = run_gpu(cfg, f, dt, 100, "fp32")
+    assert out["fails"] == 0
+    assert rel_err(out["I"], ref["I"], 1e-3).max() < 1e-4
+    assert rel_err(out["E"], ref["E"]).max() < 2e-5
+
+
+def test_kerr_storage_modes_moments_against_fp64():
+    """Kerr-Schild torus in 3D (pole boundaries, angular fluxes): FP32 and BF16
+    storage against the FP64 run (itself held to the oracle at 1e-11), on the
+    energy density and the flux moments R^{0i}.  FP32: 2e-5 on E-bar and 1e-4
+    of the largest flux component; BF16 (FP32 arithmetic): the per-intensity
+    bound 2 K 2^-9 after K steps on both."""
+    K = 5
+    cfg, f = W.kerr(nr=32, nth=16, nph=8, n_geo=4, index=41)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_gpu(cfg, f, dt, K, "fp64")
+    fl = ref["R"][:, 1:4]
+    for precision, e_bar, f_bar in (("fp32", 2e-5, 1e-4), ("bf16", 2 * K * 2.0 ** -9, 2 * K * 2.0 ** -9)):
+        out = run_gpu(cfg, f, dt, K, precision)
+        assert out["fails"] == 0
+        assert rel_err(out["E"], ref["E"]).max() < e_bar, precision
+        err_f = np.abs(out["R"][:, 1:4] - fl).max() / np.abs(fl).max()
+        assert err_f < f_bar, (precision, err_f)
