@@ -367,7 +367,9 @@ struct RevArgs {
     const uint8_t *cc_on;
 };
 
-template <class LT, int BY, int BZ, bool FUSE>
+// LK: the limiter kind fixed at compile time (RT_LIM_MC, the limiter of every
+// workload here), or -1 to read it from the arguments
+template <class LT, int BY, int BZ, bool FUSE, int LK>
 __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     using S = typename LT::S;
     using V = typename LT::V;
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     auto cf = [&](int a) { return LT::splat(cfs[a]); };
     auto hv = [&](int a) { return LT::splat(hvs[a]); };
     const V zero = LT::splat(S(0));
-    const int lim = A.limiter;
+    const int lim = LK >= 0 ? LK : A.limiter;
     const S *Ip = (const S *)A.I, *Zp = (const S *)A.Zg, *Zo = (const S *)A.Zown;
     auto ldI = [&](int off) -> V { return LT::ld(Ip + off); };
     auto ldZ = [&](int off) -> V { return LT::ld(Zp + off); };
@@ -751,7 +753,7 @@ rt_status launch_rev_t(rt_ctx *c, const RevArgs &A) {
     constexpr int TXC = RNC / (BY * BZ);
     const size_t nblk = (size_t)((A.nx[0] + TXC - 1) / TXC) * (A.nx[1] / BY) * (A.nx[2] / BZ);
     const int dyn = FUSE ? (int)(RNC * LT::NT * LT::L * sizeof(typename LT::S)) : 0;
-    auto kern = k_rev<LT, BY, BZ, FUSE>;
+    auto kern = A.limiter == RT_LIM_MC ? k_rev<LT, BY, BZ, FUSE, RT_LIM_MC> : k_rev<LT, BY, BZ, FUSE, -1>;
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     kern<<<(unsigned)nblk, LT::NT, dyn, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
