@@ -177,6 +177,27 @@ rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, 
                           const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,
                           double *dL_dug_in, double *dL_dkappa, double *dL_deta);
 
+/* Forward steps that keep their stage states for the reverse pass.  Same
+ * steps, results and end state as rt_step (dt <= 0: the cfl bound with cfl
+ * 0.4; *dt_used, may be NULL, receives the step size), with the scope of
+ * rt_step_adjoint.  Every stage's states (the ones rt_step_adjoint recomputes
+ * from its checkpoint) are written to the library-owned reverse-mode arena,
+ * and *rec_id receives a positive id of that recording.  Checkpointing
+ * schemes keep the states of their last segment this way, so that its reverse
+ * (rt_step_adjoint_recorded) needs no recompute; the paper has no counterpart.
+ * A later rt_step_record, rt_step_adjoint or rt_set_fluid replaces the
+ * recording.  Stream-ordered; the states cost the arena of rt_step_adjoint
+ * for nsteps. */
+rt_status rt_step_record(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *rec_id);
+
+/* rt_step_adjoint for the steps of the recording rec_id (rt_step_record),
+ * without the recompute: same arguments and results as rt_step_adjoint from
+ * the recording's start state, with its nsteps and dt.  RT_ESTATE if rec_id
+ * is not the context's current recording. */
+rt_status rt_step_adjoint_recorded(rt_ctx *c, long long rec_id, const double *dL_dI_out,
+                                   const double *dL_dug_out, double *dL_dI_in, double *dL_dug_in,
+                                   double *dL_dkappa, double *dL_deta);
+
 /* Launch timing of the stage kernel (no counterpart in the paper: a
  * measurement hook).  rt_set_timing(c, 1) makes rt_step record a CUDA event
  * pair around every stage launch on the context's stream; rt_get_timing

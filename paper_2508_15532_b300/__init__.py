@@ -47,7 +47,8 @@ _lib = None
 EXPORTS = ["rt_create_geodesic_grid", "rt_grid_query", "rt_destroy_grid", "rt_create", "rt_destroy",
            "rt_last_error", "rt_set_metric", "rt_set_fluid", "rt_set_intensity", "rt_get_intensity",
            "rt_set_ugas", "rt_get_ugas", "rt_cfl_dt", "rt_step", "rt_moments", "rt_grid_last_error",
-           "rt_set_timing", "rt_get_timing", "rt_cfl_dt_noalloc", "rt_step_adjoint"]
+           "rt_set_timing", "rt_get_timing", "rt_cfl_dt_noalloc", "rt_step_adjoint",
+           "rt_step_record", "rt_step_adjoint_recorded"]
 
 
 def lib():
@@ -81,6 +82,8 @@ def lib():
         L.rt_get_timing.argtypes = [vp, C.POINTER(d), C.POINTER(C.c_longlong)]
         L.rt_cfl_dt_noalloc.argtypes = [vp, d, C.POINTER(d)]
         L.rt_step_adjoint.argtypes = [vp, vp, vp, d, i, vp, vp, vp, vp, vp, vp]
+        L.rt_step_record.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_longlong)]
+        L.rt_step_adjoint_recorded.argtypes = [vp, C.c_longlong, vp, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -160,6 +163,8 @@ class RadiationStep:
         if st:
             raise RTError(st, lib().rt_last_error(None).decode())
         self.h = h
+        self.fluid_token = None
+        self.rec_id = 0
         self.nd = grid.nd
         self.ncell = int(np.prod(cfg["nx"]))
         self._check(lib().rt_set_metric(h, METRIC[cfg.get("coords", "minkowski")],
@@ -176,6 +181,8 @@ class RadiationStep:
 
     def set_fluid(self, rho, ug, ucon, kappa, alpha_s, eta=None):
         self._keep = (rho, ug, ucon, kappa, alpha_s, eta)
+        self.fluid_token = object()    # identifies this fluid (the library drops its recording)
+        self.rec_id = 0
         self._check(lib().rt_set_fluid(self.h, _ptr(rho), _ptr(ug), _ptr(ucon), _ptr(kappa), _ptr(alpha_s), _ptr(eta)))
 
     def set_intensity(self, I):
@@ -215,9 +222,26 @@ class RadiationStep:
                      dL_dkappa, dL_deta):
         """Reverse of nsteps steps from the checkpoint (rt_step_adjoint):
         writes dL_dI_in, dL_dug_in and adds to dL_dkappa, dL_deta."""
+        self.rec_id = 0    # the recompute replaces any recording
         self._check(lib().rt_step_adjoint(self.h, _ptr(I_ckpt), _ptr(ug_ckpt), float(dt), int(nsteps),
                                           _ptr(dL_dI_out), _ptr(dL_dug_out), _ptr(dL_dI_in), _ptr(dL_dug_in),
                                           _ptr(dL_dkappa), _ptr(dL_deta)))
+
+    def step_record(self, dt, nsteps):
+        """nsteps steps as step(), keeping every stage's states for the
+        reverse pass (rt_step_record); returns the recording's id."""
+        used = C.c_double()
+        rid = C.c_longlong()
+        self.rec_id = 0
+        self._check(lib().rt_step_record(self.h, float(dt), int(nsteps), C.byref(used), C.byref(rid)))
+        self.rec_id = rid.value
+        return rid.value
+
+    def step_adjoint_recorded(self, rec_id, dL_dI_out, dL_dug_out, dL_dI_in, dL_dug_in, dL_dkappa, dL_deta):
+        """Reverse of the recorded steps without their recompute
+        (rt_step_adjoint_recorded)."""
+        self._check(lib().rt_step_adjoint_recorded(self.h, int(rec_id), _ptr(dL_dI_out), _ptr(dL_dug_out),
+                                                   _ptr(dL_dI_in), _ptr(dL_dug_in), _ptr(dL_dkappa), _ptr(dL_deta)))
 
     def set_timing(self, on=True):
         self._check(lib().rt_set_timing(self.h, int(bool(on))))

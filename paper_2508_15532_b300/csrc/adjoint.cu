@@ -774,28 +774,42 @@ static rt_status launch_rev(rt_ctx *c, const RevArgs &A, bool fuse) {
     return fuse ? launch_rev_b<LaneF, true>(c, A) : launch_rev_b<LaneF, false>(c, A);
 }
 
-}  // namespace
+// The reverse pass's arena: the states of every stage of a run of N steps
+// (the stage inputs I^0..I^N and the predictor outputs I*, u_g^0..u_g^N and
+// u_g*, the stages' face opacities, the saved E-bar_- and roots), two
+// cotangent buffers in the storage type and two gas-energy cotangents.  The
+// layout depends only on N and the configuration, so a later call with the
+// same N finds the same pointers.
+struct AdjArena {
+    int N = 0;
+    std::vector<void *> In, Bs;
+    std::vector<double *> un, us, aln, als, sE, sX;
+    void *Z[2] = {nullptr, nullptr};
+    double *ubc = nullptr, *ubp = nullptr;
+};
 
-extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,
-                                     const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,
-                                     double *dL_dug_in, double *dL_dkappa, double *dL_deta) {
-    if (!c) return RT_EINVAL;
-    if (!I_ckpt || !ug_ckpt || !dL_dI_out || !dL_dI_in || !dL_dug_in || !dL_dkappa || !dL_deta || nsteps < 1)
-        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: null pointer or nsteps < 1");
-    if (c->metric < 0 || !c->have_fluid) return adj_fail(c, RT_ESTATE, "rt_set_metric and rt_set_fluid must precede rt_step_adjoint");
+static long long g_rec_counter = 0;   // ids of forward recordings (rt_step_record)
+
+static rt_status adj_check(rt_ctx *c, const char *who) {
+    const std::string w(who);
+    if (c->metric < 0 || !c->have_fluid) return adj_fail(c, RT_ESTATE, "rt_set_metric and rt_set_fluid must precede " + w);
     if (c->metric != RT_MINKOWSKI_CART || !c->static_fluid)
-        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: flat Cartesian geometry with the fluid at rest only");
-    if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: FP64 or FP32 intensities only");
-    if (c->nd > LaneD::NT || c->nd % 2) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: at most 192 directions");
+        return adj_fail(c, RT_EINVAL, w + ": flat Cartesian geometry with the fluid at rest only");
+    if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, w + ": FP64 or FP32 intensities only");
+    if (c->nd > LaneD::NT || c->nd % 2) return adj_fail(c, RT_EINVAL, w + ": at most 192 directions");
     if ((double)c->ncell * c->nd >= 2147483647.0)
-        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: n_cell * n_dir must be below 2^31");
+        return adj_fail(c, RT_EINVAL, w + ": n_cell * n_dir must be below 2^31");
     for (int a = 0; a < 3; ++a) {
         if (!c->active[a]) continue;
         int b0 = c->cfg.bc[a][0], b1 = c->cfg.bc[a][1];
         bool per = b0 == RT_BC_PERIODIC && b1 == RT_BC_PERIODIC, out = b0 == RT_BC_OUTFLOW && b1 == RT_BC_OUTFLOW;
-        if (!per && !out) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: periodic or outflow boundaries on both sides of an axis only");
-        if (per && c->cfg.nx[a] < 4) return adj_fail(c, RT_EINVAL, "rt_step_adjoint: periodic axes need at least 4 cells");
+        if (!per && !out) return adj_fail(c, RT_EINVAL, w + ": periodic or outflow boundaries on both sides of an axis only");
+        if (per && c->cfg.nx[a] < 4) return adj_fail(c, RT_EINVAL, w + ": periodic axes need at least 4 cells");
     }
+    return RT_OK;
+}
+
+static rt_status adj_dt(rt_ctx *c, double &dt) {
     if (!(dt > 0.0)) {
         if (c->dt_cfl <= 0.0) {
             rt_status st = rt_cfl_dt(c, 0.4, &c->dt_cfl);
@@ -803,20 +817,19 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
         }
         dt = c->dt_cfl;
     }
-    const rt_config &f = c->cfg;
+    return RT_OK;
+}
+
+static rt_status adj_layout(rt_ctx *c, int N, AdjArena &ar) {
     const size_t nc = (size_t)c->ncell, ni = nc * c->nd, es = c->esize;
-    const int order = f.order, ns = order == 2 ? 2 : 1;   // stages per step
-    const int N = nsteps;
-    // arena: the stage inputs I^0..I^N (and the predictor outputs I*), two
-    // cotangent buffers in the storage type, and per-cell FP64 arrays: u_g^0..u_g^N
-    // (and u_g*), the stages' face opacities, the saved E-bar_- and roots, two
-    // gas-energy cotangents
+    const int order = c->cfg.order, ns = order == 2 ? 2 : 1;   // stages per step
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t bI = up(ni * es), bC = up(nc * 8);
     const size_t nI = (size_t)(N + 1) + (order == 2 ? N : 0) + 2;
     const size_t nCell = (size_t)(N + 1) * 2 + (order == 2 ? 2 * (size_t)N : 0) + 2 * (size_t)N * ns + 2;
     const size_t need = nI * bI + nCell * bC;
     if (c->adj_bytes < need) {
+        c->rec_id = 0;
         if (c->adj) cudaFree(c->adj);
         c->adj = nullptr; c->adj_bytes = 0;
         RT_CUDA_TRY(c, cudaMalloc(&c->adj, need));
@@ -824,41 +837,62 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     }
     char *p = (char *)c->adj;
     auto take = [&](size_t b) { char *r = p; p += b; return r; };
-    std::vector<void *> In(N + 1), Bs(N);
-    std::vector<double *> un(N + 1), us(N), aln(N + 1), als(N), sE(N * ns), sX(N * ns);
-    for (int n = 0; n <= N; ++n) In[n] = take(bI);
-    if (order == 2) for (int n = 0; n < N; ++n) Bs[n] = take(bI);
-    void *Z[2] = {take(bI), take(bI)};
-    for (int n = 0; n <= N; ++n) { un[n] = (double *)take(bC); aln[n] = (double *)take(bC); }
-    if (order == 2) for (int n = 0; n < N; ++n) { us[n] = (double *)take(bC); als[n] = (double *)take(bC); }
-    for (int s = 0; s < N * ns; ++s) { sE[s] = (double *)take(bC); sX[s] = (double *)take(bC); }
-    double *ubc = (double *)take(bC), *ubp = (double *)take(bC);
+    ar.N = N;
+    ar.In.assign(N + 1, nullptr); ar.Bs.assign(N, nullptr);
+    ar.un.assign(N + 1, nullptr); ar.aln.assign(N + 1, nullptr); ar.us.assign(N, nullptr); ar.als.assign(N, nullptr);
+    ar.sE.assign(N * ns, nullptr); ar.sX.assign(N * ns, nullptr);
+    for (int n = 0; n <= N; ++n) ar.In[n] = take(bI);
+    if (order == 2) for (int n = 0; n < N; ++n) ar.Bs[n] = take(bI);
+    ar.Z[0] = take(bI); ar.Z[1] = take(bI);
+    for (int n = 0; n <= N; ++n) { ar.un[n] = (double *)take(bC); ar.aln[n] = (double *)take(bC); }
+    if (order == 2) for (int n = 0; n < N; ++n) { ar.us[n] = (double *)take(bC); ar.als[n] = (double *)take(bC); }
+    for (int s = 0; s < N * ns; ++s) { ar.sE[s] = (double *)take(bC); ar.sX[s] = (double *)take(bC); }
+    ar.ubc = (double *)take(bC); ar.ubp = (double *)take(bC);
+    return RT_OK;
+}
 
-    // 1. forward recompute from the checkpoint with the stage kernels
+// forward run from (In[0], un[0]) with the stage kernels, saving every
+// stage's state; G_last (may be null) receives the force of the last stage
+static rt_status adj_forward(rt_ctx *c, const AdjArena &ar, double dt, double *G_last) {
     struct SaveGuard {
         rt_ctx *c;
         ~SaveGuard() { c->sv_Em = nullptr; c->sv_X = nullptr; }
     } guard{c};
-    RT_CUDA_TRY(c, cudaMemcpyAsync(In[0], I_ckpt, ni * es, cudaMemcpyDeviceToDevice, c->stream));
-    RT_CUDA_TRY(c, cudaMemcpyAsync(un[0], ug_ckpt, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const int N = ar.N;
     rt_status st;
-    if ((st = rt_launch_alpha(c, un[0], aln[0])) != RT_OK) return st;
+    if ((st = rt_launch_alpha(c, ar.un[0], ar.aln[0])) != RT_OK) return st;
     for (int n = 0; n < N; ++n) {
-        if (order == 2) {
-            c->sv_Em = sE[2 * n]; c->sv_X = sX[2 * n];
-            st = rt_launch_stage(c, In[n], In[n], Bs[n], un[n], us[n], aln[n], aln[n], als[n], 0.5 * dt, nullptr);
+        double *G = n == N - 1 ? G_last : nullptr;
+        if (c->cfg.order == 2) {
+            c->sv_Em = ar.sE[2 * n]; c->sv_X = ar.sX[2 * n];
+            st = rt_launch_stage(c, ar.In[n], ar.In[n], ar.Bs[n], ar.un[n], ar.us[n], ar.aln[n], ar.aln[n], ar.als[n],
+                                 0.5 * dt, nullptr);
             if (st != RT_OK) return st;
-            c->sv_Em = sE[2 * n + 1]; c->sv_X = sX[2 * n + 1];
-            st = rt_launch_stage(c, Bs[n], In[n], In[n + 1], un[n], un[n + 1], als[n], aln[n], aln[n + 1], dt, nullptr);
+            c->sv_Em = ar.sE[2 * n + 1]; c->sv_X = ar.sX[2 * n + 1];
+            st = rt_launch_stage(c, ar.Bs[n], ar.In[n], ar.In[n + 1], ar.un[n], ar.un[n + 1], ar.als[n], ar.aln[n],
+                                 ar.aln[n + 1], dt, G);
         } else {
-            c->sv_Em = sE[n]; c->sv_X = sX[n];
-            st = rt_launch_stage(c, In[n], In[n], In[n + 1], un[n], un[n + 1], aln[n], aln[n], aln[n + 1], dt, nullptr);
+            c->sv_Em = ar.sE[n]; c->sv_X = ar.sX[n];
+            st = rt_launch_stage(c, ar.In[n], ar.In[n], ar.In[n + 1], ar.un[n], ar.un[n + 1], ar.aln[n], ar.aln[n],
+                                 ar.aln[n + 1], dt, G);
         }
         if (st != RT_OK) return st;
     }
-    c->sv_Em = nullptr; c->sv_X = nullptr;
+    return RT_OK;
+}
 
-    // 2. reverse sweep
+// reverse sweep over the arena's N steps
+static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const double *dL_dI_out,
+                             const double *dL_dug_out, double *dL_dI_in, double *dL_dug_in, double *dL_dkappa,
+                             double *dL_deta) {
+    const rt_config &f = c->cfg;
+    const size_t ni = (size_t)c->ncell * c->nd;
+    const int order = f.order, ns = order == 2 ? 2 : 1, N = ar.N;
+    const auto &In = ar.In, &Bs = ar.Bs;
+    const auto &un = ar.un, &us = ar.us, &aln = ar.aln, &als = ar.als, &sE = ar.sE, &sX = ar.sX;
+    void *const Z[2] = {ar.Z[0], ar.Z[1]};
+    double *ubc = ar.ubc, *ubp = ar.ubp;
+    rt_status st;
     RevArgs B{};
     for (int a = 0; a < 3; ++a) {
         B.nx[a] = f.nx[a]; B.act[a] = c->active[a]; B.per[a] = f.bc[a][0] == RT_BC_PERIODIC;
@@ -934,4 +968,72 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
         }
     }
     return RT_OK;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,
+                                     const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,
+                                     double *dL_dug_in, double *dL_dkappa, double *dL_deta) {
+    if (!c) return RT_EINVAL;
+    if (!I_ckpt || !ug_ckpt || !dL_dI_out || !dL_dI_in || !dL_dug_in || !dL_dkappa || !dL_deta || nsteps < 1)
+        return adj_fail(c, RT_EINVAL, "rt_step_adjoint: null pointer or nsteps < 1");
+    rt_status st;
+    if ((st = adj_check(c, "rt_step_adjoint")) != RT_OK) return st;
+    if ((st = adj_dt(c, dt)) != RT_OK) return st;
+    // the recompute overwrites the arena, and with it any recording
+    c->rec_id = 0;
+    AdjArena ar;
+    if ((st = adj_layout(c, nsteps, ar)) != RT_OK) return st;
+    const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
+    // 1. forward recompute from the checkpoint with the stage kernels
+    RT_CUDA_TRY(c, cudaMemcpyAsync(ar.In[0], I_ckpt, ni * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(ar.un[0], ug_ckpt, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if ((st = adj_forward(c, ar, dt, nullptr)) != RT_OK) return st;
+    // 2. reverse sweep
+    return adj_reverse(c, ar, dt, dL_dI_out, dL_dug_out, dL_dI_in, dL_dug_in, dL_dkappa, dL_deta);
+}
+
+extern "C" rt_status rt_step_record(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *rec_id) {
+    if (!c) return RT_EINVAL;
+    if (!rec_id || nsteps < 1) return adj_fail(c, RT_EINVAL, "rt_step_record: null rec_id or nsteps < 1");
+    *rec_id = 0;
+    if (!c->have_I) return adj_fail(c, RT_ESTATE, "the intensity must be set before rt_step_record");
+    rt_status st;
+    if ((st = adj_check(c, "rt_step_record")) != RT_OK) return st;
+    if ((st = adj_dt(c, dt)) != RT_OK) return st;
+    if (dt_used) *dt_used = dt;
+    c->rec_id = 0;
+    AdjArena ar;
+    if ((st = adj_layout(c, nsteps, ar)) != RT_OK) return st;
+    const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
+    RT_CUDA_TRY(c, cudaMemcpyAsync(ar.In[0], c->I[0], ni * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(ar.un[0], c->ug[0], nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if ((st = adj_forward(c, ar, dt, c->G)) != RT_OK) return st;
+    // the context's state becomes the end state, as after rt_step
+    const int N = nsteps;
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->I[0], ar.In[N], ni * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->ug[0], ar.un[N], nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    RT_CUDA_TRY(c, cudaMemcpyAsync(c->alpha[0], ar.aln[N], nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->rec_id = ++g_rec_counter;
+    c->rec_N = N;
+    c->rec_dt = dt;
+    *rec_id = c->rec_id;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_step_adjoint_recorded(rt_ctx *c, long long rec_id, const double *dL_dI_out,
+                                              const double *dL_dug_out, double *dL_dI_in, double *dL_dug_in,
+                                              double *dL_dkappa, double *dL_deta) {
+    if (!c) return RT_EINVAL;
+    if (!dL_dI_out || !dL_dI_in || !dL_dug_in || !dL_dkappa || !dL_deta)
+        return adj_fail(c, RT_EINVAL, "rt_step_adjoint_recorded: null pointer");
+    if (rec_id <= 0 || rec_id != c->rec_id)
+        return adj_fail(c, RT_ESTATE, "rt_step_adjoint_recorded: no valid recording with this id (a later "
+                                      "rt_step_record, rt_step_adjoint, rt_set_fluid or rt_set_metric replaced it)");
+    rt_status st;
+    if ((st = adj_check(c, "rt_step_adjoint_recorded")) != RT_OK) return st;
+    AdjArena ar;
+    if ((st = adj_layout(c, c->rec_N, ar)) != RT_OK) return st;
+    return adj_reverse(c, ar, c->rec_dt, dL_dI_out, dL_dug_out, dL_dI_in, dL_dug_in, dL_dkappa, dL_deta);
 }

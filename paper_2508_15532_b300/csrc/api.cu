@@ -114,6 +114,7 @@ extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_
     if (!c) return RT_EINVAL;
     if (c->metric < 0) return fail(c, RT_ESTATE, "rt_set_metric must precede rt_set_fluid");
     if (!rho || !u_gas || !ucon || !kappa || !alpha_s_coef) return fail(c, RT_EINVAL, "null fluid array");
+    c->rec_id = 0;   // a forward recording belongs to the fluid it ran with
     size_t n = (size_t)c->ncell * 8;
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->rho, rho, n, cudaMemcpyDefault, c->stream));
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->ug[0], u_gas, n, cudaMemcpyDefault, c->stream));

@@ -84,6 +84,11 @@ struct rt_ctx {
     // arena of the reverse pass (rt_step_adjoint), grown on demand
     double *adj = nullptr;
     size_t adj_bytes = 0;
+    // the forward recording held in the arena (rt_step_record): its id (0 =
+    // none), steps and step size
+    long long rec_id = 0;
+    int rec_N = 0;
+    double rec_dt = 0.0;
     // set during the reverse pass's recompute: the stage kernels save each
     // cell's E-bar_- and temperature-solve root X there (null otherwise)
     double *sv_Em = nullptr, *sv_X = nullptr;

@@ -32,7 +32,9 @@
 namespace {
 using namespace rtk;
 
-template <typename TS, typename TM, bool FLAT, int BY, int BZ>
+// LK: the limiter kind fixed at compile time (RT_LIM_MC), or -1 to read it
+// from the arguments
+template <typename TS, typename TM, bool FLAT, int BY, int BZ, int LK>
 __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
     constexpr int TXC = NCELL / (BY * BZ);
     constexpr int NOWN = BY * BZ;
@@ -168,8 +170,8 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 const int rb = rowY[r * (BY + 4) + q + 2] & F_MASK;
                 TM Im2 = ld_x(rb, xmap[0], jr), Im1 = ld_x(rb, xmap[1], jr);
                 TM I0 = ld_x(rb, xmap[2], jr), I1 = ld_x(rb, xmap[3], jr);
-                TM sm1 = limiter<TM>(A.limiter, I0 - Im1, Im1 - Im2);
-                TM s0 = limiter<TM>(A.limiter, I1 - I0, I0 - Im1);
+                TM sm1 = limiter<TM>(LK >= 0 ? LK : A.limiter, I0 - Im1, Im1 - Im2);
+                TM s0 = limiter<TM>(LK >= 0 ? LK : A.limiter, I1 - I0, I0 - Im1);
                 const TM *rc = recX + (o * (TXC + 1)) * 5;
                 TM IL = Im1 + TM(0.5) * sm1, IR = I0 - TM(0.5) * s0;
                 TM phi;
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                         const int q = o % BY, r = o / BY, jr = j0 + q;
                         const int rb = rowY[r * (BY + 4) + q + 2] & F_MASK;
                         TM I2 = ld_x(rb, xmap[ii + 4], jr);
-                        TM s1 = limiter<TM>(A.limiter, I2 - W1[o], W1[o] - W0[o]);
+                        TM s1 = limiter<TM>(LK >= 0 ? LK : A.limiter, I2 - W1[o], W1[o] - W0[o]);
                         const TM *rc = recX + (o * (TXC + 1) + ii + 1) * 5;
                         TM IL = W0[o] + TM(0.5) * S0[o], IR = W1[o] - TM(0.5) * s1;
                         TM phi;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                             Y[q] = (q >= 2 && q < BY + 2) ? Ic[r * BY + q - 2] : ld_row(rowY[r * (BY + 4) + q], i);
                         sy[0] = sy[BY + 3] = TM(0);
 #pragma unroll
-                        for (int q = 1; q < BY + 3; ++q) sy[q] = limiter<TM>(A.limiter, Y[q + 1] - Y[q], Y[q] - Y[q - 1]);
+                        for (int q = 1; q < BY + 3; ++q) sy[q] = limiter<TM>(LK >= 0 ? LK : A.limiter, Y[q + 1] - Y[q], Y[q] - Y[q - 1]);
 #pragma unroll
                         for (int f = 0; f <= BY; ++f) {
                             const TM *rc = recY + ((r * (BY + 1) + f) * TXC + ii) * 5;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                             Z[r] = (r >= 2 && r < BZ + 2) ? Ic[(r - 2) * BY + q] : ld_row(rowZ[q * (BZ + 4) + r], i);
                         sz[0] = sz[BZ + 3] = TM(0);
 #pragma unroll
-                        for (int r = 1; r < BZ + 3; ++r) sz[r] = limiter<TM>(A.limiter, Z[r + 1] - Z[r], Z[r] - Z[r - 1]);
+                        for (int r = 1; r < BZ + 3; ++r) sz[r] = limiter<TM>(LK >= 0 ? LK : A.limiter, Z[r + 1] - Z[r], Z[r] - Z[r - 1]);
 #pragma unroll
                         for (int f = 0; f <= BZ; ++f) {
                             const TM *rc = recZ + ((q * (BZ + 1) + f) * TXC + ii) * 5;
@@ -616,7 +618,7 @@ rt_status launch(rt_ctx *c, const StageArgs &A, int NT) {
     if (!FLAT) tm += NOWN * nd + 6 * NOWN * nd;
     size_t smem = sizeof(TM) * tm + 16 + sizeof(double) * (8 * NCELL * 6 + NCELL) +
                   sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NCELL);
-    auto kern = k_stage<TS, TM, FLAT, BY, BZ>;
+    auto kern = A.limiter == RT_LIM_MC ? k_stage<TS, TM, FLAT, BY, BZ, RT_LIM_MC> : k_stage<TS, TM, FLAT, BY, BZ, -1>;
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nseg = (A.nx0 + TXC - 1) / TXC;
     size_t nblk = (size_t)nseg * (A.nx1 / BY) * (A.nx2 / BZ);

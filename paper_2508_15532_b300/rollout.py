@@ -7,8 +7,11 @@ and the emission multiplier eta comes from the library's hand-written reverse
 pass.  The forward runs nsteps steps through rt_step and keeps (I, u_g) at the
 start of every segment of ckpt_every steps; the backward walks the segments in
 reverse, and rt_step_adjoint recomputes each segment from its checkpoint
-before reversing it.  Every step of both passes runs in the CUDA library;
-this module only moves tensors.
+before reversing it.  The last segment runs through rt_step_record, which
+keeps its stage states, so the backward reverses it without a recompute
+(rt_step_adjoint_recorded) unless the context has served another rollout or
+fluid since.  Every step of both passes runs in the CUDA library; this module
+only moves tensors.
 """
 import torch
 
@@ -34,13 +37,17 @@ class _Rollout(torch.autograd.Function):
             st.get_ugas(u)
             ck_I.append(I)
             ck_u.append(u)
-            st.step(dt, k)
+            if n + k < nsteps:
+                st.step(dt, k)
+            else:
+                ctx.rec_id = st.step_record(dt, k)
             segs.append(k)
             n += k
         IN = torch.empty_like(I0)
         uN = torch.empty(nc, dtype=torch.float64, device=dev)
         st.get_intensity(IN)
         st.get_ugas(uN)
+        ctx.fluid_token = st.fluid_token
         ctx.st, ctx.fluid, ctx.dt, ctx.segs, ctx.I_dtype = st, fluid, dt, segs, I0.dtype
         ctx.ck_I, ctx.ck_u, ctx.kappa, ctx.eta, ctx.ug0 = ck_I, ck_u, kappa, eta, ug0.detach()
         return IN, uN
@@ -48,8 +55,11 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gI, gu):
         st, f = ctx.st, ctx.fluid
-        # the context may have served another rollout since: restore this one's fluid
-        st.set_fluid(f["rho"], ctx.ug0.contiguous(), f["ucon"], ctx.kappa, f["alpha_s"], ctx.eta)
+        # the context may have served another rollout since: restore this one's
+        # fluid (which drops the library's recording of the last segment)
+        if st.fluid_token is not ctx.fluid_token:
+            st.set_fluid(f["rho"], ctx.ug0.contiguous(), f["ucon"], ctx.kappa, f["alpha_s"], ctx.eta)
+        recorded = st.rec_id != 0 and st.rec_id == ctx.rec_id
         I_like, u_like = ctx.ck_I[0], ctx.ck_u[0]
         Ib = torch.zeros_like(I_like) if gI is None else gI.to(torch.float64).contiguous().clone()
         ub = torch.zeros_like(u_like) if gu is None else gu.to(torch.float64).contiguous().clone()
@@ -58,7 +68,10 @@ class _Rollout(torch.autograd.Function):
         kb = torch.zeros_like(u_like)
         eb = torch.zeros_like(u_like)
         for idx in reversed(range(len(ctx.segs))):
-            st.step_adjoint(ctx.ck_I[idx], ctx.ck_u[idx], ctx.dt, ctx.segs[idx], Ib, ub, Ib_in, ub_in, kb, eb)
+            if recorded and idx == len(ctx.segs) - 1:
+                st.step_adjoint_recorded(ctx.rec_id, Ib, ub, Ib_in, ub_in, kb, eb)
+            else:
+                st.step_adjoint(ctx.ck_I[idx], ctx.ck_u[idx], ctx.dt, ctx.segs[idx], Ib, ub, Ib_in, ub_in, kb, eb)
             Ib, Ib_in = Ib_in, Ib
             ub, ub_in = ub_in, ub
         return Ib.to(ctx.I_dtype), ub, kb, eb, None, None, None, None, None

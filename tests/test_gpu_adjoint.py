@@ -267,3 +267,62 @@ def test_step_adjoint_boxes_fp64_and_mixed(nx, bc, limiter, order):
                 assert err <= 1e-4, (precision, name, err)
             e = np.abs(Ib - gI) / np.abs(gI).max()
             assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 0.05, (precision, np.quantile(e, 0.999), e.max())
+
+
+@pytest.mark.parametrize("precision,order", [("fp64", 2), ("fp32", 2), ("fp64", 1)])
+def test_recorded_reverse_matches_checkpoint_reverse(precision, order):
+    """rt_step_record keeps the stage states of its steps, and
+    rt_step_adjoint_recorded reverses them without the recompute: its end state
+    is rt_step's, and its gradients are those of rt_step_adjoint from the same
+    start state (the same stage kernels fill the arena either way).  A
+    recording replaced by a later rt_step_adjoint is refused with RT_ESTATE."""
+    torch = _torch()
+    import paper_2508_15532_b300 as rt
+    cfg, f = _case(order, None, False, N=8, index=64)
+    nsteps = 3
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    grid = rt.Grid(cfg["n_geo"])
+    w = T(grid.query()[1])
+    I0 = T(f["I"]) if precision == "fp64" else T(f["I"]).float()
+
+    def ctx():
+        st = rt.RadiationStep(grid, cfg, precision=precision)
+        st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+        st.set_intensity(I0)
+        return st
+
+    a, b = ctx(), ctx()
+    dt = a.cfl_dt(0.4)
+    rid = a.step_record(dt, nsteps)
+    b.step(dt, nsteps)
+    Ia, Ib = torch.empty_like(I0), torch.empty_like(I0)
+    ua = torch.empty(I0.shape[0], dtype=torch.float64, device=dev)
+    ub = torch.empty_like(ua)
+    a.get_intensity(Ia); b.get_intensity(Ib); a.get_ugas(ua); b.get_ugas(ub)
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert rel_err(Ia.double().cpu().numpy(), Ib.double().cpu().numpy(), 1e-6).max() <= tol
+    assert rel_err(ua.cpu().numpy(), ub.cpu().numpy(), 1e-6).max() <= tol
+
+    E = Ia.double() @ w
+    dI = ((2.0 * E + 3.0 * ua)[:, None] * w[None, :]).contiguous()
+    du = (3.0 * E).contiguous()
+
+    def grads(run):
+        gI = torch.empty_like(dI)
+        gu = torch.empty_like(du)
+        kb = torch.zeros_like(du)
+        eb = torch.zeros_like(du)
+        run(gI, gu, kb, eb)
+        torch.cuda.synchronize()
+        return [t.cpu().numpy() for t in (gI, gu, kb, eb)]
+
+    rec = grads(lambda gI, gu, kb, eb: a.step_adjoint_recorded(rid, dI, du, gI, gu, kb, eb))
+    ref = grads(lambda gI, gu, kb, eb: a.step_adjoint(I0, T(f["ug"]), dt, nsteps, dI, du, gI, gu, kb, eb))
+    for name, x, y in zip(("I0", "ug0", "kappa", "eta"), rec, ref):
+        err = np.abs(x - y).max() / max(np.abs(y).max(), 1e-300)
+        assert err <= tol, (name, err)
+    with pytest.raises(rt.RTError) as e:
+        a.step_adjoint_recorded(rid, dI, du, torch.empty_like(dI), torch.empty_like(du),
+                                torch.zeros_like(du), torch.zeros_like(du))
+    assert e.value.status == 5     # RT_ESTATE
