@@ -128,9 +128,12 @@ template <typename R> __device__ __forceinline__ R tpow_neg(R T, R p) {
     return pow(T, -p);
 }
 
-template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, R X, R *h, R *dh) {
+// *hs: the size of the terms that make up h, so that |h| <= eps * hs is h at
+// the level of its own rounding (with alpha^s dt >> 1, h is the difference of
+// two terms ~alpha^s dt X that cancel to ~X)
+template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, R X, R *h, R *dh, R *hs) {
     R T = q.Tm + (q.Em - X) * q.iY;
-    if (!(T > R(0))) { *h = R(1e30); *dh = R(1); return; }
+    if (!(T > R(0))) { *h = R(1e30); *dh = R(1); *hs = R(0); return; }
     // T^-p and 1/T with one division (p = 3.5: 1/T = T^2 sqrt(T) T^-3.5)
     R tp, iT;
     if (q.p == R(3.5)) {
@@ -146,16 +149,19 @@ template <typename R> __device__ __forceinline__ void teq_eval(const Teq<R> &q, 
     R em = q.B2 * q.eta * q.arad * aa * T4;
     R lin = (aa + q.as) * q.dt - q.B2 * q.as;
     *h = lin * X - q.B1 - em;
+    *hs = ((aa + q.as) * q.dt + q.B2 * q.as) * X + q.B1 + em;
     // dh/dX with dT/dX = -1/Y
     *dh = lin + (q.p * aa * iT) * q.dt * X * q.iY + em * (R(4) - q.p) * iT * q.iY;
 }
 
-// safeguarded Newton on [lo, hi] with h(lo) <= 0 < h(hi); returns converged flag
+// safeguarded Newton on [lo, hi] with h(lo) <= 0 < h(hi); returns converged
+// flag.  Converged: a Newton step below tol X, a bracket below tol hi, or a
+// residual at its rounding level (|h| <= tol hs), where no step can do better
 template <typename R> __device__ bool newton_E(const Teq<R> &q, R X, R &lo, R &hi, int maxit, R tol, R *Xout) {
-    R h, dh;
+    R h, dh, hs;
     for (int it = 0; it < maxit; ++it) {
-        teq_eval(q, X, &h, &dh);
-        if (h == R(0)) { *Xout = X; return true; }      // exact root: keep it
+        teq_eval(q, X, &h, &dh, &hs);
+        if (fabs(h) <= tol * hs) { *Xout = X; return true; }   // exact root or rounding-level residual
         if (h > R(0)) hi = fmin(hi, X); else lo = fmax(lo, X);
         R d = h / dh;
         if (fabs(d) <= tol * X) { *Xout = fmin(fmax(X - d, lo), hi); return true; }   // converged Newton step

@@ -22,6 +22,11 @@ Workloads (sizes are the defaults; smaller variants keep the same recipe):
                free-free absorption plus electron scattering, I = B(T).
 * ``kerr3d``   the same in 3D with 128 phi cells and 5% density/temperature noise.
 * ``adjoint3d`` the flat3d recipe at 64^3 (rollout of 64 steps, checkpoint every 8).
+* ``diffusion1d`` the static-diffusion slab of section 4: flat 1D, 64 cells on
+               [-1, 1] with outflow ends, 162 directions, rho = 1, pure
+               scattering alpha^s = 1e3 (no absorption, cold gas u_g = 1e-10),
+               isotropic I = E0 / (4 pi) with E0 = exp(-x^2 / (2 sigma^2)),
+               sigma^2 = 1.25e-2, held at E0(0.5) for |x| > 0.5; t = 10.
 """
 import math
 
@@ -226,3 +231,28 @@ def kerr2d(**kw):
 def kerr3d(**kw):
     kw.setdefault("nph", 128)
     return kerr(index=3, **kw)
+
+
+# ------------------------------------------------------------------ diffusion1d
+DIFF_SIGMA2 = 1.25e-2
+DIFF_ALPHA_S = 1e3
+
+
+def diffusion1d(N=64, n_geo=4, ug=1e-10):
+    """Static radiative diffusion through a scattering slab (section 4): the
+    initial energy density, held constant beyond |x| = 0.5, and an isotropic
+    intensity carrying it.  Returns (cfg, fields, x) with x the cell centres.
+    Without absorption the gas temperature does not enter the radiation; ``ug``
+    other than the cold 1e-10 serves FP32 storage, whose energy ledger carries
+    an absolute rounding of ~1e-7 E-bar per stage."""
+    dx = 2.0 / N
+    cfg = base_config(n_geo, (N, 1, 1), (-1.0, 0.0, 0.0), (dx, 1.0, 1.0),
+                      (("outflow", "outflow"), ("periodic", "periodic"), ("periodic", "periodic")),
+                      workload="diffusion1d")
+    x = -1.0 + (np.arange(N) + 0.5) * dx
+    E0 = np.exp(-np.minimum(x * x, 0.25) / (2.0 * DIFF_SIGMA2))
+    nd = 10 * n_geo * n_geo + 2
+    fields = dict(rho=np.ones(N), ug=np.full(N, float(ug)), ucon=static_ucon(N), kappa=np.zeros(N),
+                  alpha_s=np.full(N, DIFF_ALPHA_S), eta=np.ones(N),
+                  I=np.outer(E0 / (4.0 * math.pi), np.ones(nd)))
+    return cfg, fields, x

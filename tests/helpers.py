@@ -1,8 +1,11 @@
 """Shared helpers of the parity tests: run one workload on the CUDA library
 and on the FP64 oracle from the same seeded inputs."""
+import math
+
 import numpy as np
 
 import oracle
+from paper_2508_15532_b300 import workloads as W
 
 
 def rel_err(x, ref, floor_frac=1e-6):
@@ -48,3 +51,20 @@ def run_gpu(cfg, f, dt, nsteps, precision="fp64", grid=None):
                G=G.cpu().numpy(), fails=nfail)
     del st
     return out
+
+
+def diffusion_closed_form(x, t, K, sigma2=W.DIFF_SIGMA2):
+    """eq. diff_analytic: a Gaussian of variance sigma2 spreading under
+    dE/dt = K d2E/dx2 (the paper writes K = 1 / (3 alpha^s), D = 2 K / sigma2)."""
+    v = 1.0 + 2.0 * K * t / sigma2
+    return v ** -0.5 * np.exp(-x * x / (2.0 * v * sigma2))
+
+
+def scheme_diffusion_coefficient(dirs, w, abar=1.0, alpha=W.DIFF_ALPHA_S):
+    """Thick limit of the damped face flux (eqs. rad_speeds, flux_Jiang): with
+    f(tau), g(tau) -> 1/tau, direction s carries -|n^x_s| / (2 tau) (I_{l+1} - I_l)
+    (pinned by test_flux_thick_limit_is_diffusive), tau = abar alpha dx.  An
+    isotropic field I = E / (4 pi) then carries the energy flux
+    -(sum_s |n^x_s| dOmega_s) / (8 pi abar alpha) dE/dx, i.e. K = 1 / (4 abar alpha)
+    for the exact sum 2 pi: 3/4 of the continuum 1 / (3 alpha)."""
+    return float(np.abs(np.asarray(dirs)[:, 0]) @ np.asarray(w)) / (8.0 * math.pi * abar * alpha)

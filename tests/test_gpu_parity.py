@@ -224,3 +224,57 @@ def test_kerr_storage_modes_moments_against_fp64():
         assert rel_err(out["E"], ref["E"]).max() < e_bar, precision
         err_f = np.abs(out["R"][:, 1:4] - fl).max() / np.abs(fl).max()
         assert err_f < f_bar, (precision, err_f)
+
+
+def test_static_diffusion_fp64_fp32():
+    """Section 4's static diffusion slab (pure scattering, alpha^s = 1e3, 64
+    cells, 162 directions) to t = 10 (800 steps) on the CUDA path, where the
+    temperature solve's residual cancels (alpha^s dt = 12.5).  FP64 on the
+    paper's cold slab against the oracle at the FP64 bar after 100 steps and at
+    t = 10; FP32 storage on a warm slab (u_g = 1: the FP32 energy ledger's
+    rounding, ~1e-7 E-bar per stage, would drive the cold gas energy of 1e-10
+    negative) against the oracle at the FP32 bars after 100 steps.  Both against
+    eq. diff_analytic with the scheme's thick-limit coefficient at t = 10,
+    within 0.5% of the peak over |x| < 0.5, as the oracle."""
+    from helpers import diffusion_closed_form, scheme_diffusion_coefficient
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    for prec, tdt, ug in (("fp64", torch.float64, 1e-10), ("fp32", torch.float32, 1.0)):
+        cfg, f, x = W.diffusion1d(ug=ug)
+        o = oracle.Oracle(cfg)
+        o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+        o.set_intensity(f["I"])
+        g = o.grid()
+        w = g["w"]
+        dt = o.cfl_dt(0.4)
+        n = int(round(10.0 / dt))
+        assert o.step(dt, 100) == 0
+        I100 = o.intensity()
+        if prec == "fp64":
+            assert o.step(dt, n - 100) == 0
+            Iend = o.intensity()
+        Ek = diffusion_closed_form(x, n * dt, scheme_diffusion_coefficient(g["dir"], w))
+        inner = np.abs(x) < 0.5
+        st = rt.RadiationStep(rt.Grid(cfg["n_geo"]), cfg, precision=prec)
+        st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+        I0 = T(f["I"]).to(tdt).contiguous()
+        st.set_intensity(I0)
+        I = torch.empty_like(I0)
+        _, nfail = st.step(dt, 100, check=True)
+        assert nfail == 0
+        st.get_intensity(I)
+        got = I.double().cpu().numpy()
+        if prec == "fp64":
+            assert rel_err(got, I100).max() <= 1e-11
+        else:
+            assert rel_err(got, I100, 1e-3).max() <= 1e-4
+            assert rel_err(got @ w, I100 @ w).max() <= 2e-5
+        _, nfail = st.step(dt, n - 100, check=True)
+        assert nfail == 0
+        st.get_intensity(I)
+        got = I.double().cpu().numpy()
+        if prec == "fp64":
+            assert rel_err(got, Iend).max() <= 1e-11
+        E = got @ w
+        assert np.abs(E - Ek)[inner].max() <= 5e-3 * Ek.max(), prec
+        del st
