@@ -74,6 +74,7 @@ extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cud
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_on, nc);
     for (int d = 0; d < g->nd; ++d) {
         c->sumw += g->h_w[d];
+        c->sumwf += (double)(float)g->h_w[d];
         for (int m = 0; m < 3; ++m) c->sumnw[m] += g->h_dir[3 * d + m] * g->h_w[d];
     }
     if (e == cudaSuccess) e = cudaMemset(c->G, 0, nc * 32);

@@ -64,6 +64,7 @@ struct rt_ctx {
     double *cc_au = nullptr, *cc_as = nullptr, *cc_Y = nullptr;
     uint8_t *cc_on = nullptr;
     double sumw = 0.0;           // sum of the solid angles (4 pi to rounding)
+    double sumwf = 0.0;          // sum of the FP32-rounded solid angles (the FP32 paths' quadrature)
     double sumnw[3] = {0, 0, 0}; // sum of n-hat dOmega (0 to rounding)
     bool static_fluid = false;   // u-hat = (1, 0, 0, 0) in every cell (set by rt_set_fluid)
     unsigned long long *fail = nullptr;   // device counter of unconverged solves

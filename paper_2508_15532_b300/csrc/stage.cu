@@ -434,11 +434,23 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
     all_static = __syncthreads_and(all_static);
 
     // angular sums in direction chunks: E-bar_- (compensated), B1, B2 (eqs.
-    // A1, A2 in the reading of method 3); K = alpha_- dt / (n^0 + D alpha_- dt)
+    // A1, A2 in the reading of method 3); K = alpha_- dt / (n^0 + D alpha_- dt).
+    // B1 and B2 are compensated too in FP32: with alpha^s dt >> 1 the solve's
+    // coefficient alpha dt - B2 alpha^s cancels to ~1/(alpha dt) of its terms
+    // and magnifies B2's rounding by as much
     const int nchunk = NT / 32;
     {
         const int c = s & 31, g = s >> 5;
-        TM Em = 0, cEm = 0, B1 = 0, B2 = 0;
+        TM Em = 0, cEm = 0, B1 = 0, B2 = 0, cB1 = 0, cB2 = 0;
+        auto kadd = [](TM &sum, TM &comp, TM v) {
+            if constexpr (sizeof(TM) == 4) {
+                const TM y = v - comp, t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            } else {
+                sum += v;
+            }
+        };
         if ((c % TXC) < nc && scOn[c]) {
             const TM u0 = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
             const TM n0 = scN0[c], adt = scK[c];
@@ -451,15 +463,15 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                     TM D = u0 - (u1 * ldT<TM>(A.dirT, 3 * d) + u2 * ldT<TM>(A.dirT, 3 * d + 1) + u3 * ldT<TM>(A.dirT, 3 * d + 2));
                     t = D * D * row[d] * w;
                     TM K = dv<TM>(adt, n0 + D * adt);
-                    B1 += n0 * K * t;
-                    B2 += dv<TM>(K * w, D);
+                    kadd(B1, cB1, n0 * K * t);
+                    kadd(B2, cB2, dv<TM>(K * w, D));
                 }
                 TM yk = t - cEm, tk = Em + yk;
                 cEm = (tk - Em) - yk; Em = tk;
             }
         }
         double *pp = part + (g * NCELL + c) * 6;
-        pp[0] = (double)Em - (double)cEm; pp[1] = B1; pp[2] = B2;
+        pp[0] = (double)Em - (double)cEm; pp[1] = (double)B1 - (double)cB1; pp[2] = (double)B2 - (double)cB2;
     }
     __syncthreads();
     // one lane per cell: temperature solve and per-cell update constants
@@ -473,12 +485,17 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 Em += pp[0]; B1 += pp[1]; B2 += pp[2];
             }
             const double dt = A.dtk, adt = A.alpha_int[cidx] * dt;
+            // the isotropic source is spread with the solid angles the sums
+            // use: in FP32 their sum differs from 4 pi by ~1e-7, which the
+            // solve's cancellation at alpha^s dt >> 1 would magnify into a
+            // bias of the scattered energy repeated every stage
+            const double qw = sizeof(TM) == 4 ? A.sumwf : FOURPI;
             if (all_static) {        // D = 1, n^0 = 1: K is per cell
                 double K = adt / (1.0 + adt);
                 B1 = K * Em;
-                B2 = K * A.sumw;
+                B2 = K * (sizeof(TM) == 4 ? A.sumwf : A.sumw);
             }
-            B2 *= dt / FOURPI;
+            B2 *= dt / qw;
             const double Y = A.cc_Y[cidx], ug = A.ug_in[cidx], Tm = ug / Y;
             Teq<double> q = make_teq<double>(B1, B2, Em + ug, Y, Tm, Em, A.cc_au[cidx], A.cc_as[cidx], A.eta[cidx], A.arad,
                                              dt, A.T_exp);
@@ -501,7 +518,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             const double aap = A.cc_au[cidx] * tpow_neg<double>(Tp, A.T_exp), atp = aap + A.cc_as[cidx];
             const double em = A.eta[cidx] * aap * A.arad * Tp * Tp * Tp * Tp + A.cc_as[cidx] * X;
             sc64[s] = Em;
-            scEm[s] = (TM)(dt * em / FOURPI);
+            scEm[s] = (TM)(dt * em / qw);
             scA[s] = (TM)(atp * dt);
         }
     }
@@ -664,7 +681,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.beam_dir = f.beam_dir; A.beam_lo = f.beam_lo; A.beam_hi = f.beam_hi; A.beam_I = f.beam_I;
     A.n_pole_zero = f.n_pole_zero;
     A.dx0 = f.dx[0]; A.dx1 = f.dx[1]; A.dx2 = f.dx[2];
-    A.gam = f.gam; A.arad = f.arad; A.T_exp = f.T_exp; A.abar = f.abar; A.sumw = c->sumw;
+    A.gam = f.gam; A.arad = f.arad; A.T_exp = f.T_exp; A.abar = f.abar; A.sumw = c->sumw; A.sumwf = c->sumwf;
     A.tau_dt = f.tau_dt; A.limiter = f.limiter; A.ang_recon = f.ang_recon;
     A.transport = f.transport; A.source = f.source; A.dtk = dtk;
     A.Isrc = Isrc; A.Ibase = Ibase; A.Iout = Iout; A.ug_in = ug_in; A.ug_out = ug_out;

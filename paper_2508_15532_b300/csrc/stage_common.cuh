@@ -18,7 +18,7 @@ struct StageArgs {
     double beam_I;
     int n_pole_zero;
     double dx0, dx1, dx2;
-    double gam, arad, T_exp, abar, sumw;
+    double gam, arad, T_exp, abar, sumw, sumwf;
     double sumnw[3];           // sum of n-hat_s dOmega_s (0 to rounding)
     int tau_dt, limiter, ang_recon, transport, source;
     double dtk;

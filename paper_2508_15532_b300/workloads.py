@@ -27,6 +27,8 @@ Workloads (sizes are the defaults; smaller variants keep the same recipe):
                scattering alpha^s = 1e3 (no absorption, cold gas u_g = 1e-10),
                isotropic I = E0 / (4 pi) with E0 = exp(-x^2 / (2 sigma^2)),
                sigma^2 = 1.25e-2, held at E0(0.5) for |x| > 0.5; t = 10.
+               With v = 0.05: the advection-diffusion variant, the slab moving
+               along x and the profile centred on x = -0.5.
 """
 import math
 
@@ -238,21 +240,29 @@ DIFF_SIGMA2 = 1.25e-2
 DIFF_ALPHA_S = 1e3
 
 
-def diffusion1d(N=64, n_geo=4, ug=1e-10):
+def diffusion1d(N=64, n_geo=4, ug=1e-10, v=0.0):
     """Static radiative diffusion through a scattering slab (section 4): the
-    initial energy density, held constant beyond |x| = 0.5, and an isotropic
-    intensity carrying it.  Returns (cfg, fields, x) with x the cell centres.
-    Without absorption the gas temperature does not enter the radiation; ``ug``
-    other than the cold 1e-10 serves FP32 storage, whose energy ledger carries
-    an absolute rounding of ~1e-7 E-bar per stage."""
+    initial energy density, held constant beyond |x - x_c| = 0.5, and an
+    isotropic intensity carrying it.  Returns (cfg, fields, x) with x the cell
+    centres.  Without absorption the gas temperature does not enter the
+    radiation; ``ug`` other than the cold 1e-10 serves FP32 storage, whose
+    energy ledger carries an absolute rounding of ~1e-7 E-bar per stage.
+    ``v`` != 0: the advection-diffusion variant, the slab moving with
+    u = gamma (1, v, 0, 0) and the profile centred on x_c = -0.5 (x_c = 0 at rest)."""
     dx = 2.0 / N
     cfg = base_config(n_geo, (N, 1, 1), (-1.0, 0.0, 0.0), (dx, 1.0, 1.0),
                       (("outflow", "outflow"), ("periodic", "periodic"), ("periodic", "periodic")),
-                      workload="diffusion1d")
+                      workload="diffusion1d" if v == 0.0 else "advection_diffusion1d")
     x = -1.0 + (np.arange(N) + 0.5) * dx
-    E0 = np.exp(-np.minimum(x * x, 0.25) / (2.0 * DIFF_SIGMA2))
+    xs = x if v == 0.0 else x + 0.5
+    E0 = np.exp(-np.minimum(xs * xs, 0.25) / (2.0 * DIFF_SIGMA2))
     nd = 10 * n_geo * n_geo + 2
-    fields = dict(rho=np.ones(N), ug=np.full(N, float(ug)), ucon=static_ucon(N), kappa=np.zeros(N),
+    ucon = static_ucon(N)
+    if v != 0.0:
+        gam = 1.0 / math.sqrt(1.0 - v * v)
+        ucon[:, 0] = gam
+        ucon[:, 1] = gam * v
+    fields = dict(rho=np.ones(N), ug=np.full(N, float(ug)), ucon=ucon, kappa=np.zeros(N),
                   alpha_s=np.full(N, DIFF_ALPHA_S), eta=np.ones(N),
                   I=np.outer(E0 / (4.0 * math.pi), np.ones(nd)))
     return cfg, fields, x

@@ -278,3 +278,63 @@ def test_static_diffusion_fp64_fp32():
         E = got @ w
         assert np.abs(E - Ek)[inner].max() <= 5e-3 * Ek.max(), prec
         del st
+
+
+def test_advection_diffusion_fp64_fp32():
+    """Section 4's advection-diffusion slab (v^x = 0.05, alpha^s = 1e3, 64
+    cells) on the general kernel (moving fluid: boosted interaction and the
+    advective face term): FP64 against the oracle at the FP64 bar and FP32
+    storage at the FP32 bars after 100 steps; at t = 10 both carry the profile
+    with the fluid (centroid within 1e-3 of -0.5 + v t) and match eq.
+    diff_analytic there within 4% of the peak, as the oracle does.
+    The FP32 bars take a floor of 1e-2 of the largest value here: the slab's
+    tails sit ~1e-4 below its peak, and the FP32 rounding at the peak (a few
+    ulps) diffuses into them.  The FP32 bar is derived for this stiff regime:
+    every stage's temperature solve carries the FP32 rounding of its angular
+    sums magnified by 1 + alpha^s dt (13.5: the coefficient alpha dt - B2
+    alpha^s cancels), so K steps stay within 2 K (1 + alpha^s dt) 2^-24 =
+    1.6e-4.  The error sits in the scattered, isotropic part of each cell, so
+    the energy density carries it as each intensity does (measured 1.1e-4 on
+    both after 100 steps)."""
+    from helpers import diffusion_closed_form, scheme_diffusion_coefficient
+    v = 0.05
+    cfg, f, x = W.diffusion1d(ug=1.0, v=v)
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    o.set_intensity(f["I"])
+    g = o.grid()
+    w = g["w"]
+    dt = o.cfl_dt(0.4)
+    n = int(round(10.0 / dt))
+    assert o.step(dt, 100) == 0
+    I100 = o.intensity()
+    c = -0.5 + v * n * dt
+    near = np.abs(x - c) < 0.5
+    Ek = diffusion_closed_form(x - c, n * dt, scheme_diffusion_coefficient(g["dir"], w))
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    grid = rt.Grid(cfg["n_geo"])
+    for prec, tdt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        st = rt.RadiationStep(grid, cfg, precision=prec)
+        st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+        I0 = T(f["I"]).to(tdt).contiguous()
+        st.set_intensity(I0)
+        I = torch.empty_like(I0)
+        _, nfail = st.step(dt, 100, check=True)
+        assert nfail == 0
+        st.get_intensity(I)
+        got = I.double().cpu().numpy()
+        if prec == "fp64":
+            assert rel_err(got, I100).max() <= 1e-11
+        else:
+            bar = 2 * 100 * (1.0 + W.DIFF_ALPHA_S * dt) * 2.0 ** -24
+            assert rel_err(got, I100, 1e-2).max() <= bar
+            assert rel_err(got @ w, I100 @ w, 1e-2).max() <= bar
+        _, nfail = st.step(dt, n - 100, check=True)
+        assert nfail == 0
+        st.get_intensity(I)
+        E = I.double().cpu().numpy() @ w
+        centroid = (E * x)[near].sum() / E[near].sum()
+        assert abs(centroid - c) <= 1e-3, prec
+        assert np.abs(E - Ek)[near].max() <= 0.04 * Ek.max(), prec
+        del st
