@@ -368,8 +368,10 @@ struct RevArgs {
 };
 
 // LK: the limiter kind fixed at compile time (RT_LIM_MC, the limiter of every
-// workload here), or -1 to read it from the arguments
-template <class LT, int BY, int BZ, bool FUSE, int LK>
+// workload here), or -1 to read it from the arguments.  PER: every active axis
+// is periodic, so no stencil row lies beyond an outflow boundary and the ghost
+// folding drops out at compile time
+template <class LT, int BY, int BZ, bool FUSE, int LK, bool PER>
 __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     using S = typename LT::S;
     using V = typename LT::V;
@@ -455,6 +457,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     auto hv = [&](int a) { return LT::splat(hvs[a]); };
     const V zero = LT::splat(S(0));
     const int lim = LK >= 0 ? LK : A.limiter;
+    auto beyond = [](int desc) -> bool {   // a stencil row beyond an outflow boundary
+        if constexpr (PER) return false;
+        else return (desc & F_OUT) != 0;
+    };
     const S *Ip = (const S *)A.I, *Zp = (const S *)A.Zg, *Zo = (const S *)A.Zown;
     auto ldI = [&](int off) -> V { return LT::ld(Ip + off); };
     auto ldZ = [&](int off) -> V { return LT::ld(Zp + off); };
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     //  + S~_p (gr_p - gl_p) + S~_{p-1} gl_{p-1} - S~_{p+1} gr_{p+1},
     //  with gl, gr the derivatives of the half slopes.)
     const bool xon = A.transport && A.act[0];
-    const bool lowX = xon && i0 == 0 && !A.per[0];
+    const bool lowX = !PER && xon && i0 == 0 && !A.per[0];
     V xE[NOWN], xCa[NOWN], xIRb[NOWN], xR1[NOWN], xPh[NOWN], xI0[NOWN], xI1[NOWN], xH0[NOWN], xB0[NOWN], xB1[NOWN],
         xAb[NOWN];
     if (xon) {
@@ -484,7 +490,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
             for (int u = 0; u < 4; ++u) {
                 const int xd = xmap[u], off = ob + (xd & F_IDX) * nd;
                 Iw[u] = ldI(off);
-                Zw[u] = (xd & F_OUT) ? zero : ldZ(off);
+                Zw[u] = beyond(xd) ? zero : ldZ(off);
             }
             const V d01 = Iw[1] - Iw[0], d12 = Iw[2] - Iw[1], d23 = Iw[3] - Iw[2];
             V hs1, gl1, gr1, gd1, hs2, gl2, gr2, gd2;
@@ -516,7 +522,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
             for (int o = 0; o < NOWN; ++o) {
                 const int off = own(o) + (xd & F_IDX) * nd;
                 cp_async8f(&pfb[st][o][d0], (const float *)Ip + off);
-                if (!(xd & F_OUT)) cp_async8f(&pfb[st][NOWN + o][d0], (const float *)Zp + off);
+                if (!beyond(xd)) cp_async8f(&pfb[st][NOWN + o][d0], (const float *)Zp + off);
             }
         }
     };
@@ -529,7 +535,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         V Ic[NOWN], Zc[NOWN], acc[NOWN], ab[NOWN];
         if (xon) {
             const int xd = xmap[ii + 4];
-            const bool hiE = !A.per[0] && i == nx0 - 1;
+            const bool hiE = !PER && !A.per[0] && i == nx0 - 1;
             if constexpr (PFX) {
                 if (ii + 1 < nc) pf_issue(ii + 1);
                 cp_commit();
@@ -543,10 +549,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                     const float2 a = *reinterpret_cast<const float2 *>(&pfb[ii & 1][o][d0]);
                     const float2 b = *reinterpret_cast<const float2 *>(&pfb[ii & 1][NOWN + o][d0]);
                     I2 = LT::splat(0); Z2 = zero;
-                    if constexpr (L == 2) { I2 = F2{a.x, a.y}; if (!(xd & F_OUT)) Z2 = F2{b.x, b.y}; }
+                    if constexpr (L == 2) { I2 = F2{a.x, a.y}; if (!beyond(xd)) Z2 = F2{b.x, b.y}; }
                     (void)off;
                 } else {
-                    I2 = ldI(off); Z2 = (xd & F_OUT) ? zero : ldZ(off);
+                    I2 = ldI(off); Z2 = beyond(xd) ? zero : ldZ(off);
                 }
                 const V dr = xI1[o] - xI0[o], dl = I2 - xI1[o];
                 V hsN, glN, grN, gdN;
@@ -580,12 +586,12 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
 #pragma unroll
             for (int k = 0; k < NB + 4; ++k) {
                 const int d = rows[k];
-                out |= (unsigned)((d & F_OUT) != 0) << k;
+                out |= (unsigned)beyond(d) << k;
                 if (k >= 2 && k < NB + 2) { Yv[k] = Ic[ownidx(k - 2)]; Bv[k] = Zc[ownidx(k - 2)]; }
                 else {
                     const int off = (d & F_IDX) * nd + d0 + ie;
                     Yv[k] = ldI(off);
-                    Bv[k] = (d & F_OUT) ? zero : ldZ(off);
+                    Bv[k] = beyond(d) ? zero : ldZ(off);
                 }
             }
             V dI[NB + 3];
@@ -753,7 +759,10 @@ rt_status launch_rev_t(rt_ctx *c, const RevArgs &A) {
     constexpr int TXC = RNC / (BY * BZ);
     const size_t nblk = (size_t)((A.nx[0] + TXC - 1) / TXC) * (A.nx[1] / BY) * (A.nx[2] / BZ);
     const int dyn = FUSE ? (int)(RNC * LT::NT * LT::L * sizeof(typename LT::S)) : 0;
-    auto kern = A.limiter == RT_LIM_MC ? k_rev<LT, BY, BZ, FUSE, RT_LIM_MC> : k_rev<LT, BY, BZ, FUSE, -1>;
+    bool per = true;   // every active axis periodic
+    for (int a = 0; a < 3; ++a) per = per && (!A.act[a] || A.per[a]);
+    auto kern = A.limiter == RT_LIM_MC ? (per ? k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, true> : k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, false>)
+                                       : (per ? k_rev<LT, BY, BZ, FUSE, -1, true> : k_rev<LT, BY, BZ, FUSE, -1, false>);
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     kern<<<(unsigned)nblk, LT::NT, dyn, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
