@@ -428,7 +428,9 @@ __device__ __forceinline__ F2 phi2(F2 n, F2 an, const Rec4<float> &r, F2 IL, F2 
 
 constexpr int FP2_NT = 96;
 
-template <typename TS, int BY, int BZ, bool WANTG>
+// SB: the stage's base intensities are its input (the predictor), fixed at
+// compile time so that that instance carries no base-prefetch code
+template <typename TS, int BY, int BZ, bool WANTG, bool SB>
 __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
     constexpr int TXC = NCELL / (BY * BZ), NOWN = BY * BZ, NW = FP2_NT / 32;
     __shared__ int xmap[TXC + 4];
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(FP2_NT, 5) k_stage_fp2(const StageArgs A) {
         for (int q = 0; q < BY; ++q)
 #pragma unroll
             for (int r = 0; r < BZ + 4; ++r) oz[q][r] = roff(rowZ[q * (BZ + 4) + r]);
-        const bool same_base = A.Isrc == A.Ibase;
+        constexpr bool same_base = SB;
         auto cp8 = [&](float *dst, const TS *src) {
             unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
@@ -742,8 +744,10 @@ rt_status launch_fs(rt_ctx *c, const StageArgs &A, int NT) {
         for (int sd = 0; sd < 2; ++sd) simple = simple && (A.bc[a][sd] == RT_BC_PERIODIC || A.bc[a][sd] == RT_BC_OUTFLOW);
     if constexpr (sizeof(TM) == 4) {
         if (simple && A.nd % 2 == 0 && A.nd <= 2 * FP2_NT) {
-            if (A.G) k_stage_fp2<TS, BY, BZ, true><<<(unsigned)nblk, FP2_NT, 0, c->stream>>>(A);
-            else k_stage_fp2<TS, BY, BZ, false><<<(unsigned)nblk, FP2_NT, 0, c->stream>>>(A);
+            const bool sb = A.Isrc == A.Ibase;
+            auto kern = A.G ? (sb ? k_stage_fp2<TS, BY, BZ, true, true> : k_stage_fp2<TS, BY, BZ, true, false>)
+                            : (sb ? k_stage_fp2<TS, BY, BZ, false, true> : k_stage_fp2<TS, BY, BZ, false, false>);
+            kern<<<(unsigned)nblk, FP2_NT, 0, c->stream>>>(A);
             RT_CUDA_TRY(c, cudaGetLastError());
             return RT_OK;
         }
