@@ -29,15 +29,16 @@ class _Cfg(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _I = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(mutant: int = 0):
+    """The oracle library; mutant > 0 loads a build with one planted mistake
+    (only the test that shows the pins catch such mistakes asks for one)."""
+    if mutant not in _libs:
+        L = C.CDLL(build(mutant=mutant))
         L.or_create.restype = C.c_void_p
         L.or_create.argtypes = [C.POINTER(_Cfg)]
         L.or_destroy.argtypes = [C.c_void_p]
@@ -63,8 +64,9 @@ def lib():
         L.or_face_flux.argtypes = [C.c_double] * 8
         L.or_mapr.argtypes = [C.c_void_p, _D, _D]
         L.or_adjoint.argtypes = [C.c_void_p, _D, _D, C.c_int, C.c_double, _D, _D, _D, _D, _D]
-        _lib = L
-    return _lib
+        L.or_ghost_fill.argtypes = [C.c_void_p, _D, C.c_void_p, _I]
+        _libs[mutant] = L
+    return _libs[mutant]
 
 
 def make_cfg(cfg: dict) -> _Cfg:
@@ -96,20 +98,21 @@ def _f(x):
 class Oracle:
     """One oracle problem: grid, geometry, fluid and intensity state."""
 
-    def __init__(self, cfg: dict):
+    def __init__(self, cfg: dict, mutant: int = 0):
         self.cfg = dict(cfg)
         self._c = make_cfg(cfg)
-        self.h = lib().or_create(C.byref(self._c))
+        self.L = lib(mutant)
+        self.h = self.L.or_create(C.byref(self._c))
         if not self.h:
-            raise RuntimeError("oracle: " + lib().or_error().decode())
+            raise RuntimeError("oracle: " + self.L.or_error().decode())
         nd, ne = C.c_int(), C.c_int()
-        lib().or_grid_sizes(self.h, C.byref(nd), C.byref(ne))
+        self.L.or_grid_sizes(self.h, C.byref(nd), C.byref(ne))
         self.nd, self.ne = nd.value, ne.value
         self.ncell = int(np.prod(cfg["nx"]))
 
     def __del__(self):
         if getattr(self, "h", None):
-            lib().or_destroy(self.h)
+            self.L.or_destroy(self.h)
             self.h = None
 
     def grid(self):
@@ -117,66 +120,74 @@ class Oracle:
         d = dict(dir=np.zeros((nd, 3)), w=np.zeros(nd), nnb=np.zeros(nd, np.int32),
                  nbr=np.zeros((nd, 6), np.int32), edge=np.zeros((ne, 2), np.int32),
                  dlam=np.zeros(ne), emid=np.zeros((ne, 3)), eu=np.zeros((ne, 3)))
-        lib().or_grid_get(self.h, d["dir"], d["w"], d["nnb"], d["nbr"], d["edge"], d["dlam"], d["emid"], d["eu"])
+        self.L.or_grid_get(self.h, d["dir"], d["w"], d["nnb"], d["nbr"], d["edge"], d["dlam"], d["emid"], d["eu"])
         m = np.zeros(nd, np.int32)
-        lib().or_grid_mirror(self.h, m)
+        self.L.or_grid_mirror(self.h, m)
         d["mirror"] = m
         return d
 
     def set_fluid(self, rho, ug, ucon, kappa, alpha_s, eta=None):
         eta = np.ones(self.ncell) if eta is None else eta
-        lib().or_set_fluid(self.h, _f(rho), _f(ug), _f(ucon), _f(kappa), _f(alpha_s), _f(eta))
+        self.L.or_set_fluid(self.h, _f(rho), _f(ug), _f(ucon), _f(kappa), _f(alpha_s), _f(eta))
 
     def set_intensity(self, I):
-        lib().or_set_intensity(self.h, _f(I))
+        self.L.or_set_intensity(self.h, _f(I))
 
     def set_ug(self, ug):
-        lib().or_set_ug(self.h, _f(ug))
+        self.L.or_set_ug(self.h, _f(ug))
 
     def intensity(self):
         out = np.zeros(self.ncell * self.nd)
-        lib().or_get_intensity(self.h, out)
+        self.L.or_get_intensity(self.h, out)
         return out.reshape(self.ncell, self.nd)
 
     def ug(self):
         out = np.zeros(self.ncell)
-        lib().or_get_ug(self.h, out)
+        self.L.or_get_ug(self.h, out)
         return out
 
     def cfl_dt(self, cfl):
-        return lib().or_cfl_dt(self.h, float(cfl))
+        return self.L.or_cfl_dt(self.h, float(cfl))
 
     def step(self, dt, nsteps=1):
-        return lib().or_step(self.h, float(dt), int(nsteps))
+        return self.L.or_step(self.h, float(dt), int(nsteps))
 
     def source_only(self, dt):
-        return lib().or_source_only(self.h, float(dt))
+        return self.L.or_source_only(self.h, float(dt))
 
     def moments(self):
         R = np.zeros(self.ncell * 10); E = np.zeros(self.ncell); G = np.zeros(self.ncell * 4)
-        lib().or_moments(self.h, R, E, G)
+        self.L.or_moments(self.h, R, E, G)
         return R.reshape(-1, 10), E, G.reshape(-1, 4)
 
     def geometry_at(self, x):
         g = np.zeros(16); e = np.zeros(16); om = np.zeros(64); sg = np.zeros(1)
-        lib().or_geometry_at(self.h, _f(x), g, e, om, sg)
+        self.L.or_geometry_at(self.h, _f(x), g, e, om, sg)
         return g.reshape(4, 4), e.reshape(4, 4), om.reshape(4, 4, 4), sg[0]
 
     def edge_speeds(self, cell):
         w = np.zeros(self.ne)
-        lib().or_edge_speeds(self.h, int(cell), w)
+        self.L.or_edge_speeds(self.h, int(cell), w)
         return w
 
     def mapr(self, Icell):
         out = np.zeros(self.nd * 6)
-        lib().or_mapr(self.h, _f(Icell), out)
+        self.L.or_mapr(self.h, _f(Icell), out)
         return out.reshape(self.nd, 6)
+
+    def ghosts(self, I):
+        """The ghosted copy of I the transport stage reads, shape (gn2, gn1, gn0, nd)."""
+        gn = np.zeros(3, np.int32)
+        self.L.or_ghost_fill(self.h, _f(I), None, gn)
+        out = np.zeros(int(np.prod(gn)) * self.nd)
+        self.L.or_ghost_fill(self.h, _f(I), out.ctypes.data_as(C.c_void_p), gn)
+        return out.reshape(gn[2], gn[1], gn[0], self.nd)
 
     def adjoint(self, I0, ug0, nsteps, dt, dL_dI, dL_dug):
         gI = np.zeros(self.ncell * self.nd); gk = np.zeros(self.ncell); ge = np.zeros(self.ncell)
-        rc = lib().or_adjoint(self.h, _f(I0), _f(ug0), int(nsteps), float(dt), _f(dL_dI), _f(dL_dug), gI, gk, ge)
+        rc = self.L.or_adjoint(self.h, _f(I0), _f(ug0), int(nsteps), float(dt), _f(dL_dI), _f(dL_dug), gI, gk, ge)
         if rc != 0:
-            raise RuntimeError("oracle adjoint: " + lib().or_error().decode())
+            raise RuntimeError("oracle adjoint: " + self.L.or_error().decode())
         return gI.reshape(self.ncell, self.nd), gk, ge
 
 

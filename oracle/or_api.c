@@ -169,3 +169,9 @@ int or_moments(const or_ctx *c, double *R, double *Ebar, double *G) {
             }
     return 0;
 }
+
+int or_ghost_fill(const or_ctx *c, const double *I, double *Ig, int gn[3]) {
+    for (int a = 0; a < 3; ++a) gn[a] = c->gn[a];
+    if (Ig) or_fill_ghosts(c, I, Ig);
+    return 0;
+}

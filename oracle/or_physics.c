@@ -8,6 +8,17 @@
  */
 #include "or_internal.h"
 
+/* OR_MUTANT (default 0) plants one known mistake, for the test that shows the
+   pins of the angular flux and the pole boundary catch it; builds with it are
+   kept apart (oracle/build.py, liboracle_m<k>.so) and never serve as oracle:
+   1 drift sign flipped, 2 angular upwind side taken from the sign of the
+   weighted speed n_0 v.u (downwind wherever n_0 < 0), 3 pole ghost without
+   the phi + pi shift, 4 pole ghost without the direction mirror, 6 angular
+   flux without the n_0 weight */
+#ifndef OR_MUTANT
+#define OR_MUTANT 0
+#endif
+
 /* n^mu = e^mu_(a) nhat^(a) with nhat^(0) = 1 (eq. n_vector_definition mapped by
    eq. tetrad_transform) and the covariant time component n_0 = g_{0 mu} n^mu */
 void or_tetrad_dir(const or_geom *g, const double nh[3], double n_up[4], double *n_lo0) {
@@ -78,8 +89,12 @@ int or_map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row) {
         else if (bc == OR_BC_OUTFLOW) idx[a] = side ? n - 1 : 0;
         else if (bc == OR_BC_POLE) {
             idx[a] = side ? 2 * n - 1 - idx[a] : -1 - idx[a];
+#if OR_MUTANT != 4
             *mir ^= 1;
+#endif
+#if OR_MUTANT != 3
             if (a == 1 && c->c.nx[2] > 1) idx[2] = (idx[2] + c->c.nx[2] / 2) % c->c.nx[2];
+#endif
         } else {   /* beam: fixed inflow on axis 0, lower side */
             *fixed_row = (a == 0 && side == 0) ? idx[1] : -2;
             idx[a] = side ? n - 1 : 0;
@@ -170,7 +185,7 @@ int or_mapr(const or_ctx *c, const double *Icell, double *out) {
    photon direction m (the geodesic equation in the tetrad frame; it gives
    r^nu, r^zeta, r^psi of eq. angular_n_vectors as components, without a
    polar chart), evaluated at the edge midpoint as in eq. (angular_fluxes). */
-static void edge_speeds(const or_ctx *c, const or_geom *g, double *wsp) {
+static void edge_speeds(const or_ctx *c, const or_geom *g, double *wsp, double *vu) {
     const or_grid *G = &c->G;
     for (int e = 0; e < G->ne; ++e) {
         const double *mm = G->emid + 3 * e, *u = G->eu + 3 * e;
@@ -183,15 +198,22 @@ static void edge_speeds(const or_ctx *c, const or_geom *g, double *wsp) {
         }
         double v[3];
         for (int i = 0; i < 3; ++i) v[i] = -(q[i + 1] - mm[i] * q[0]);
+#if OR_MUTANT == 1
+        for (int i = 0; i < 3; ++i) v[i] = -v[i];
+#endif
         double nup[4], n0;
         or_tetrad_dir(g, mm, nup, &n0);
+#if OR_MUTANT == 6
+        n0 = 1.0;
+#endif
         wsp[e] = n0 * (v[0] * u[0] + v[1] * u[1] + v[2] * u[2]);
+        if (vu) vu[e] = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
     }
 }
 
 int or_edge_speeds(const or_ctx *c, int cell, double *wspeed) {
     int i = cell % c->c.nx[0], j = (cell / c->c.nx[0]) % c->c.nx[1];
-    edge_speeds(c, or_gcen(c, i, j), wspeed);
+    edge_speeds(c, or_gcen(c, i, j), wspeed, NULL);
     return 0;
 }
 
@@ -225,7 +247,7 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
     /* cells are independent: OpenMP over (k, j) rows, per-thread scratch */
 #pragma omp parallel
     {
-    double *wsp = malloc(sizeof(double) * c->G.ne);
+    double *wsp = malloc(sizeof(double) * c->G.ne), *vu = malloc(sizeof(double) * c->G.ne);
     double *Icell = malloc(sizeof(double) * nd), *rec = malloc(sizeof(double) * 6 * nd);
 #pragma omp for collapse(2) schedule(static)
     for (int k = 0; k < c->c.nx[2]; ++k)
@@ -234,7 +256,7 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
                 int ci = or_cidx(c, i, j, k), gi = or_gidx(c, i, j, k);
                 const or_geom *gcc = or_gcen(c, i, j);
                 if (angular) {
-                    edge_speeds(c, gcc, wsp);
+                    edge_speeds(c, gcc, wsp, vu);
                     for (int s = 0; s < nd; ++s) Icell[s] = Ig[(size_t)gi * nd + s];
                     for (int s = 0; s < nd; ++s) mapr_dir(c, Icell, s, rec + 6 * s);
                 }
@@ -284,7 +306,14 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
                             /* reconstructed values on the s0 side (L) and the s1 side (R) */
                             double Iown = rec[6 * s + q], Ioth = rec[6 * t + back];
                             double IL = (s == s0) ? Iown : Ioth, IR = (s == s0) ? Ioth : Iown;
+                            /* eq. (angular_fluxes): the upwind side follows the sign of the
+                               drift v.u itself, not of the flux weight n_0 v.u (n_0 < 0 for
+                               future-directed photons wherever d_t is timelike) */
+#if OR_MUTANT == 2
                             double F = w * (w > 0.0 ? IL : IR);
+#else
+                            double F = w * (vu[e] > 0.0 ? IL : IR);
+#endif
                             ang += c->G.dlam[e] * (s == s0 ? F : -F);
                         }
                         ang /= c->G.w[s];
@@ -295,7 +324,7 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
                     Iout[(size_t)ci * nd + s] = In;
                 }
             }
-    free(wsp); free(Icell); free(rec);
+    free(wsp); free(vu); free(Icell); free(rec);
     }
     free(Ig); free(alg); free(vg);
 }

@@ -84,6 +84,10 @@ int or_moments(const or_ctx *c, double *R, double *Ebar, double *G);
    (index (a*4+b)*4+c), sqrt(-g) */
 int or_geometry_at(const or_ctx *c, const double x[3], double *g, double *e,
                    double *omega, double *sqrtg);
+/* the ghosted copy of I that the transport stage reads: Ig[(gk*gn1 + gj)*gn0 + gi]
+   over the extents gn_a = nx_a + 4 (2 ghost layers on each side of an active
+   axis; inactive axes: nx_a), direction fastest; beam ghosts hold the beam */
+int or_ghost_fill(const or_ctx *c, const double *I, double *Ig, int gn[3]);
 /* angular speed coefficient n_0(m) (v(m).u) for every edge at a cell centre */
 int or_edge_speeds(const or_ctx *c, int cell, double *wspeed);
 
