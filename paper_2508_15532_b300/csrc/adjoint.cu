@@ -15,6 +15,7 @@
 //     stage's input.  The interaction adjoint is written in terms of its
 //     output I_+ = (I_* + c)/(1 + a), so I_* is never stored, and its root
 //     enters through the implicit function theorem.
+#include <atomic>
 #include "stage_common.cuh"
 #include "f32x2.cuh"
 #include <algorithm>
@@ -797,11 +798,13 @@ struct AdjArena {
     double *ubc = nullptr, *ubp = nullptr;
 };
 
-static long long g_rec_counter = 0;   // ids of forward recordings (rt_step_record)
+// ids of forward recordings (rt_step_record); contexts may record from several host threads
+static std::atomic<long long> g_rec_counter{0};
 
 static rt_status adj_check(rt_ctx *c, const char *who) {
     const std::string w(who);
     if (c->metric < 0 || !c->have_fluid) return adj_fail(c, RT_ESTATE, "rt_set_metric and rt_set_fluid must precede " + w);
+    if (rt_status d = rt_check_device(c)) return d;
     if (c->metric != RT_MINKOWSKI_CART || !c->static_fluid)
         return adj_fail(c, RT_EINVAL, w + ": flat Cartesian geometry with the fluid at rest only");
     if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, w + ": FP64 or FP32 intensities only");
@@ -1024,7 +1027,7 @@ extern "C" rt_status rt_step_record(rt_ctx *c, double dt, int nsteps, double *dt
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->I[0], ar.In[N], ni * c->esize, cudaMemcpyDeviceToDevice, c->stream));
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->ug[0], ar.un[N], nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->alpha[0], ar.aln[N], nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    c->rec_id = ++g_rec_counter;
+    c->rec_id = g_rec_counter.fetch_add(1) + 1;
     c->rec_N = N;
     c->rec_dt = dt;
     *rec_id = c->rec_id;

@@ -18,13 +18,24 @@ static rt_status fail(rt_ctx *c, rt_status st, const char *msg) {
     return st;
 }
 
+rt_status rt_check_device(rt_ctx *c) {
+    int dev = -1;
+    RT_CUDA_TRY(c, cudaGetDevice(&dev));
+    if (dev != c->device) {
+        c->err = "the current CUDA device (" + std::to_string(dev) + ") is not the context's (" +
+                 std::to_string(c->device) + ")";
+        return RT_EINVAL;
+    }
+    return RT_OK;
+}
+
 static void free_ctx(rt_ctx *c) {
     if (!c) return;
     for (auto &pr : c->ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     void *ptrs[] = {c->I[0], c->I[1], c->I[2], c->ug[0], c->ug[1], c->ug[2], c->alpha[0], c->alpha[1], c->rho,
                     c->kap, c->cs, c->eta, c->ucon, c->vel, c->uhat, c->G, c->fail, c->pt_e, c->pt_ei, c->pt_V,
                     c->pt_n0, c->pt_len, c->pt_om, c->cenU_d, c->cenU_f, c->mask, c->fn_d, c->fn_f, c->fP_d,
-                    c->fP_f, c->ew_d, c->ew_f, c->cc_au, c->cc_as, c->cc_Y, c->cc_on, c->adj};
+                    c->fP_f, c->ew_d, c->ew_f, c->eneg, c->cc_au, c->cc_as, c->cc_Y, c->cc_on, c->adj, c->gac};
     for (void *p : ptrs) if (p) cudaFree(p);
     delete c;
 }
@@ -52,6 +63,11 @@ extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cud
     c->cfg = f;
     c->g = g;
     c->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        g_create_err = "no current CUDA device";
+        delete c;
+        return RT_ECUDA;
+    }
     c->nd = g->nd; c->ne = g->ne;
     c->ncell = f.nx[0] * f.nx[1] * f.nx[2];
     for (int a = 0; a < 3; ++a) c->active[a] = f.nx[a] > 1;
@@ -72,6 +88,7 @@ extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cud
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_as, nc * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_Y, nc * 8);
     if (e == cudaSuccess) e = cudaMalloc(&c->cc_on, nc);
+    if (e == cudaSuccess) e = cudaMalloc(&c->gac, nc * sizeof(float2));
     for (int d = 0; d < g->nd; ++d) {
         c->sumw += g->h_w[d];
         c->sumwf += (double)(float)g->h_w[d];
@@ -98,6 +115,7 @@ extern "C" rt_status rt_set_metric(rt_ctx *c, int kind, const double *params) {
     if (!c) return RT_EINVAL;
     if (kind != RT_MINKOWSKI_CART && kind != RT_KERR_SCHILD) return fail(c, RT_EINVAL, "unknown metric kind");
     if (c->metric >= 0) return fail(c, RT_ESTATE, "the metric is already set");
+    if (rt_status d = rt_check_device(c)) return d;
     c->metric = kind;
     if (kind == RT_KERR_SCHILD) {
         if (!params) return fail(c, RT_EINVAL, "Kerr-Schild needs {M, a}");
@@ -115,6 +133,7 @@ extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_
     if (!c) return RT_EINVAL;
     if (c->metric < 0) return fail(c, RT_ESTATE, "rt_set_metric must precede rt_set_fluid");
     if (!rho || !u_gas || !ucon || !kappa || !alpha_s_coef) return fail(c, RT_EINVAL, "null fluid array");
+    if (rt_status d = rt_check_device(c)) return d;
     c->rec_id = 0;   // a forward recording belongs to the fluid it ran with
     size_t n = (size_t)c->ncell * 8;
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->rho, rho, n, cudaMemcpyDefault, c->stream));
@@ -151,6 +170,9 @@ extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_
 
 extern "C" rt_status rt_set_intensity(rt_ctx *c, const void *I) {
     if (!c || !I) return RT_EINVAL;
+    if (rt_status d = rt_check_device(c)) return d;
+    // a deferred G belongs to the state being replaced
+    if (c->g_lazy) if (rt_status st = rt_resolve_g(c)) return st;
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->I[0], I, (size_t)c->ncell * c->nd * c->esize, cudaMemcpyDefault, c->stream));
     c->have_I = true;
     return RT_OK;
@@ -165,6 +187,7 @@ static bool is_host(const void *p) {
 extern "C" rt_status rt_get_intensity(rt_ctx *c, void *I) {
     if (!c || !I) return RT_EINVAL;
     if (!c->have_I) return fail(c, RT_ESTATE, "no intensity set");
+    if (rt_status d = rt_check_device(c)) return d;
     RT_CUDA_TRY(c, cudaMemcpyAsync(I, c->I[0], (size_t)c->ncell * c->nd * c->esize, cudaMemcpyDefault, c->stream));
     if (is_host(I)) RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return RT_OK;
@@ -173,6 +196,7 @@ extern "C" rt_status rt_get_intensity(rt_ctx *c, void *I) {
 extern "C" rt_status rt_set_ugas(rt_ctx *c, const double *u_gas) {
     if (!c || !u_gas) return RT_EINVAL;
     if (!c->have_fluid) return fail(c, RT_ESTATE, "rt_set_fluid must precede rt_set_ugas");
+    if (rt_status d = rt_check_device(c)) return d;
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->ug[0], u_gas, (size_t)c->ncell * 8, cudaMemcpyDefault, c->stream));
     return rt_launch_alpha(c, c->ug[0], c->alpha[0]);
 }
@@ -180,6 +204,7 @@ extern "C" rt_status rt_set_ugas(rt_ctx *c, const double *u_gas) {
 extern "C" rt_status rt_get_ugas(rt_ctx *c, double *u_gas) {
     if (!c || !u_gas) return RT_EINVAL;
     if (!c->have_fluid) return fail(c, RT_ESTATE, "no fluid set");
+    if (rt_status d = rt_check_device(c)) return d;
     RT_CUDA_TRY(c, cudaMemcpyAsync(u_gas, c->ug[0], (size_t)c->ncell * 8, cudaMemcpyDefault, c->stream));
     if (is_host(u_gas)) RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return RT_OK;
@@ -188,6 +213,7 @@ extern "C" rt_status rt_get_ugas(rt_ctx *c, double *u_gas) {
 extern "C" rt_status rt_cfl_dt(rt_ctx *c, double cfl, double *dt) {
     if (!c || !dt || !(cfl > 0.0)) return RT_EINVAL;
     if (c->metric < 0) return fail(c, RT_ESTATE, "rt_set_metric must precede rt_cfl_dt");
+    if (rt_status d = rt_check_device(c)) return d;
     double m;
     rt_status st = rt_launch_cfl(c, &m);
     if (st != RT_OK) return st;
@@ -238,6 +264,7 @@ extern "C" rt_status rt_get_timing(rt_ctx *c, double *ms, long long *launches) {
 extern "C" rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *n_fail) {
     if (!c || nsteps < 0) return RT_EINVAL;
     if (c->metric < 0 || !c->have_fluid || !c->have_I) return fail(c, RT_ESTATE, "metric, fluid and intensity must be set");
+    if (rt_status d = rt_check_device(c)) return d;
     if (!(dt > 0.0)) {
         if (c->dt_cfl <= 0.0) {
             rt_status st = rt_cfl_dt(c, 0.4, &c->dt_cfl);
@@ -281,12 +308,14 @@ extern "C" rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, 
 extern "C" rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G) {
     if (!c) return RT_EINVAL;
     if (!c->have_fluid || !c->have_I) return fail(c, RT_ESTATE, "fluid and intensity must be set");
+    if (rt_status d = rt_check_device(c)) return d;
     size_t nc = (size_t)c->ncell;
     bool hostR = R && is_host(R), hostE = Ebar && is_host(Ebar);
     double *dR = R, *dE = Ebar;
     if (hostR) RT_CUDA_TRY(c, cudaMalloc(&dR, nc * 80));
     if (hostE) RT_CUDA_TRY(c, cudaMalloc(&dE, nc * 8));
-    rt_status st = rt_launch_moments(c, dR, dE);
+    rt_status st = G && c->g_lazy ? rt_resolve_g(c) : RT_OK;
+    if (st == RT_OK) st = rt_launch_moments(c, dR, dE);
     if (st == RT_OK && hostR) RT_CUDA_TRY(c, cudaMemcpyAsync(R, dR, nc * 80, cudaMemcpyDeviceToHost, c->stream));
     if (st == RT_OK && hostE) RT_CUDA_TRY(c, cudaMemcpyAsync(Ebar, dE, nc * 8, cudaMemcpyDeviceToHost, c->stream));
     if (G) RT_CUDA_TRY(c, cudaMemcpyAsync(G, c->G, nc * 32, cudaMemcpyDefault, c->stream));

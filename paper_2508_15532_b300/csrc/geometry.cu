@@ -222,10 +222,13 @@ __global__ void k_dir_tables(int npt, int nd, double n0cut, const double *__rest
 // photon direction m, v^i = -(omega^i_{bc} - m^i omega^0_{bc}) m^b m^c
 // (geodesic equation in the tetrad frame; its components are the r^zeta,
 // r^psi of eq. angular_n_vectors), taken at the edge midpoint (eq. angular_fluxes).
+// eneg records where n_0(m) < 0: the flux takes its upwind value from the
+// sign of v.u_e (eq. angular_fluxes), which there is the opposite of the sign
+// of the tabulated product.
 __global__ void k_edge_tables(int npt, int ne, const double *__restrict__ emid, const double *__restrict__ eu,
                               const double *__restrict__ dlam, const double *__restrict__ pe,
                               const double *__restrict__ pg0, const double *__restrict__ pom,
-                              double *__restrict__ ew, float *__restrict__ ewf) {
+                              double *__restrict__ ew, float *__restrict__ ewf, uint8_t *__restrict__ eneg) {
     size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (idx >= (size_t)npt * ne) return;
     int p = (int)(idx / ne), e = (int)(idx % ne);
@@ -250,6 +253,7 @@ __global__ void k_edge_tables(int npt, int ne, const double *__restrict__ emid, 
     double v = dlam[e] * n0lo * vu;
     ew[idx] = v;
     ewf[idx] = (float)v;
+    eneg[idx] = n0lo < 0.0;
 }
 
 rt_status rt_build_geometry(rt_ctx *c) {
@@ -281,6 +285,7 @@ rt_status rt_build_geometry(rt_ctx *c) {
     RT_CUDA_TRY(c, A((void **)&c->fP_f, sizeof(float) * 3 * nPD));
     RT_CUDA_TRY(c, A((void **)&c->ew_d, sizeof(double) * nPE));
     RT_CUDA_TRY(c, A((void **)&c->ew_f, sizeof(float) * nPE));
+    RT_CUDA_TRY(c, A((void **)&c->eneg, nPE));
     k_points<<<(npt + 63) / 64, 64, 0, c->stream>>>(c->metric, c->M, c->a, c->gn[0], c->gn[1], ng0, ng1, cf.x0[0],
                                                     cf.x0[1], cf.x0[2], cf.dx[0], cf.dx[1], cf.dx[2], c->pt_e, c->pt_ei,
                                                     c->pt_V, c->pt_n0, c->pt_om, pg0, fe, fg0, fA, c->pt_len);
@@ -290,7 +295,8 @@ rt_status rt_build_geometry(rt_ctx *c) {
                                                                       c->fn_d, c->fn_f, c->fP_d, c->fP_f);
     RT_CUDA_TRY(c, cudaGetLastError());
     k_edge_tables<<<(unsigned)((nPE + 255) / 256), 256, 0, c->stream>>>(npt, ne, c->g->emid, c->g->eu, c->g->dlam,
-                                                                       c->pt_e, pg0, c->pt_om, c->ew_d, c->ew_f);
+                                                                       c->pt_e, pg0, c->pt_om, c->ew_d, c->ew_f,
+                                                                       c->eneg);
     RT_CUDA_TRY(c, cudaGetLastError());
     RT_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     cudaFree(pg0); cudaFree(fe); cudaFree(fg0); cudaFree(fA);

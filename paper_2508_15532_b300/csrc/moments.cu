@@ -51,6 +51,33 @@ __global__ void k_moments(int ncell, int nd, int nx0, int nx1, int gn0, int ng0,
     }
 }
 
+// Force on the gas of an interaction of the packed FP32 stage kernel (flat
+// geometry, fluid at rest), formed from its per-cell (a, c) and the state it
+// left, I_+ = (I + c)/(1 + a): Delta R^{0 mu} = c sum_s n^mu dOmega_s
+// - a sum_s n^mu I_+ dOmega_s, G = -Delta R^{0 mu} / dt (section 3.5.3).  One
+// warp per cell, FP64 sums.
+template <typename TS>
+__global__ void k_gdefer(int ncell, int nd, const void *__restrict__ I, const double *__restrict__ dir,
+                         const double *__restrict__ w, const float2 *__restrict__ gac, double sumw, double sn0,
+                         double sn1, double sn2, double idt, double *__restrict__ G) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= ncell) return;
+    const int c = warp;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = lane; s < nd; s += 32) {
+        const double Iw = ldd<TS>(I, (size_t)c * nd + s) * w[s];
+        acc[0] += Iw;
+        for (int m = 0; m < 3; ++m) acc[1 + m] += dir[3 * s + m] * Iw;
+    }
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0) {
+        const double a = gac[c].x, cc = gac[c].y;
+        const double sn[4] = {sumw, sn0, sn1, sn2};
+        for (int m = 0; m < 4; ++m) G[4 * (size_t)c + m] = -(cc * sn[m] - a * acc[m]) * idt;
+    }
+}
+
 // minimum over cells (pole-zeroed rows excluded), active axes and directions
 // of dx^a n^0 / |n^a|; positive doubles order like their bit patterns
 __global__ void k_cfl(int nx0, int nx1, int nd, int gn0, int ng0, int ng1, int flat, int npole, int a0, int a1,
@@ -101,6 +128,21 @@ rt_status rt_launch_moments(rt_ctx *c, double *R, double *Ebar) {
                                                                 ng0, ng1, flat, c->I[0], c->g->dir, c->g->w, c->pt_e,
                                                                 c->uhat, R, Ebar);
     RT_CUDA_TRY(c, cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status rt_resolve_g(rt_ctx *c) {
+    if (!c->g_lazy) return RT_OK;
+    unsigned blocks = (unsigned)(((size_t)c->ncell * 32 + 255) / 256);
+    const double idt = 1.0 / c->g_dt;
+    if (c->cfg.precision == RT_FP32)
+        k_gdefer<float><<<blocks, 256, 0, c->stream>>>(c->ncell, c->nd, c->I[0], c->g->dir, c->g->w, c->gac, c->sumw,
+                                                       c->sumnw[0], c->sumnw[1], c->sumnw[2], idt, c->G);
+    else
+        k_gdefer<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>(c->ncell, c->nd, c->I[0], c->g->dir, c->g->w, c->gac,
+                                                               c->sumw, c->sumnw[0], c->sumnw[1], c->sumnw[2], idt, c->G);
+    RT_CUDA_TRY(c, cudaGetLastError());
+    c->g_lazy = false;
     return RT_OK;
 }
 
@@ -231,8 +273,8 @@ extern "C" rt_status rt_cfl_dt_noalloc(rt_ctx *c, double cfl, double *dt) {
                  "limit of " + std::to_string((size_t)CFL_NA_MAX_BLOCKS * CFL_NA_ITEMS) + "; use rt_cfl_dt";
         return RT_EINVAL;
     }
-    int dev = 0;
-    RT_CUDA_TRY(c, cudaGetDevice(&dev));
+    if (rt_status d = rt_check_device(c)) return d;
+    const int dev = c->device;
     if (dev < 0 || dev >= CFL_NA_MAX_DEVICES) {
         c->err = "rt_cfl_dt_noalloc: device ordinal beyond " + std::to_string(CFL_NA_MAX_DEVICES);
         return RT_EINVAL;

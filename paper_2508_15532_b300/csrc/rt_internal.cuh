@@ -42,6 +42,7 @@ struct rt_ctx {
     rt_config cfg{};
     const rt_grid *g = nullptr;
     cudaStream_t stream = nullptr;
+    int device = -1;             // CUDA device current at rt_create: every buffer lives there
     int ncell = 0, nd = 0, ne = 0;
     int active[3] = {0, 0, 0};
     int gn[2] = {0, 0};          // ghosted extents of the (x1, x2) geometry table
@@ -60,6 +61,12 @@ struct rt_ctx {
     double *vel = nullptr;       // [ncell*3] coordinate velocity u^a/u^0
     double *uhat = nullptr;      // [ncell*4] tetrad-frame fluid velocity
     double *G = nullptr;         // [ncell*4]
+    // the packed FP32 stage kernel leaves the force on the gas of its
+    // interaction as per-cell (a, c) (I_+ = (I + c)/(1 + a)); rt_moments then
+    // forms G from them and the moments of the current state (g_lazy)
+    float2 *gac = nullptr;       // [ncell]
+    bool g_lazy = false;
+    double g_dt = 0.0;
     // per-cell constants of the fluid: kappa rho^m, alpha_s rho, rho/(Gamma-1), floor switch
     double *cc_au = nullptr, *cc_as = nullptr, *cc_Y = nullptr;
     uint8_t *cc_on = nullptr;
@@ -81,6 +88,7 @@ struct rt_ctx {
     double *fn_d = nullptr; float *fn_f = nullptr;         // [3*npt*nd] n^a at the lower face
     double *fP_d = nullptr; float *fP_f = nullptr;         // [3*npt*nd] dA_a n_0 at the lower face
     double *ew_d = nullptr; float *ew_f = nullptr;         // [npt*ne] dlam_e n_0(m) v(m).u_e
+    uint8_t *eneg = nullptr;     // [npt*ne] 1 where n_0(m) < 0: the upwind side follows v.u, i.e. the opposite sign of ew
     double dt_cfl = 0.0;
     // arena of the reverse pass (rt_step_adjoint), grown on demand
     double *adj = nullptr;
@@ -108,6 +116,11 @@ struct rt_ctx {
         }                                                                             \
     } while (0)
 
+// RT_EINVAL unless the calling thread's current device is the context's (its
+// buffers and stream belong to that device; a launch elsewhere would read
+// another GPU's pointers)
+rt_status rt_check_device(rt_ctx *c);
+
 // geometry (geometry.cu)
 rt_status rt_build_geometry(rt_ctx *c);
 rt_status rt_compute_uhat(rt_ctx *c);
@@ -122,4 +135,6 @@ rt_status rt_launch_cellconst(rt_ctx *c);
 
 // moments (moments.cu)
 rt_status rt_launch_moments(rt_ctx *c, double *R, double *Ebar);
+// G of a deferred interaction (g_lazy) into c->G from the current state; clears g_lazy
+rt_status rt_resolve_g(rt_ctx *c);
 rt_status rt_launch_cfl(rt_ctx *c, double *dt_min_host);

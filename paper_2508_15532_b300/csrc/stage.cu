@@ -360,10 +360,12 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                         for (int q = 0; q < RT_MAXNB; ++q) {
                             if (q < rg_kk) {
                                 const bool own = (rg_own >> q) & 1u;
-                                TM w = ldT<TM>(A.ew, (size_t)pc * A.ne + rg_e[q]);
+                                const size_t pe = (size_t)pc * A.ne + rg_e[q];
+                                TM w = ldT<TM>(A.ew, pe);
                                 TM Io = Arec[(o * nd + s) * 6 + q], It2 = Arec[(o * nd + rg_nb[q]) * 6 + rg_bk[q]];
                                 TM IL = own ? Io : It2, IR = own ? It2 : Io;
-                                TM F = w * (w > TM(0) ? IL : IR);
+                                // eq. angular_fluxes: upwind by the sign of v.u_e (w = dlam n_0 v.u_e)
+                                TM F = w * (((w > TM(0)) != (__ldg(A.eneg + pe) != 0)) ? IL : IR);
                                 a += own ? F : -F;
                             }
                         }
@@ -687,7 +689,8 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.Isrc = Isrc; A.Ibase = Ibase; A.Iout = Iout; A.ug_in = ug_in; A.ug_out = ug_out;
     A.alpha_in = alpha_in; A.alpha_int = alpha_int; A.alpha_out = alpha_out;
     A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y; A.cc_on = c->cc_on;
-    A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.G = G; A.fail = c->fail;
+    A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.G = G; A.gac = c->gac; A.fail = c->fail;
+    if (G) c->g_lazy = false;   // set again below if the packed kernel defers G
     A.sv_Em = c->sv_Em; A.sv_X = c->sv_X;
     A.mirror = g->mirror; A.nnb = g->nnb; A.nbr = g->nbr; A.ring_edge = g->ring_edge; A.ring_back = g->ring_back;
     A.edge = g->edge;
@@ -705,6 +708,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
         A.fn = dbl ? (const void *)c->fn_d : (const void *)c->fn_f;
         A.fP = dbl ? (const void *)c->fP_d : (const void *)c->fP_f;
         A.ew = dbl ? (const void *)c->ew_d : (const void *)c->ew_f;
+        A.eneg = c->eneg;
         A.mask = c->mask; A.pt_V = c->pt_V; A.pt_n0 = c->pt_n0; A.pt_len = c->pt_len; A.pt_e = c->pt_e;
     }
     for (int m = 0; m < 3; ++m) A.sumnw[m] = c->sumnw[m];

@@ -30,6 +30,7 @@ struct StageArgs {
     const double *cc_au, *cc_as, *cc_Y, *eta, *vel, *uhat;
     const uint8_t *cc_on;
     double *G;
+    float2 *gac;               // packed FP32 path: per-cell (a, c) of the interaction, for a deferred G
     unsigned long long *fail;
     double *sv_Em, *sv_X;      // optional per-cell E-bar_- and root X of the interaction (reverse-pass recompute)
     const int *mirror, *nnb, *nbr, *ring_edge, *ring_back, *edge;
@@ -38,6 +39,7 @@ struct StageArgs {
     int gn0, ng0, ng1;
     const void *cenU, *fn, *fP, *ew;           // math-type geometry tables (curved)
     const uint8_t *mask;
+    const uint8_t *eneg;       // per (point, edge): n_0(m) < 0 (see k_edge_tables)
     const double *pt_V, *pt_n0, *pt_e;
     const double *pt_len;
 };
@@ -174,6 +176,18 @@ template <typename R> __device__ bool newton_E(const Teq<R> &q, R X, R &lo, R &h
     }
     *Xout = X;
     return false;
+}
+
+// 1/x in FP64 without the FP64 division sequence (long on this part's FP64
+// pipe): an FP32 reciprocal refined by two Newton-Raphson steps
+// y <- y + y (1 - x y), each of which squares the relative error (1e-7 ->
+// 1e-14 -> rounding level); the exact division outside the FP32 range
+__device__ __forceinline__ double rcp64(double x) {
+    const double ax = fabs(x);
+    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
 }
 
 // T^-p in FP64 for the mixed path: for p = 3.5 an FP32 reciprocal square
