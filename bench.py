@@ -79,7 +79,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -127,6 +127,91 @@ def cpu_oracle_rate(n_cells, n_geo, steps):
     el = time.perf_counter() - t0
     nd = 10 * n_geo * n_geo + 2
     return n_cells ** 3 * nd * steps / el, el
+
+
+def oracle_windows(f, N, dt, nsteps, I_gpu, ug_gpu, win=24, core=8, nwin=2, seed=11):
+    """The CPU baseline and the stated error in one leg: the FP64 oracle (warmed
+    on a small box first) steps windows of the full box (outflow edges; a cell
+    after nsteps depends only on cells 2 nsteps per stage away, so a window's
+    central part is exact), timed, and the GPU state of the same steps is
+    compared with it there.  Returns (oracle cell-angle updates/s, sample
+    text, errors)."""
+    import oracle
+    from paper_2508_15532_b300 import workloads as W
+    nd = I_gpu.shape[1]
+    cw = W.base_config(4, (8, 8, 8), (0, 0, 0), (1.0 / N,) * 3, (("outflow", "outflow"),) * 3)
+    ow = oracle.Oracle(cw)                       # warm-up: library load, page faults, OpenMP pool
+    sub8 = {k: np.asarray(f[k])[: 8 ** 3] for k in ("rho", "ug", "ucon", "kappa", "alpha_s", "eta")}
+    ow.set_fluid(sub8["rho"], sub8["ug"], sub8["ucon"], sub8["kappa"], sub8["alpha_s"], sub8["eta"])
+    ow.set_intensity(np.asarray(f["I"][: 8 ** 3], dtype=np.float64))
+    ow.step(dt, 1)
+    rng = np.random.default_rng(seed)
+    starts = [(N - win // 2,) * 3] + [tuple(int(x) for x in rng.integers(0, N, 3)) for _ in range(nwin - 1)]
+    I3, u3 = I_gpu.reshape(N, N, N, nd), ug_gpu.reshape(N, N, N)
+    w = None
+    eI = eE = eU = 0.0
+    el = 0.0
+    c = slice(core, win - core)
+    for st in starts:
+        ii = [(st[a] + np.arange(win)) % N for a in range(3)]
+        sel = np.ix_(ii[2], ii[1], ii[0])
+        sub = lambda a: np.ascontiguousarray(np.asarray(a).reshape(N, N, N, *np.asarray(a).shape[1:])[sel]
+                                             .reshape(win ** 3, *np.asarray(a).shape[1:]))
+        cs = W.base_config(4, (win, win, win), (0, 0, 0), (1.0 / N,) * 3, (("outflow", "outflow"),) * 3)
+        o = oracle.Oracle(cs)
+        o.set_fluid(sub(f["rho"]), sub(f["ug"]), sub(f["ucon"]), sub(f["kappa"]), sub(f["alpha_s"]), sub(f["eta"]))
+        o.set_intensity(sub(np.asarray(f["I"], dtype=np.float64)))
+        t0 = time.perf_counter()
+        o.step(dt, nsteps)
+        el += time.perf_counter() - t0
+        if w is None:
+            w = o.grid()["w"]
+        Ir = o.intensity().reshape(win, win, win, nd)[c, c, c]
+        Ig = I3[sel][c, c, c].astype(np.float64)
+        fl = 1e-3 * np.abs(Ir).max()
+        eI = max(eI, float((np.abs(Ig - Ir) / np.maximum(np.abs(Ir), fl)).max()))
+        Er, Eg = Ir @ w, Ig @ w
+        eE = max(eE, float((np.abs(Eg - Er) / np.abs(Er)).max()))
+        ur = o.ug().reshape(win, win, win)[c, c, c]
+        eU = max(eU, float((np.abs(u3[sel][c, c, c] - ur) / np.abs(ur)).max()))
+    rate = len(starts) * win ** 3 * nd * nsteps / el
+    sample = ("%d windows of %d^3 cells (one across the periodic boundary) of the %d^3 box, 162 directions, "
+              "%d steps each (%.1f s), after a warm-up step on 8^3" % (len(starts), win, N, nsteps, el))
+    errs = {"intensity_max_rel": eI, "intensity_floor": "1e-3 of the window's largest", "Ebar_max_rel": eE,
+            "ugas_max_rel": eU, "steps": nsteps,
+            "cells_compared": "%d windows x %d^3 central cells x %d directions" % (len(starts), win - 2 * core, nd),
+            "bars": {"intensity": 1e-4, "Ebar": 2e-5}}
+    return rate, sample, errs
+
+
+def step_leg(dev, grid, cfg, f, prec, warm=1, steps=3):
+    """ms per rt_step and the stage kernel's mean launch time for one more
+    workload or precision (CUDA events on the library stream)."""
+    import torch
+    import paper_2508_15532_b300 as rt
+    stream = torch.cuda.Stream(device=dev)
+    tdt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[prec]
+    with torch.cuda.stream(stream):
+        st = rt.RadiationStep(grid, cfg, precision=prec, stream=stream.cuda_stream)
+        T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+        st.set_fluid(*[T(f[k]) for k in ("rho", "ug", "ucon", "kappa", "alpha_s", "eta")])
+        st.set_intensity(torch.as_tensor(np.asarray(f["I"])).to(dev).to(tdt))
+        dt = st.cfl_dt(0.4)
+        for _ in range(warm):
+            st.step(dt, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        st.set_timing(True)
+        e0.record(stream)
+        for _ in range(steps):
+            st.step(dt, 1)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        stage_ms, launches = st.get_timing()
+        st.set_timing(False)
+    del st
+    return ms, stage_ms / max(launches, 1)
 
 
 def max_over_ranks(x, dist=None):
@@ -229,6 +314,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=9)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the FP64-step and kerr3d legs (profiling runs)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the reverse mode (FP64 and mixed) and print its JSON line")
     ap.add_argument("--adjoint-cells", type=int, default=64)
@@ -300,7 +387,6 @@ def main():
         ug_host = torch.from_numpy(np.ascontiguousarray(f["ug"])).pin_memory()
         st.set_intensity(I_host)
         dt = st.cfl_dt(0.4)
-    del f
     stream.synchronize()
 
     def barrier():
@@ -388,6 +474,49 @@ def main():
     h2d = I_host.numel() * I_host.element_size() + ug_host.numel() * 8
     d2h = out_I.numel() * out_I.element_size() + out_ug.numel() * 8
 
+    # ---- stated error against the FP64 oracle and the CPU baseline (one leg):
+    # two steps of the bench's workload from its initial state, in the bench's
+    # launch configuration, compared on oracle windows that are also timed
+    cpu = err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "flat3d":
+        NE = 2
+        with torch.cuda.stream(stream):
+            st.set_intensity(I_host)
+            st.set_ugas(ug_host)
+            st.step(dt, NE)
+            st.get_intensity(out_I)
+            st.get_ugas(out_ug)
+        stream.synchronize()
+        rate, sample, err = oracle_windows(f, N, dt, NE, out_I.float().numpy() if prec == "bf16" else out_I.numpy(),
+                                           out_ug.numpy())
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+    del f
+
+    # ---- the all-FP64 GPU step and the Kerr-Schild torus (kerr3d) on the same box
+    fp64_leg = kerr_leg = None
+    if rank == 0 and world == 1 and not args.no_extra_legs and args.workload == "flat3d":
+        peak_gbs = measured_peaks()[0]
+        cfg64, f64 = W.flat3d(N=N, n_geo=4, intensity_dtype=np.float64)
+        ms64, lms64 = step_leg(dev, grid, cfg64, f64, "fp64")
+        del f64
+        ca = ncell * nd
+        alg64 = (ca * 5 * 8 + ncell * FLUID_BYTES_PER_CELL_STEP) / 2.0
+        fp64_leg = {"workload": wname + " %d^3, all FP64" % N, "ms_per_step": ms64, "value": ca / (ms64 * 1e-3),
+                    "unit": UNIT, "kernel": "k_stage_fs<double> (transport + interaction, fused)",
+                    "avg_launch_ms": lms64, "roofline_frac": alg64 / (lms64 * 1e-3) / 1e9 / peak_gbs,
+                    "algorithmic_bytes_per_launch": alg64}
+        cfgk, fk = W.kerr3d(n_geo=4)
+        fk["I"] = fk["I"].astype(np.float32)
+        msk, lmsk = step_leg(dev, grid, cfgk, fk, "fp32")
+        nck = int(np.prod(cfgk["nx"]))
+        del fk
+        algk = (nck * nd * 5 * 4 + nck * FLUID_BYTES_PER_CELL_STEP) / 2.0
+        kerr_leg = {"workload": "kerr3d-kerr-schild-a0.9-torus %dx%dx%d, FP32 storage" % tuple(cfgk["nx"]),
+                    "ms_per_step": msk, "value": nck * nd / (msk * 1e-3), "unit": UNIT,
+                    "kernel": "k_stage (general: Kerr-Schild, MAPR angular flux, boosted interaction)",
+                    "avg_launch_ms": lmsk, "roofline_frac": algk / (lmsk * 1e-3) / 1e9 / peak_gbs,
+                    "algorithmic_bytes_per_launch": algk}
+
     adj = adj_mixed = None
     if world == 1 and not args.no_adjoint:
         del st
@@ -395,12 +524,6 @@ def main():
         adj_mixed = adjoint_leg(dev, stream, grid, "fp32")
         st = None
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_ref = args.ref_cells
-        rate, el = cpu_oracle_rate(n_ref, 4, 1)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "%d^3 periodic box of the same recipe, 162 directions, 1 step (%.1f s)" % (n_ref, el)}
 
     if rank == 0:
         line = {
@@ -413,6 +536,9 @@ def main():
                        "l2": "inputs larger than L2 (%.2f GB per intensity array)" % (cell_angles * S / 1e9)},
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "error_vs_oracle": err,
+            "fp64_step": fp64_leg,
+            "kerr3d": kerr_leg,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "steps": E, "mode": "pinned host buffers; %d contexts on %d streams take steps in turn" % (NCTX, NCTX)},
             "gpu_launches": int(launches),

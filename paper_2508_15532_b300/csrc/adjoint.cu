@@ -144,7 +144,25 @@ __device__ __forceinline__ void lim_pre(int kind, float dl, float dr, float prod
         hs = 0.0f; gl = 0.0f; gr = 0.0f;
     }
 }
+// MC for a pair of lanes: the value from the min/max form (mc_half_xs, the
+// forward kernel's); the branch from exact equalities, since hs equals dl
+// bit for bit exactly when |dl| is a minimum (taken first at ties) and dr when
+// |dr| is (and |dl| is not); otherwise the quarter sum.  The branch masks are
+// 1/0 per lane, combined with packed arithmetic:
+//   gl = ok (e_l + e_q / 4), gr = ok (e_r + e_q / 4), e_q = 1 - e_l - e_r
+__device__ __forceinline__ void limv_mc(F2 dl, F2 dr, F2 &hs, F2 &gl, F2 &gr, F2 &gd) {
+    const F2 prod = dl * dr, q4 = f2(0.25f) * (dl + dr);
+    hs = F2{mc_half_xs(dl.x, dr.x, q4.x), mc_half_xs(dl.y, dr.y, q4.y)};
+    const F2 ok = F2{prod.x > 0.0f ? 1.0f : 0.0f, prod.y > 0.0f ? 1.0f : 0.0f};
+    const F2 el = F2{hs.x == dl.x ? 1.0f : 0.0f, hs.y == dl.y ? 1.0f : 0.0f};
+    const F2 er0 = F2{hs.x == dr.x ? 1.0f : 0.0f, hs.y == dr.y ? 1.0f : 0.0f};
+    const F2 er = fma2(F2{-er0.x, -er0.y}, el, er0);
+    gl = ok * fma2(f2(-0.25f), er, fma2(f2(0.75f), el, f2(0.25f)));
+    gr = ok * fma2(f2(-0.25f), el, fma2(f2(0.75f), er, f2(0.25f)));
+    gd = gr - gl;
+}
 __device__ __forceinline__ void limv(int kind, F2 dl, F2 dr, F2 &hs, F2 &gl, F2 &gr, F2 &gd) {
+    if (kind == RT_LIM_MC) { limv_mc(dl, dr, hs, gl, gr, gd); return; }
     const F2 prod = dl * dr, q4 = f2(0.25f) * (dl + dr);
     lim_pre(kind, dl.x, dr.x, prod.x, q4.x, hs.x, gl.x, gr.x);
     lim_pre(kind, dl.y, dr.y, prod.y, q4.y, hs.y, gl.y, gr.y);
@@ -381,12 +399,14 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     constexpr int NRED = FUSE ? 2 * NOWN : NOWN;   // per x position: alpha-bar (and Q) of the own cells
     __shared__ int xmap[TXC + 4];                  // x1 window: positions i0 - 2 .. i0 + TXC + 1
     __shared__ int rowY[BZ * (BY + 4)], rowZ[BY * (BZ + 4)];
+    // the same positions and rows as element offsets (times n_dir), resolved once
+    __shared__ int xoff[TXC + 4], rowYo[BZ * (BY + 4)], rowZo[BY * (BZ + 4)];
     __shared__ __align__(16) S recX[NOWN][TXC + 3][8];   // x1 faces between window positions f, f + 1
     __shared__ __align__(16) S recY[BZ][BY + 3][TXC][8];
     __shared__ __align__(16) S recZ[BY][BZ + 3][TXC][8];
     __shared__ S part[NW][NRED][TXC];
     __shared__ S partP[NW][RNC];
-    __shared__ double cInv[RNC], cUb[RNC], cEmb[RNC];
+    __shared__ S cInv[RNC], cUb[RNC], cEmb[RNC];   // rounded to the pass's type once, at the solve
     // FP32 pass: the x1 pipeline's next own-row values (I and Zg at x1 = i + 3)
     // are copied one position ahead with cp.async (double-buffered)
     constexpr bool PFX = L == 2;
@@ -408,16 +428,21 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         if (per) return ((q % n) + n) % n;
         return (q < 0 ? 0 : n - 1) | F_OUT;
     };
-    for (int t = p; t < TXC + 4; t += NT) xmap[t] = mapq(i0 - 2 + t, nx0, A.per[0]);
+    for (int t = p; t < TXC + 4; t += NT) {
+        xmap[t] = mapq(i0 - 2 + t, nx0, A.per[0]);
+        xoff[t] = (xmap[t] & F_IDX) * nd;
+    }
     for (int t = p; t < BZ * (BY + 4); t += NT) {
         const int q = t % (BY + 4), r = t / (BY + 4);
         const int my = mapq(j0 - 2 + q, nx1, A.per[1]);
         rowY[t] = (((k0 + r) * nx1 + (my & F_IDX)) * nx0) | (my & F_OUT);
+        rowYo[t] = ((k0 + r) * nx1 + (my & F_IDX)) * nx0 * nd;
     }
     for (int t = p; t < BY * (BZ + 4); t += NT) {
         const int r = t % (BZ + 4), q = t / (BZ + 4);
         const int mz = mapq(k0 - 2 + r, nx2, A.per[2]);
         rowZ[t] = (((mz & F_IDX) * nx1 + j0 + q) * nx0) | (mz & F_OUT);
+        rowZo[t] = ((mz & F_IDX) * nx1 + j0 + q) * nx0 * nd;
     }
     __syncthreads();
     if (A.transport) {
@@ -467,7 +492,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     auto ldZ = [&](int off) -> V { return LT::ld(Zp + off); };
     // element offsets (32 bits: the host checks n_cell n_dir < 2^31) of the
     // stencil rows at x1 = 0, and which of them lie beyond an outflow boundary
-    auto own = [&](int o) -> int { return (rowY[(o / BY) * (BY + 4) + o % BY + 2] & F_IDX) * nd + d0; };
+    int ownv[NOWN];
+#pragma unroll
+    for (int o = 0; o < NOWN; ++o) ownv[o] = rowYo[(o / BY) * (BY + 4) + o % BY + 2] + d0;
+    auto own = [&](int o) -> int { return ownv[o]; };
 
     // x1 pipeline per own row, at own position p: xE = the part of p's
     // cotangent known before face p + 3/2 (faces p -+ 1/2 and the slope terms
@@ -489,7 +517,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
             V Iw[4], Zw[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int xd = xmap[u], off = ob + (xd & F_IDX) * nd;
+                const int xd = xmap[u], off = ob + xoff[u];
                 Iw[u] = ldI(off);
                 Zw[u] = beyond(xd) ? zero : ldZ(off);
             }
@@ -518,10 +546,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     auto pf_issue = [&](int ii) {
         if constexpr (PFX) {
             if (!act) return;
-            const int xd = xmap[ii + 4], st = ii & 1;
+            const int xd = xmap[ii + 4], st = ii & 1, xo = xoff[ii + 4];
 #pragma unroll
             for (int o = 0; o < NOWN; ++o) {
-                const int off = own(o) + (xd & F_IDX) * nd;
+                const int off = own(o) + xo;
                 cp_async8f(&pfb[st][o][d0], (const float *)Ip + off);
                 if (!beyond(xd)) cp_async8f(&pfb[st][NOWN + o][d0], (const float *)Zp + off);
             }
@@ -542,9 +570,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 cp_commit();
                 cp_wait1();
             }
+            const int xo = xoff[ii + 4];
 #pragma unroll
             for (int o = 0; o < NOWN; ++o) {
-                const int off = own(o) + (xd & F_IDX) * nd;
+                const int off = own(o) + xo;
                 V I2, Z2;
                 if constexpr (PFX) {
                     const float2 a = *reinterpret_cast<const float2 *>(&pfb[ii & 1][o][d0]);
@@ -580,7 +609,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         }
         // one column of NB own cells along x2 or x3 (window rows k = 0 .. NB + 3,
         // own rows k = 2 .. NB + 1)
-        auto column = [&](auto NBc, const int *rows, int ax, auto ownidx, auto recp) {
+        auto column = [&](auto NBc, const int *rows, const int *rowso, int ax, auto ownidx, auto recp) {
             constexpr int NB = decltype(NBc)::value;
             V Yv[NB + 4], Bv[NB + 4];
             unsigned out = 0u;
@@ -590,7 +619,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 out |= (unsigned)beyond(d) << k;
                 if (k >= 2 && k < NB + 2) { Yv[k] = Ic[ownidx(k - 2)]; Bv[k] = Zc[ownidx(k - 2)]; }
                 else {
-                    const int off = (d & F_IDX) * nd + d0 + ie;
+                    const int off = rowso[k] + d0 + ie;
                     Yv[k] = ldI(off);
                     Bv[k] = beyond(d) ? zero : ldZ(off);
                 }
@@ -631,13 +660,15 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         if (A.transport && A.act[1]) {
 #pragma unroll
             for (int r = 0; r < BZ; ++r)
-                column(std::integral_constant<int, BY>{}, rowY + r * (BY + 4), 1, [&](int q) { return r * BY + q; },
+                column(std::integral_constant<int, BY>{}, rowY + r * (BY + 4), rowYo + r * (BY + 4), 1,
+                       [&](int q) { return r * BY + q; },
                        [&](int f) -> const S * { return recY[r][f][ii]; });
         }
         if (A.transport && A.act[2]) {
 #pragma unroll
             for (int q = 0; q < BY; ++q)
-                column(std::integral_constant<int, BZ>{}, rowZ + q * (BZ + 4), 2, [&](int r) { return r * BY + q; },
+                column(std::integral_constant<int, BZ>{}, rowZ + q * (BZ + 4), rowZo + q * (BZ + 4), 2,
+                       [&](int r) { return r * BY + q; },
                        [&](int f) -> const S * { return recZ[q][f][ii]; });
         }
         S red[NRED];
@@ -715,7 +746,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 A.ub_dst[c] = (A.ub_dst_acc ? A.ub_dst[c] : 0.0) + r.ugb;
                 A.kb[c] += kbv + r.kb;
                 A.eb[c] += r.eb;
-                cInv[lc] = r.inv; cUb[lc] = r.ub; cEmb[lc] = r.Emb;
+                cInv[lc] = (S)r.inv; cUb[lc] = (S)r.ub; cEmb[lc] = (S)r.Emb;
             }
         }
     }
@@ -736,7 +767,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                     } else {
                         ib = sIt[lc * (NT * L) + d0];
                     }
-                    const V out = (ib - LT::splat((S)cUb[lc]) * wv) * LT::splat((S)cInv[lc]) + LT::splat((S)cEmb[lc]) * wv;
+                    const V out = (ib - LT::splat(cUb[lc]) * wv) * LT::splat(cInv[lc]) + LT::splat(cEmb[lc]) * wv;
                     LT::st((S *)A.Zout + own(o) + (i0 + ii) * nd, out);
                 }
             }
