@@ -11,7 +11,7 @@ import numpy as np
 
 from .build import build
 
-BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3}
+BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3, "halo": 4}
 COORDS = {"minkowski": 0, "kerr_schild": 1}
 LIMITER = {"mc": 0, "minmod": 1, "donor": 2}
 ANG = {"mapr": 0, "donor": 1}
@@ -55,6 +55,13 @@ def lib(mutant: int = 0):
         L.or_cfl_dt.argtypes = [C.c_void_p, C.c_double]
         L.or_step.restype = C.c_long
         L.or_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.or_step_stage.restype = C.c_long
+        L.or_step_stage.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.or_halo_doubles.restype = C.c_size_t
+        L.or_halo_doubles.argtypes = [C.c_void_p]
+        L.or_halo_pack.argtypes = [C.c_void_p, C.c_int, _D, _D]
+        L.or_halo_unpack.argtypes = [C.c_void_p, _D, _D]
+        L.or_set_fluid_halo.argtypes = [C.c_void_p, _D, _D]
         L.or_source_only.restype = C.c_long
         L.or_source_only.argtypes = [C.c_void_p, C.c_double]
         L.or_moments.argtypes = [C.c_void_p, _D, _D, _D]
@@ -148,6 +155,36 @@ class Oracle:
 
     def cfl_dt(self, cfl):
         return self.L.or_cfl_dt(self.h, float(cfl))
+
+    def step_stage(self, dt, stage):
+        """One stage of a step (0: predictor or the single Euler stage, 1:
+        corrector); the unconverged temperature solves of the stage."""
+        r = self.L.or_step_stage(self.h, float(dt), int(stage))
+        if r < 0:
+            raise RuntimeError("oracle: " + self.L.or_error().decode())
+        return r
+
+    def halo_doubles(self):
+        return int(self.L.or_halo_doubles(self.h))
+
+    def halo_pack(self, stage):
+        """(lo, hi): the first and last two owned x3 planes of the source of
+        `stage` (intensities, then gas energies)."""
+        n = self.halo_doubles()
+        lo, hi = np.empty(n), np.empty(n)
+        if self.L.or_halo_pack(self.h, int(stage), lo, hi):
+            raise RuntimeError("oracle: " + self.L.or_error().decode())
+        return lo, hi
+
+    def halo_unpack(self, lo, hi):
+        if self.L.or_halo_unpack(self.h, _f(lo), _f(hi)):
+            raise RuntimeError("oracle: " + self.L.or_error().decode())
+
+    def set_fluid_halo(self, lo, hi):
+        """Fluid of the ghost planes, per side [2 planes * P, 7] as (rho,
+        kappa, alpha_s coefficient, u^0..u^3)."""
+        if self.L.or_set_fluid_halo(self.h, _f(lo), _f(hi)):
+            raise RuntimeError("oracle: " + self.L.or_error().decode())
 
     def step(self, dt, nsteps=1):
         return self.L.or_step(self.h, float(dt), int(nsteps))

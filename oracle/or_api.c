@@ -9,6 +9,13 @@ void or_set_err(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 const char *or_error(void) { return g_err; }
 
 or_ctx *or_create(const or_config *cfg) {
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            if (cfg->bc[a][sd] == OR_BC_HALO && (a != 2 || cfg->nx[2] < 2 ||
+                                                  cfg->bc[1][0] == OR_BC_POLE || cfg->bc[1][1] == OR_BC_POLE)) {
+                or_set_err("halo boundaries: x3 faces only, at least 2 x3 cells, no pole boundary on x2");
+                return NULL;
+            }
     or_ctx *c = calloc(1, sizeof(or_ctx));
     c->c = *cfg;
     if (or_build_grid(&c->G, cfg->n_geo) != 0) { or_set_err("grid: n must be a power of two"); free(c); return NULL; }
@@ -38,6 +45,18 @@ or_ctx *or_create(const or_config *cfg) {
     c->cs = calloc(n, sizeof(double)); c->eta = calloc(n, sizeof(double));
     c->G4 = calloc(4 * n, sizeof(double));
     for (size_t i = 0; i < n; ++i) { c->ucon[4 * i] = 1.0; c->eta[i] = 1.0; }
+    c->Is = calloc(n * c->G.nd, sizeof(double)); c->I2 = calloc(n * c->G.nd, sizeof(double));
+    c->ugs = calloc(n, sizeof(double)); c->ug2 = calloc(n, sizeof(double));
+    c->halo = cfg->bc[2][0] == OR_BC_HALO || cfg->bc[2][1] == OR_BC_HALO;
+    if (c->halo) {
+        size_t P2 = 2 * (size_t)cfg->nx[0] * cfg->nx[1];
+        for (int sd = 0; sd < 2; ++sd) {
+            c->hI[sd] = calloc(P2 * c->G.nd, sizeof(double)); c->hug[sd] = calloc(P2, sizeof(double));
+            c->hrho[sd] = calloc(P2, sizeof(double)); c->hkap[sd] = calloc(P2, sizeof(double));
+            c->hcs[sd] = calloc(P2, sizeof(double)); c->hucon[sd] = calloc(4 * P2, sizeof(double));
+            for (size_t q = 0; q < P2; ++q) c->hucon[sd][4 * q] = 1.0;
+        }
+    }
     return c;
 }
 
@@ -46,6 +65,10 @@ void or_destroy(or_ctx *c) {
     or_free_grid(&c->G);
     free(c->gc); for (int a = 0; a < 3; ++a) free(c->gf[a]);
     free(c->I); free(c->ug); free(c->rho); free(c->ucon); free(c->kap); free(c->cs); free(c->eta); free(c->G4);
+    free(c->Is); free(c->I2); free(c->ugs); free(c->ug2);
+    for (int sd = 0; sd < 2; ++sd) {
+        free(c->hI[sd]); free(c->hug[sd]); free(c->hrho[sd]); free(c->hkap[sd]); free(c->hcs[sd]); free(c->hucon[sd]);
+    }
     free(c);
 }
 
@@ -105,30 +128,80 @@ double or_cfl_dt(const or_ctx *c, double cfl) {
     return cfl * best;
 }
 
-/* one full step, section 3.6: predictor (transport over dt/2 from I^n, then
-   the implicit interaction over dt/2) and corrector (transport over dt from
-   I^n with the fluxes of the predictor state, then the interaction over dt);
-   the gas enters each interaction with u_g^n */
-long or_step(or_ctx *c, double dt, int nsteps) {
+/* one stage of a step, section 3.6: the predictor (transport over dt/2 from
+   I^n, then the implicit interaction over dt/2) and the corrector (transport
+   over dt from I^n with the fluxes of the predictor state, then the
+   interaction over dt); the gas enters each interaction with u_g^n.  Order 1
+   is a single Euler stage.  The state takes the step's result after its last
+   stage. */
+long or_step_stage(or_ctx *c, double dt, int stage) {
     size_t n = (size_t)c->ncell, ni = n * c->G.nd;
-    double *Is = malloc(sizeof(double) * ni), *I2 = malloc(sizeof(double) * ni);
-    double *ugs = malloc(sizeof(double) * n), *ug2 = malloc(sizeof(double) * n);
+    int last = c->c.order == 1 ? 0 : 1;
+    if (stage != c->next_stage || stage > last) { or_set_err("or_step_stage: stage out of order"); return -1; }
     long fails = 0;
-    for (int st = 0; st < nsteps; ++st) {
-        if (c->c.order == 1) {
-            if (c->c.transport) or_transport_stage(c, c->I, c->ug, c->I, dt, I2); else memcpy(I2, c->I, sizeof(double) * ni);
-            if (c->c.source) fails += or_source_step(c, I2, c->ug, ug2, dt, c->G4); else memcpy(ug2, c->ug, sizeof(double) * n);
-        } else {
-            if (c->c.transport) or_transport_stage(c, c->I, c->ug, c->I, 0.5 * dt, Is); else memcpy(Is, c->I, sizeof(double) * ni);
-            if (c->c.source) fails += or_source_step(c, Is, c->ug, ugs, 0.5 * dt, NULL); else memcpy(ugs, c->ug, sizeof(double) * n);
-            if (c->c.transport) or_transport_stage(c, Is, ugs, c->I, dt, I2); else memcpy(I2, c->I, sizeof(double) * ni);
-            if (c->c.source) fails += or_source_step(c, I2, c->ug, ug2, dt, c->G4); else memcpy(ug2, c->ug, sizeof(double) * n);
-        }
-        memcpy(c->I, I2, sizeof(double) * ni);
-        memcpy(c->ug, ug2, sizeof(double) * n);
+    if (stage == 0 && last == 1) {
+        if (c->c.transport) or_transport_stage(c, c->I, c->ug, c->I, 0.5 * dt, c->Is); else memcpy(c->Is, c->I, sizeof(double) * ni);
+        if (c->c.source) fails += or_source_step(c, c->Is, c->ug, c->ugs, 0.5 * dt, NULL); else memcpy(c->ugs, c->ug, sizeof(double) * n);
+        c->next_stage = 1;
+        return fails;
     }
-    free(Is); free(I2); free(ugs); free(ug2);
+    const double *Isrc = stage == 0 ? c->I : c->Is, *usrc = stage == 0 ? c->ug : c->ugs;
+    if (c->c.transport) or_transport_stage(c, Isrc, usrc, c->I, dt, c->I2); else memcpy(c->I2, c->I, sizeof(double) * ni);
+    if (c->c.source) fails += or_source_step(c, c->I2, c->ug, c->ug2, dt, c->G4); else memcpy(c->ug2, c->ug, sizeof(double) * n);
+    memcpy(c->I, c->I2, sizeof(double) * ni);
+    memcpy(c->ug, c->ug2, sizeof(double) * n);
+    c->next_stage = 0;
     return fails;
+}
+
+long or_step(or_ctx *c, double dt, int nsteps) {
+    if (c->halo) { or_set_err("or_step: a context with x3 halos steps by stages (or_step_stage)"); return -1; }
+    long fails = 0;
+    for (int st = 0; st < nsteps; ++st)
+        for (int stage = 0; stage <= (c->c.order == 1 ? 0 : 1); ++stage) fails += or_step_stage(c, dt, stage);
+    return fails;
+}
+
+size_t or_halo_doubles(const or_ctx *c) {
+    size_t P2 = 2 * (size_t)c->c.nx[0] * c->c.nx[1];
+    return P2 * c->G.nd + P2;
+}
+
+int or_halo_pack(const or_ctx *c, int stage, double *lo, double *hi) {
+    if (!c->halo) { or_set_err("or_halo_pack: no x3 halo"); return -1; }
+    size_t P = (size_t)c->c.nx[0] * c->c.nx[1], nd = c->G.nd, n = (size_t)c->ncell;
+    const double *I = stage == 0 ? c->I : c->Is, *u = stage == 0 ? c->ug : c->ugs;
+    double *dst[2] = {lo, hi};
+    size_t first[2] = {0, n - 2 * P};
+    for (int sd = 0; sd < 2; ++sd) {
+        memcpy(dst[sd], I + first[sd] * nd, sizeof(double) * 2 * P * nd);
+        memcpy(dst[sd] + 2 * P * nd, u + first[sd], sizeof(double) * 2 * P);
+    }
+    return 0;
+}
+
+int or_halo_unpack(or_ctx *c, const double *lo, const double *hi) {
+    if (!c->halo) { or_set_err("or_halo_unpack: no x3 halo"); return -1; }
+    size_t P = (size_t)c->c.nx[0] * c->c.nx[1], nd = c->G.nd;
+    const double *src[2] = {lo, hi};
+    for (int sd = 0; sd < 2; ++sd) {
+        memcpy(c->hI[sd], src[sd], sizeof(double) * 2 * P * nd);
+        memcpy(c->hug[sd], src[sd] + 2 * P * nd, sizeof(double) * 2 * P);
+    }
+    return 0;
+}
+
+int or_set_fluid_halo(or_ctx *c, const double *lo, const double *hi) {
+    if (!c->halo) { or_set_err("or_set_fluid_halo: no x3 halo"); return -1; }
+    size_t P2 = 2 * (size_t)c->c.nx[0] * c->c.nx[1];
+    const double *src[2] = {lo, hi};
+    for (int sd = 0; sd < 2; ++sd)
+        for (size_t q = 0; q < P2; ++q) {
+            const double *f = src[sd] + 7 * q;
+            c->hrho[sd][q] = f[0]; c->hkap[sd][q] = f[1]; c->hcs[sd][q] = f[2];
+            for (int m = 0; m < 4; ++m) c->hucon[sd][4 * q + m] = f[3 + m];
+        }
+    return 0;
 }
 
 long or_source_only(or_ctx *c, double dt) {

@@ -58,6 +58,14 @@ struct or_ctx {
     double *I, *ug;
     double *rho, *ucon, *kap, *cs, *eta;
     double *G4;           /* [ncell*4] force on the gas from the last interaction */
+    /* stage states of the step in progress: predictor (Is, ugs), step result (I2, ug2) */
+    double *Is, *ugs, *I2, *ug2;
+    int next_stage;
+    /* x3 halo (OR_BC_HALO): ghost planes k = -2, -1 (side 0) and nx2, nx2 + 1
+       (side 1), plane-major like the cells; intensities and gas energy of the
+       stage source, fluid of the ghost cells */
+    int halo;
+    double *hI[2], *hug[2], *hrho[2], *hkap[2], *hcs[2], *hucon[2];
 };
 
 static inline int or_gidx(const or_ctx *c, int i, int j, int k) {
@@ -87,6 +95,11 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
 long or_source_step(or_ctx *c, double *I, const double *ug_in, double *ug_out, double dtk, double *G4);
 double or_limiter(int kind, double dl, double dr);
 int or_map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row);
+/* ghost fluid and gas energy of the ghosted cell (i, j, k) of a transport
+   stage whose source gas energy is ug_src: the cell it copies, or the caller's
+   halo plane */
+void or_ghost_fluid(const or_ctx *c, int i, int j, int k, const double *ug_src, double *rho, double *ug,
+                    double *kap, double *cs, const double **ucon);
 void or_fill_ghosts(const or_ctx *c, const double *I, double *Ig);
 
 #endif

@@ -80,12 +80,16 @@ double or_face_flux(double n, double IL, double IR, double Il, double Ir,
    (theta -> -theta, phi -> phi + pi), seen with theta-hat and phi-hat reversed. */
 int or_map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row) {
     *mir = 0; *fixed_row = -1;
+    int halo = -1;
     for (int a = 0; a < 3; ++a) {
         int n = c->c.nx[a];
         if (idx[a] >= 0 && idx[a] < n) continue;
         int side = idx[a] < 0 ? 0 : 1;
         int bc = c->c.bc[a][side];
-        if (bc == OR_BC_PERIODIC) idx[a] = ((idx[a] % n) + n) % n;
+        if (bc == OR_BC_HALO) {            /* x3 only: plane 0, 1 of the caller's ghost planes */
+            halo = side;
+            idx[a] = side ? idx[a] - n : idx[a] + 2;
+        } else if (bc == OR_BC_PERIODIC) idx[a] = ((idx[a] % n) + n) % n;
         else if (bc == OR_BC_OUTFLOW) idx[a] = side ? n - 1 : 0;
         else if (bc == OR_BC_POLE) {
             idx[a] = side ? 2 * n - 1 - idx[a] : -1 - idx[a];
@@ -100,7 +104,29 @@ int or_map_cell(const or_ctx *c, int idx[3], int *mir, int *fixed_row) {
             idx[a] = side ? n - 1 : 0;
         }
     }
+    if (halo >= 0) { *fixed_row = -3 - halo; return 2; }
     return *fixed_row == -1 ? 1 : 0;
+}
+
+/* cell of the caller's halo plane p (0, 1) at (i, j) */
+static size_t halo_cell(const or_ctx *c, int p, int i, int j) {
+    return ((size_t)p * c->c.nx[1] + j) * c->c.nx[0] + i;
+}
+
+void or_ghost_fluid(const or_ctx *c, int i, int j, int k, const double *ug_src, double *rho, double *ug,
+                    double *kap, double *cs, const double **ucon) {
+    int idx[3] = {i, j, k}, mir, row;
+    int r = or_map_cell(c, idx, &mir, &row);
+    if (r == 2) {
+        int side = -3 - row;
+        size_t h = halo_cell(c, idx[2], idx[0], idx[1]);
+        *rho = c->hrho[side][h]; *ug = c->hug[side][h]; *kap = c->hkap[side][h]; *cs = c->hcs[side][h];
+        *ucon = c->hucon[side] + 4 * h;
+        return;
+    }
+    int ci = or_cidx(c, idx[0], idx[1], idx[2]);
+    *rho = c->rho[ci]; *ug = ug_src[ci]; *kap = c->kap[ci]; *cs = c->cs[ci];
+    *ucon = c->ucon + 4 * (size_t)ci;
 }
 
 void or_fill_ghosts(const or_ctx *c, const double *I, double *Ig) {
@@ -111,6 +137,11 @@ void or_fill_ghosts(const or_ctx *c, const double *I, double *Ig) {
                 int idx[3] = {i, j, k}, mir, row;
                 int ok = or_map_cell(c, idx, &mir, &row);
                 double *dst = Ig + (size_t)or_gidx(c, i, j, k) * nd;
+                if (ok == 2) {
+                    const double *src = c->hI[-3 - row] + halo_cell(c, idx[2], idx[0], idx[1]) * nd;
+                    for (int s = 0; s < nd; ++s) dst[s] = src[s];
+                    continue;
+                }
                 if (!ok) {
                     for (int s = 0; s < nd; ++s)
                         dst[s] = (row >= c->c.beam_lo && row < c->c.beam_hi && s == c->c.beam_dir) ? c->c.beam_I : 0.0;
@@ -235,11 +266,11 @@ void or_transport_stage(or_ctx *c, const double *Isrc, const double *ug_src,
     for (int k = -c->ng[2]; k < c->c.nx[2] + c->ng[2]; ++k)
         for (int j = -c->ng[1]; j < c->c.nx[1] + c->ng[1]; ++j)
             for (int i = -c->ng[0]; i < c->c.nx[0] + c->ng[0]; ++i) {
-                int idx[3] = {i, j, k}, mir, row;
-                or_map_cell(c, idx, &mir, &row);
-                int ci = or_cidx(c, idx[0], idx[1], idx[2]), gi = or_gidx(c, i, j, k);
-                alg[gi] = or_cell_alpha(c, c->rho[ci], ug_src[ci], c->kap[ci], c->cs[ci]);
-                const double *u = c->ucon + 4 * (size_t)ci;
+                int gi = or_gidx(c, i, j, k);
+                double rho, ug, kap, cs;
+                const double *u;
+                or_ghost_fluid(c, i, j, k, ug_src, &rho, &ug, &kap, &cs, &u);
+                alg[gi] = or_cell_alpha(c, rho, ug, kap, cs);
                 for (int a = 0; a < 3; ++a) vg[3 * (size_t)gi + a] = u[a + 1] / u[0];
             }
     int stride[3] = {1, c->gn[0], c->gn[0] * c->gn[1]};

@@ -20,7 +20,7 @@ extern "C" {
 #endif
 
 /* boundary kinds per logical face */
-enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_POLE = 2, OR_BC_BEAM = 3 };
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_POLE = 2, OR_BC_BEAM = 3, OR_BC_HALO = 4 };
 /* coordinates */
 enum { OR_MINKOWSKI_CART = 0, OR_KERR_SCHILD = 1 };
 
@@ -72,8 +72,28 @@ int or_get_ug(const or_ctx *c, double *ug);
 int or_set_ug(or_ctx *c, const double *ug);
 
 double or_cfl_dt(const or_ctx *c, double cfl);
-/* nsteps full steps; returns the number of cells whose temperature root was not bracketed */
+/* nsteps full steps; returns the number of cells whose temperature root was
+   not bracketed (-1 for a context with x3 halos, which steps by stages) */
 long or_step(or_ctx *c, double dt, int nsteps);
+/* one stage of a step of size dt (section 3.6): stage 0 is the predictor
+   (order 2) or the single Euler stage (order 1), stage 1 the corrector; the
+   state takes the step's result after its last stage.  Returns the unconverged
+   temperature solves of the stage (-1 for a stage out of order). */
+long or_step_stage(or_ctx *c, double dt, int stage);
+
+/* x3 slab decomposition (section 8 of the design: spatial domain
+   decomposition).  With OR_BC_HALO on an x3 face the two ghost planes on
+   that side come from the caller: per side, 2 planes of nx0*nx1 cells, the
+   stage source's intensities [2*P*nd] followed by its gas energies [2*P]
+   (or_halo_doubles of them).  or_halo_pack writes the first two (lo) and last
+   two (hi) owned planes of the source of `stage`; or_halo_unpack takes the
+   neighbours' packs as this context's ghost planes for the next stage.
+   or_set_fluid_halo: the ghost planes' fluid, per side [2*P*7] as (rho, kappa,
+   alpha_s coefficient, u^0, u^1, u^2, u^3) per cell. */
+size_t or_halo_doubles(const or_ctx *c);
+int or_halo_pack(const or_ctx *c, int stage, double *lo, double *hi);
+int or_halo_unpack(or_ctx *c, const double *lo, const double *hi);
+int or_set_fluid_halo(or_ctx *c, const double *lo, const double *hi);
 /* one interaction step only (no transport) */
 long or_source_only(or_ctx *c, double dt);
 /* R[cell*10] coordinate R^{mu nu} (00,01,02,03,11,12,13,22,23,33), Ebar[cell],

@@ -26,6 +26,7 @@ import pytest
 
 import oracle
 from paper_2508_15532_b300 import workloads as W
+import angular_cases as AC
 
 ETA = np.diag([-1.0, 1, 1, 1])
 
@@ -132,6 +133,33 @@ def test_photon_orbit_direction():
     r1 = 2 * (1 + math.cos(2.0 / 3.0 * math.acos(-0.5)))
     assert photon_orbit_fate(0.5, 0.95 * r1) < 0
     assert photon_orbit_fate(0.5, 1.05 * r1) > 0
+
+
+def orbit_turn(f, mutant=0):
+    """Change of the mean coordinate radial speed <d ln r/dt> of a direction bump
+    started on the tangential photon at f r_1 (a = 0.5), minus the same change
+    at r_1 itself (which removes the part due to the bump's spreading)."""
+    r1 = AC.photon_orbit_radius(0.5)
+    out = []
+    for r in (f * r1, r1):
+        cfg, fl, dt, n, vr = AC.orbit_bump(r, mutant=mutant)
+        o = oracle.Oracle(cfg, mutant=mutant)
+        o.set_fluid(fl["rho"], fl["ug"], fl["ucon"], fl["kappa"], fl["alpha_s"], fl["eta"])
+        o.set_intensity(fl["I"])
+        o.step(dt, n)
+        w = o.grid()["w"]
+        out.append(AC.mean_vr(o.intensity(), w, vr) - AC.mean_vr(fl["I"], w, vr))
+    return out[0] - out[1]
+
+
+def test_photon_orbit_drift_direction():
+    """Section 4.7 as a directional pin of the oracle's angular drift: radiation
+    moving tangentially just inside the prograde circular photon orbit turns
+    inward (its mean radial speed falls), just outside it turns outward.
+    Measured: -4.4e-4 at 0.95 r_1, +4.9e-4 at 1.05 r_1 after t = 0.5; a drift of
+    the opposite sign gives +1.1e-3 and -8.6e-4."""
+    assert orbit_turn(0.95) < -2e-4
+    assert orbit_turn(1.05) > 2e-4
 
 
 # --------------------------------------------------------------- stationary fields
@@ -311,11 +339,12 @@ def failed_pins(mutant):
         "upwind": lambda: upwind_bump(mutant)[0] >= -1e-15,
         "beam": lambda: tangential_beam(mutant) < 0.15,
         "pole": lambda: pole_ghost_error(mutant) < 1e-13,
+        "orbit": lambda: orbit_turn(0.95, mutant) < -2e-4 and orbit_turn(1.05, mutant) > 2e-4,
     }
     return sorted(name for name, ok in checks.items() if not ok())
 
 
-@pytest.mark.parametrize("mutant,expect", [(1, "drift"), (2, "upwind"), (3, "pole"), (4, "pole"), (6, "drift")])
+@pytest.mark.parametrize("mutant,expect", [(1, "drift"), (1, "orbit"), (2, "upwind"), (3, "pole"), (4, "pole"), (6, "drift")])
 def test_planted_mistakes_are_caught(mutant, expect):
     """Mistakes planted in copies of the oracle (drift sign flipped; upwind side
     taken from the weighted speed n_0 v.u, i.e. downwind where n_0 < 0; pole
