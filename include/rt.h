@@ -28,6 +28,8 @@
 #ifndef RT_B300_H
 #define RT_B300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -39,7 +41,7 @@ typedef enum {
 
 typedef enum { RT_FP64 = 0, RT_FP32 = 1, RT_BF16 = 2 } rt_precision;
 typedef enum { RT_MINKOWSKI_CART = 0, RT_KERR_SCHILD = 1 } rt_metric_kind;
-typedef enum { RT_BC_PERIODIC = 0, RT_BC_OUTFLOW = 1, RT_BC_POLE = 2, RT_BC_BEAM = 3 } rt_bc;
+typedef enum { RT_BC_PERIODIC = 0, RT_BC_OUTFLOW = 1, RT_BC_POLE = 2, RT_BC_BEAM = 3, RT_BC_HALO = 4 } rt_bc;
 typedef enum { RT_LIM_MC = 0, RT_LIM_MINMOD = 1, RT_LIM_DONOR = 2 } rt_limiter;
 
 typedef struct rt_grid rt_grid;   /* opaque, library-owned */
@@ -143,6 +145,53 @@ rt_status rt_cfl_dt_noalloc(rt_ctx *c, double cfl, double *dt);
  * NULL) receives the number of unconverged temperature solves (then
  * RT_ENOCONV).  Asynchronous unless n_fail is non-NULL. */
 rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *n_fail);
+
+/* One stage of a step (section 3.6): stage 0 is the predictor (transport
+ * over dt/2 and the interaction over dt/2; for order 1 the single Euler
+ * stage), stage 1 the corrector; the stages of a step run in order, and the
+ * state takes the step's result after its last stage.  rt_step is the loop of
+ * these stages.  dt <= 0: the cfl bound with cfl 0.4.  *n_fail as for
+ * rt_step.  RT_ESTATE for a stage out of order.  This is how a context with
+ * x3 halo faces steps: before each stage its caller fills the ghost planes
+ * (rt_halo_pack / rt_halo_unpack). */
+rt_status rt_step_stage(rt_ctx *c, double dt, int stage, long long *n_fail);
+
+/* x3 slab decomposition (spatial domain decomposition of the box along x3;
+ * the paper plans the transfer between GPUs as further work, section 5.2).
+ * A context whose config has RT_BC_HALO on an x3 face owns a slab of a larger
+ * box: its nx[2] planes, x0[2] the slab's own origin.  The transport reads two
+ * cells on each side of a face (the piecewise-linear reconstruction of section
+ * 3.4), so before every stage the two planes beyond each halo face must hold
+ * the neighbouring slab's values of that stage's source: its intensities and
+ * the opacity of its flux stage (the interaction and the angular flux are
+ * cell-local).  Cells are x1-fastest, so a plane is contiguous.
+ * Limits: x3 faces only, nx[2] >= 2, no pole boundary on x2 (its ghost is the
+ * cell at phi + pi, on another slab) and no beam; rt_step, rt_step_record and
+ * rt_step_adjoint refuse such a context (RT_EINVAL).
+ *
+ * rt_halo_bytes: bytes of one side's halo block, 2 P n_dir S + 8 P for P =
+ * nx[0] nx[1] cells per plane and S bytes per stored intensity (0 without a
+ * halo face).
+ * rt_halo_pack: copies the halo blocks of the source of `stage` (which must be
+ * the next stage to run) into the caller's buffers lo and hi (host or device,
+ * rt_halo_bytes each): the intensities of the first two owned planes then
+ * the flux opacity of the first plane (lo), and those of the last two planes
+ * and of the last plane (hi).  Stream-ordered; a host buffer is complete
+ * after the stream synchronises.
+ * rt_halo_unpack: takes the neighbours' blocks as this context's ghost planes
+ * for `stage`: lo is the lower neighbour's hi block, hi the upper
+ * neighbour's lo block; a side that is the box's own boundary is ignored
+ * (may be NULL).  Stream-ordered.
+ * rt_set_fluid_halo: the fluid of the ghost planes, per halo side [2 P * 7]
+ * doubles (rho, kappa, alpha_s coefficient, u^0, u^1, u^2, u^3 per cell,
+ * lower side's plane -2 first, upper side's plane nx[2] first), of which the
+ * advective face term uses the velocity.  Needed (after every rt_set_fluid)
+ * unless the fluid is at rest in flat space; otherwise rt_step_stage returns
+ * RT_ESTATE. */
+rt_status rt_halo_bytes(const rt_ctx *c, size_t *bytes);
+rt_status rt_halo_pack(rt_ctx *c, int stage, void *lo, void *hi);
+rt_status rt_halo_unpack(rt_ctx *c, int stage, const void *lo, const void *hi);
+rt_status rt_set_fluid_halo(rt_ctx *c, const double *lo, const double *hi);
 
 /* Moments, eq. (R): R [n_cell*10] = coordinate R^{mu nu} (00,01,02,03,11,12,
  * 13,22,23,33) = sum_s n^mu n^nu I_s dOmega_s; Ebar [n_cell] comoving energy

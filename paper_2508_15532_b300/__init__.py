@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "librt_b300.so")
 
 RT_STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOCONV", 5: "RT_ESTATE",
              6: "RT_ETIMEOUT"}
-BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3}
+BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3, "halo": 4}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
 LIMITER = {"mc": 0, "minmod": 1, "donor": 2}
 ANG = {"mapr": 0, "donor": 1}
@@ -84,6 +84,11 @@ def lib():
         L.rt_step_adjoint.argtypes = [vp, vp, vp, d, i, vp, vp, vp, vp, vp, vp]
         L.rt_step_record.argtypes = [vp, d, i, C.POINTER(d), C.POINTER(C.c_longlong)]
         L.rt_step_adjoint_recorded.argtypes = [vp, C.c_longlong, vp, vp, vp, vp, vp, vp]
+        L.rt_step_stage.argtypes = [vp, d, i, C.POINTER(C.c_longlong)]
+        L.rt_halo_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.rt_halo_pack.argtypes = [vp, i, vp, vp]
+        L.rt_halo_unpack.argtypes = [vp, i, vp, vp]
+        L.rt_set_fluid_halo.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -251,6 +256,47 @@ class RadiationStep:
         ms, n = C.c_double(), C.c_longlong()
         self._check(lib().rt_get_timing(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    # ---- x3 slab of a decomposed box (RT_BC_HALO faces; see partition.py)
+    def step_stage(self, dt, stage, check=False):
+        """One stage of a step (rt_step_stage); the unconverged solves if check."""
+        nf = C.c_longlong()
+        self._check(lib().rt_step_stage(self.h, float(dt), int(stage), C.byref(nf) if check else None))
+        return nf.value if check else 0
+
+    def halo_bytes(self):
+        b = C.c_size_t()
+        self._check(lib().rt_halo_bytes(self.h, C.byref(b)))
+        return b.value
+
+    def _halo_bufs(self):
+        if getattr(self, "_hb", None) is None:
+            import torch
+            n = self.halo_bytes()
+            self._hb = [torch.empty(n, dtype=torch.uint8, device="cuda") for _ in range(4)]
+        return self._hb
+
+    def halo_pack(self, stage):
+        """(lo, hi) device byte tensors: the halo blocks of the source of
+        `stage` (rt_halo_pack); reused by the next call."""
+        b = self._halo_bufs()
+        self._check(lib().rt_halo_pack(self.h, int(stage), _ptr(b[0]), _ptr(b[1])))
+        self._pack_stage = int(stage)
+        return b[0], b[1]
+
+    def halo_recv_buffers(self):
+        b = self._halo_bufs()
+        return b[2], b[3]
+
+    def halo_unpack(self, lo, hi, stage=None):
+        stage = self._pack_stage if stage is None else stage
+        self._check(lib().rt_halo_unpack(self.h, int(stage), _ptr(lo), _ptr(hi)))
+
+    def set_fluid_halo(self, lo, hi):
+        """Fluid of the ghost planes, per side [2 nx0 nx1, 7] float64 (rho,
+        kappa, alpha_s coefficient, u^0..u^3)."""
+        self._keep_halo = (lo, hi)
+        self._check(lib().rt_set_fluid_halo(self.h, _ptr(lo), _ptr(hi)))
 
     def moments(self, R=None, Ebar=None, G=None):
         self._check(lib().rt_moments(self.h, _ptr(R), _ptr(Ebar), _ptr(G)))

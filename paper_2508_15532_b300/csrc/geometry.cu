@@ -321,11 +321,29 @@ __global__ void k_uhat(int ncell, int nx0, int nx1, int gn0, int ng0, int ng1, i
     for (int a = 0; a < 3; ++a) vel[3 * (size_t)cidx + a] = u[a + 1] / u[0];
 }
 
+// per cell sum_s w_s / D_s^2 (FP64), D_s = u-hat^0 - u-hat.n_s; the solid
+// angles are the stage kernels' (FP32-rounded for FP32 math)
+__global__ void k_wbar(int ncell, int nd, const double *__restrict__ uhat, const double *__restrict__ dir,
+                       const double *__restrict__ w, const float *__restrict__ wf, double *__restrict__ wbar) {
+    int cidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cidx >= ncell) return;
+    const double *u = uhat + 4 * (size_t)cidx;
+    double sum = 0.0;
+    for (int s = 0; s < nd; ++s) {
+        const double D = u[0] - (u[1] * dir[3 * s] + u[2] * dir[3 * s + 1] + u[3] * dir[3 * s + 2]);
+        sum += (wf ? (double)wf[s] : w[s]) / (D * D);
+    }
+    wbar[cidx] = sum;
+}
+
 rt_status rt_compute_uhat(rt_ctx *c) {
     int ng0 = c->active[0] ? 2 : 0, ng1 = c->active[1] ? 2 : 0;
     k_uhat<<<(c->ncell + 255) / 256, 256, 0, c->stream>>>(c->ncell, c->cfg.nx[0], c->cfg.nx[1], c->gn[0], ng0, ng1,
                                                          c->metric == RT_MINKOWSKI_CART, c->ucon, c->pt_ei, c->uhat,
                                                          c->vel);
+    RT_CUDA_TRY(c, cudaGetLastError());
+    k_wbar<<<(c->ncell + 127) / 128, 128, 0, c->stream>>>(c->ncell, c->nd, c->uhat, c->g->dir, c->g->w,
+                                                         c->cfg.precision == RT_FP64 ? nullptr : c->g->wf, c->wbar);
     RT_CUDA_TRY(c, cudaGetLastError());
     return RT_OK;
 }

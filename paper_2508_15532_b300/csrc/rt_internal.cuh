@@ -52,6 +52,14 @@ struct rt_ctx {
     size_t esize = 8;            // bytes per stored intensity
     std::string err;
 
+    // x3 slab of a decomposed box (RT_BC_HALO on an x3 face): the intensity
+    // arrays, the flux opacities and the coordinate velocity carry two ghost
+    // planes below and above the owned cells; the pointers below point at the
+    // owned cell 0 and the allocations start 2 planes earlier
+    bool halo = false;
+    bool halo_fluid = false;      // rt_set_fluid_halo called since rt_set_fluid
+    int next_stage = 0;           // rt_step_stage: the stage the step in progress expects
+    size_t hcells = 0;            // cells in two planes (2 nx0 nx1) when halo, else 0
     // intensity state: current, predictor, next (rotated after each step)
     void *I[3] = {nullptr, nullptr, nullptr};
     double *ug[3] = {nullptr, nullptr, nullptr};
@@ -60,6 +68,10 @@ struct rt_ctx {
     double *rho = nullptr, *kap = nullptr, *cs = nullptr, *eta = nullptr, *ucon = nullptr;
     double *vel = nullptr;       // [ncell*3] coordinate velocity u^a/u^0
     double *uhat = nullptr;      // [ncell*4] tetrad-frame fluid velocity
+    // [ncell] sum_s w_s / D_s^2 in FP64, D_s = u-hat^0 - u-hat.n_s, with the
+    // solid angles the context's stage kernels use (FP32-rounded for FP32 and
+    // BF16 storage): the leading part of the interaction's sum B2
+    double *wbar = nullptr;
     double *G = nullptr;         // [ncell*4]
     // the packed FP32 stage kernel leaves the force on the gas of its
     // interaction as per-cell (a, c) (I_+ = (I + c)/(1 + a)); rt_moments then
@@ -106,6 +118,12 @@ struct rt_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     size_t ev_used = 0;
 };
+
+// start of the allocation behind an array whose pointer sits hcells cells of
+// `per` bytes after it (x3 halo planes), for cudaFree
+inline void *rt_halo_base(const rt_ctx *c, void *p, size_t per) {
+    return p ? (void *)((char *)p - c->hcells * per) : nullptr;
+}
 
 #define RT_CUDA_TRY(c, call)                                                          \
     do {                                                                              \

@@ -424,7 +424,11 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             on = A.source && A.cc_on[cidx] && am > 0.0 && Tm > 0.0;
             const int pc = FLAT ? 0 : (j + A.ng1) * A.gn0 + (i0 + ii + A.ng0);
             double n0 = FLAT ? 1.0 : A.pt_n0[pc];
-            for (int m = 0; m < 4; ++m) scU[4 * s + m] = (TM)A.uhat[4 * cidx + m];
+            // u-hat^0 is kept as u-hat^0 - 1 (exact in FP64 for u^0 in [1, 2]):
+            // D = 1 + ((u^0 - 1) - u.n) then carries no FP32 rounding of u^0,
+            // which would shift every direction's D the same way
+            scU[4 * s] = (TM)(A.uhat[4 * cidx] - 1.0);
+            for (int m = 1; m < 4; ++m) scU[4 * s + m] = (TM)A.uhat[4 * cidx + m];
             scN0[s] = (TM)n0;
             scK[s] = (TM)(am * A.dtk);
             if (on && !(A.uhat[4 * cidx + 1] == 0.0 && A.uhat[4 * cidx + 2] == 0.0 && A.uhat[4 * cidx + 3] == 0.0 &&
@@ -454,19 +458,32 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             }
         };
         if ((c % TXC) < nc && scOn[c]) {
-            const TM u0 = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
-            const TM n0 = scN0[c], adt = scK[c];
+            const TM u0m = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
+            const TM n0 = scN0[c], adt = scK[c], kn = dv<TM>(adt, n0);
             const TM *row = It + c * ndp;
             for (int d = g; d < nd; d += nchunk) {
                 TM w = ldT<TM>(A.wT, d);
                 TM t;
                 if (all_static) t = row[d] * w;
                 else {
-                    TM D = u0 - (u1 * ldT<TM>(A.dirT, 3 * d) + u2 * ldT<TM>(A.dirT, 3 * d + 1) + u3 * ldT<TM>(A.dirT, 3 * d + 2));
+                    TM D = TM(1) + (u0m - (u1 * ldT<TM>(A.dirT, 3 * d) + u2 * ldT<TM>(A.dirT, 3 * d + 1) +
+                                           u3 * ldT<TM>(A.dirT, 3 * d + 2)));
                     t = D * D * row[d] * w;
-                    TM K = dv<TM>(adt, n0 + D * adt);
-                    kadd(B1, cB1, n0 * K * t);
-                    kadd(B2, cB2, dv<TM>(K * w, D));
+                    if constexpr (sizeof(TM) == 4) {
+                        // rq = n^0 / (n^0 + D alpha dt), K = (alpha dt / n^0) rq; the
+                        // sum gathers the small remainder w-bar rq of
+                        // B2 = dt/(4 pi) (sum w-bar - sum w-bar rq) (w-bar = w / D^2),
+                        // whose leading sum is per-cell FP64 (wbar): B2 then
+                        // carries no FP32 rounding that the solve's cancellation
+                        // alpha dt - B2 alpha^s would magnify
+                        const TM iD = dv<TM>(TM(1), D), rq = dv<TM>(n0, n0 + D * adt);
+                        kadd(B1, cB1, n0 * (kn * rq) * t);
+                        kadd(B2, cB2, w * iD * iD * rq);
+                    } else {
+                        TM K = dv<TM>(adt, n0 + D * adt);
+                        kadd(B1, cB1, n0 * K * t);
+                        kadd(B2, cB2, dv<TM>(K * w, D));
+                    }
                 }
                 TM yk = t - cEm, tk = Em + yk;
                 cEm = (tk - Em) - yk; Em = tk;
@@ -496,6 +513,8 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 double K = adt / (1.0 + adt);
                 B1 = K * Em;
                 B2 = K * (sizeof(TM) == 4 ? A.sumwf : A.sumw);
+            } else if (sizeof(TM) == 4) {
+                B2 = A.wbar[cidx] - B2;
             }
             B2 *= dt / qw;
             const double Y = A.cc_Y[cidx], ug = A.ug_in[cidx], Tm = ug / Y;
@@ -536,7 +555,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             if (scOn[lc]) {
                 if (all_static) v = (v + scEm[lc]) / (TM(1) + scA[lc]);
                 else {
-                    TM D = scU[4 * lc] - (scU[4 * lc + 1] * nh[0] + scU[4 * lc + 2] * nh[1] + scU[4 * lc + 3] * nh[2]);
+                    TM D = TM(1) + (scU[4 * lc] - (scU[4 * lc + 1] * nh[0] + scU[4 * lc + 2] * nh[1] + scU[4 * lc + 3] * nh[2]));
                     TM n0 = scN0[lc];
                     v = dv<TM>(n0 * v + dv<TM>(scEm[lc], D * D * D), n0 + D * scA[lc]);
                 }
@@ -553,12 +572,12 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
         const int c = s & 31, g = s >> 5;
         TM Ep = 0, cEp = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
         if ((c % TXC) < nc && scOn[c]) {
-            const TM u0 = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
+            const TM u0m = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
             const TM *rp = Ip + c * ndp, *rt = It + c * ndp;
             for (int d = g; d < nd; d += nchunk) {
                 TM w = ldT<TM>(A.wT, d);
                 TM x = ldT<TM>(A.dirT, 3 * d), y = ldT<TM>(A.dirT, 3 * d + 1), z = ldT<TM>(A.dirT, 3 * d + 2);
-                TM D = all_static ? TM(1) : u0 - (u1 * x + u2 * y + u3 * z);
+                TM D = all_static ? TM(1) : TM(1) + (u0m - (u1 * x + u2 * y + u3 * z));
                 TM t = D * D * rp[d] * w;
                 TM yk = t - cEp, tk = Ep + yk;
                 cEp = (tk - Ep) - yk; Ep = tk;
@@ -689,7 +708,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.Isrc = Isrc; A.Ibase = Ibase; A.Iout = Iout; A.ug_in = ug_in; A.ug_out = ug_out;
     A.alpha_in = alpha_in; A.alpha_int = alpha_int; A.alpha_out = alpha_out;
     A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y; A.cc_on = c->cc_on;
-    A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.G = G; A.gac = c->gac; A.fail = c->fail;
+    A.eta = c->eta; A.vel = c->vel; A.uhat = c->uhat; A.wbar = c->wbar; A.G = G; A.gac = c->gac; A.fail = c->fail;
     if (G) c->g_lazy = false;   // set again below if the packed kernel defers G
     A.sv_Em = c->sv_Em; A.sv_X = c->sv_X;
     A.mirror = g->mirror; A.nnb = g->nnb; A.nbr = g->nbr; A.ring_edge = g->ring_edge; A.ring_back = g->ring_back;
@@ -712,6 +731,13 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
         A.mask = c->mask; A.pt_V = c->pt_V; A.pt_n0 = c->pt_n0; A.pt_len = c->pt_len; A.pt_e = c->pt_e;
     }
     for (int m = 0; m < 3; ++m) A.sumnw[m] = c->sumnw[m];
+    if (c->halo) {
+        // neighbour-read arrays from the first ghost plane (see StageArgs::kb)
+        A.kb = 2;
+        A.Isrc = (const char *)Isrc - c->hcells * c->nd * c->esize;
+        A.alpha_in = alpha_in - c->hcells;
+        A.vel = c->vel - 3 * c->hcells;
+    }
     int NT = ((c->nd + 31) / 32) * 32;
     if (NT < 64) NT = 64;
     if (NT > MAXNT) { c->err = "more than 256 directions per cell are not supported by the stage kernel"; return RT_EINVAL; }

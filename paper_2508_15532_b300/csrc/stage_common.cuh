@@ -21,6 +21,12 @@ struct StageArgs {
     double gam, arad, T_exp, abar, sumw, sumwf;
     double sumnw[3];           // sum of n-hat_s dOmega_s (0 to rounding)
     int tau_dt, limiter, ang_recon, transport, source;
+    // x3 slab (RT_BC_HALO): the row descriptors of the general and the flat
+    // kernel count cells from plane -kb (the first ghost plane), and Isrc,
+    // alpha_in and vel point there, so that descriptors stay non-negative;
+    // the packed kernel takes kb = 0 with pointers at the owned origin and
+    // signed offsets
+    int kb;
     double dtk;
     const void *Isrc; const void *Ibase; void *Iout;
     const double *ug_in; double *ug_out;
@@ -28,6 +34,7 @@ struct StageArgs {
     const double *alpha_int;   // opacity at the interaction's initial gas state
     double *alpha_out;         // opacity after the interaction
     const double *cc_au, *cc_as, *cc_Y, *eta, *vel, *uhat;
+    const double *wbar;        // per cell sum_s w_s / D_s^2 in FP64 (the FP32 paths' solid angles)
     const uint8_t *cc_on;
     double *G;
     float2 *gac;               // packed FP32 path: per-cell (a, c) of the interaction, for a deferred G
@@ -93,6 +100,7 @@ __device__ inline int map_axis(const StageArgs &A, int ax, int q, int *flags, in
     int n = ax == 0 ? A.nx0 : (ax == 1 ? A.nx1 : A.nx2);
     if (q >= 0 && q < n) return q;
     int side = q < 0 ? 0 : 1, bc = A.bc[ax][side];
+    if (bc == RT_BC_HALO) return q;     // the caller's ghost planes (x3 only)
     if (bc == RT_BC_PERIODIC) return (q + n) % n;
     if (bc == RT_BC_POLE) {
         *flags ^= F_MIR;
@@ -109,7 +117,7 @@ __device__ inline int row_desc(const StageArgs &A, int j, int k) {
     int jm = map_axis(A, 1, j, &fl, &ks);
     int km = map_axis(A, 2, k, &fl, nullptr);
     if (ks) km = (km + ks) % A.nx2;
-    return ((km * A.nx1 + jm) * A.nx0) | fl;
+    return (((km + A.kb) * A.nx1 + jm) * A.nx0) | fl;
 }
 
 // ------------------------------------------------------------ temperature

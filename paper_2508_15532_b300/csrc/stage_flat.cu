@@ -196,6 +196,9 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
 #pragma unroll
             for (int r = 0; r < BZ + 4; ++r) oz[q][r] = roff(rowZ[q * (BZ + 4) + r]);
         const bool same_base = A.Isrc == A.Ibase;
+        // own-row offsets count from the first ghost plane of an x3 slab
+        // (StageArgs::kb); the base array starts at the owned origin
+        const int kbo = A.kb * A.nx1 * A.nx0 * nd;
         if (A.transport) {
             TM W0[NOWN], W1[NOWN], S0[NOWN], Flo[NOWN];
 #pragma unroll
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
 #pragma unroll
                     for (int o = 0; o < NOWN; ++o) {
                         TM Ib = same_base ? Ic[o]
-                                          : IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + i * nd));
+                                          : IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] - kbo + i * nd));
                         putIt(o * TXC + ii, Ib - acc[o]);
                     }
                 }
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(FS_NT, MinBlocks<TM>::v) k_stage_fs(const Stag
             for (int o = 0; o < NOWN; ++o)
 #pragma unroll
                 for (int ii = 0; ii < TXC; ++ii)
-                    if (ii < nc) putIt(o * TXC + ii, IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] + (i0 + ii) * nd)));
+                    if (ii < nc) putIt(o * TXC + ii, IO<TS, TM>::ld(A.Ibase, (size_t)(oy[o / BY][o % BY + 2] - kbo + (i0 + ii) * nd)));
         }
     }
 
@@ -429,9 +432,11 @@ template <int ND> struct Fp2Shape {
 };
 
 // cell index along one periodic or outflow axis for any q (set-up only)
+// (RT_BC_HALO: the caller's ghost planes, addressed by signed offsets from the
+// owned origin)
 __device__ __forceinline__ int wrap_po(int q, int n, int bclo, int bchi) {
-    if (q < 0) return bclo == RT_BC_PERIODIC ? ((q % n) + n) % n : 0;
-    if (q >= n) return bchi == RT_BC_PERIODIC ? q % n : n - 1;
+    if (q < 0) return bclo == RT_BC_PERIODIC ? ((q % n) + n) % n : (bclo == RT_BC_HALO ? q : 0);
+    if (q >= n) return bchi == RT_BC_PERIODIC ? q % n : (bchi == RT_BC_HALO ? q : n - 1);
     return q;
 }
 
@@ -461,8 +466,10 @@ __global__ void __launch_bounds__(Fp2Shape<ND>::NT, Fp2Shape<ND>::MINB) k_stage_
     // the base intensities (both first reads from HBM), copied asynchronously
     constexpr bool PFX = sizeof(TS) == 4;
     // unrolling of the x1 loop; measured at 128^3 x 162: FP32 storage runs
-    // 13% faster unrolled by 4 than fully, BF16 storage 10% slower
-    constexpr int XUNROLL = PFX ? 4 : TXC;
+    // 13% faster unrolled by 4 than fully and 5% faster again rolled (its
+    // instruction-fetch stalls fall with the code size), BF16 storage 10%
+    // slower unrolled by 4 than fully
+    constexpr int XUNROLL = PFX ? 1 : TXC;
     __shared__ __align__(8) float pfb[2][2 * NOWN][PFX ? 2 * NT : 2];
 
     const int p = threadIdx.x, lane = p & 31, warp = p >> 5;
@@ -778,15 +785,24 @@ __global__ void __launch_bounds__(Fp2Shape<ND>::NT, Fp2Shape<ND>::MINB) k_stage_
 }
 
 template <typename TS, typename TM, int BY, int BZ>
-rt_status launch_fs(rt_ctx *c, const StageArgs &A, int NT) {
+rt_status launch_fs(rt_ctx *c, const StageArgs &A0, int NT) {
+    const StageArgs &A = A0;
     constexpr int TXC = NCELL / (BY * BZ);
     size_t nblk = (size_t)((A.nx0 + TXC - 1) / TXC) * (A.nx1 / BY) * (A.nx2 / BZ);
     bool simple = true;
     for (int a = 0; a < 3; ++a)
-        for (int sd = 0; sd < 2; ++sd) simple = simple && (A.bc[a][sd] == RT_BC_PERIODIC || A.bc[a][sd] == RT_BC_OUTFLOW);
+        for (int sd = 0; sd < 2; ++sd)
+            simple = simple && (A.bc[a][sd] == RT_BC_PERIODIC || A.bc[a][sd] == RT_BC_OUTFLOW || A.bc[a][sd] == RT_BC_HALO);
     if constexpr (sizeof(TM) == 4) {
         if (simple && A.nd == 162) {
             constexpr int ND = 162, PNT = Fp2Shape<ND>::NT;
+            StageArgs A = A0;
+            if (A.kb) {     // signed offsets from the owned origin (see StageArgs::kb)
+                A.Isrc = (const char *)A.Isrc + c->hcells * c->nd * c->esize;
+                A.alpha_in += c->hcells;
+                A.vel += 3 * c->hcells;
+                A.kb = 0;
+            }
             const bool sb = A.Isrc == A.Ibase;
             auto kern = A.G ? (sb ? k_stage_fp2<TS, ND, BY, BZ, true, true> : k_stage_fp2<TS, ND, BY, BZ, true, false>)
                             : (sb ? k_stage_fp2<TS, ND, BY, BZ, false, true> : k_stage_fp2<TS, ND, BY, BZ, false, false>);
@@ -819,7 +835,7 @@ rt_status launch_fs_blk(rt_ctx *c, const StageArgs &A, int NT) {
 
 bool rt_stage_fast_ok(const rt_ctx *c) {
     return c->metric == RT_MINKOWSKI_CART && c->static_fluid && c->cfg.limiter == RT_LIM_MC &&
-           c->cfg.n_pole_zero == 0 && c->nd <= FS_NT && (double)c->ncell * c->nd < 2147483647.0;
+           c->cfg.n_pole_zero == 0 && c->nd <= FS_NT && (double)(c->ncell + 2 * c->hcells) * c->nd < 2147483647.0;
 }
 
 rt_status rt_launch_stage_fs(rt_ctx *c, const StageArgs &A, int NT) {
