@@ -40,6 +40,10 @@ struct LaneF {
     __device__ static V ld(const float *p) { float2 v = __ldg(reinterpret_cast<const float2 *>(p)); return F2{v.x, v.y}; }
     __device__ static void st(float *p, V v) { *reinterpret_cast<float2 *>(p) = make_float2(v.x, v.y); }
     __device__ static void st64(double *p, V v) { *reinterpret_cast<double2 *>(p) = make_double2(v.x, v.y); }
+    __device__ static V ld64(const double *p) {
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        return F2{(float)v.x, (float)v.y};
+    }
     __device__ static float hsum(V v) { return v.x + v.y; }
     __device__ static V vabs(V v) { return F2{fabsf(v.x), fabsf(v.y)}; }
     __device__ static V dirv(const double *dir, int d, int a) { return F2{(float)dir[3 * d + a], (float)dir[3 * d + 3 + a]}; }
@@ -54,6 +58,7 @@ struct LaneD {
     __device__ static V ld(const double *p) { return __ldg(p); }
     __device__ static void st(double *p, V v) { *p = v; }
     __device__ static void st64(double *p, V v) { *p = v; }
+    __device__ static V ld64(const double *p) { return __ldg(p); }
     __device__ static double hsum(V v) { return v; }
     __device__ static V vabs(V v) { return fabs(v); }
     __device__ static V dirv(const double *dir, int d, int a) { return dir[3 * d + a]; }
@@ -224,21 +229,14 @@ __device__ __forceinline__ typename LT::V face_tau(typename LT::V phib, typename
 
 // Per-cell FP64 arithmetic without FP64 divisions or square roots, which are
 // long instruction sequences on this part's FP64 pipe (1/64 of the FP32 rate):
-// an FP32 estimate refined by two FP64 Newton steps (relative error at the
-// FP64 rounding level), with the exact operation outside the FP32 range.
-__device__ __forceinline__ double rcp_nr(double x) {
-    const double ax = fabs(x);
-    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-    double y = (double)__frcp_rn((float)x);
-    y = fma(y, fma(-x, y, 1.0), y);
-    return fma(y, fma(-x, y, 1.0), y);
-}
+// an FP32 estimate refined by one FP64 Newton step (Newton's method squares
+// the relative error: ~1e-14 from the FP32 estimates' ~1e-7), with the exact
+// operation outside the FP32 range (tested on the exponent bits).
+__device__ __forceinline__ double rcp_nr(double x) { return rcp64(x); }
 __device__ __forceinline__ double rsqrt_nr(double x) {   // x > 0
-    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-    double y = (double)rsqrtf((float)x);
-    const double h = 0.5 * x;
-    y = y * fma(-h * y, y, 1.5);
-    return y * fma(-h * y, y, 1.5);
+    if (!in_fp32_range(x)) return 1.0 / sqrt(x);
+    const double y = (double)rsqrtf((float)x);
+    return y * fma(-0.5 * x * y, y, 1.5);
 }
 // T^-p and 1/T (T > 0); for p = 3.5 both from r = T^-1/2: T^-3.5 = r^7, 1/T = r^2
 __device__ __forceinline__ void tpow_inv(double T, double p, double &tp, double &iT) {
@@ -265,15 +263,16 @@ __device__ __forceinline__ double rho_m(double au, double kap, double rho, doubl
 // Given P = sum Ibo, Q = sum Ibo I_+ (Ibo: cotangent of I_+) and ub (cotangent
 // of u_g+), the cotangent of I_* in direction s is (Ibo_s - ub w_s) inv + Emb w_s.
 struct SrcRev { double inv, ub, Emb, ugb, kb, eb; };
-__device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, double eta, double kap, double rho,
-                          double Em, double X, double P, double Q, double ub, double dt, double S, double p,
-                          double ar, double rho_exp) {
+// iY = 1/Y, (tm, iTm) = (T_-^-p, 1/T_-) and rhom = rho^m come from the caller,
+// which needs them for the opacity chain too.
+__device__ SrcRev src_rev(bool on, double iY, double ugm, double au, double as, double eta, double tm, double iTm,
+                          double rhom, double Em, double X, double P, double Q, double ub, double dt, double S,
+                          double p, double ar) {
     SrcRev o{1.0, 0.0, 0.0, ub, 0.0, 0.0};
     if (!on) return o;
     constexpr double i4pi = 1.0 / FOURPI;
-    const double iY = rcp_nr(Y), Tm = ugm * iY;
-    double tm, iTm, tp, iTp;
-    tpow_inv(Tm, p, tm, iTm);
+    const double Tm = ugm * iY;
+    double tp, iTp;
     const double am = au * tm + as;
     const double adt = am * dt, i1a = rcp_nr(1.0 + adt), K = adt * i1a, B2 = K * S * dt * i4pi;
     const double Tp = Tm + (Em - X) * iY;
@@ -315,7 +314,7 @@ __device__ SrcRev src_rev(bool on, double Y, double ugm, double au, double as, d
     Tmb += amb * (-p) * au * tm * iTm;
     o.inv = inv; o.ub = ub; o.Emb = Emb;
     o.ugb = ub + Tmb * iY;
-    o.kb = aub * rho_m(au, kap, rho, rho_exp);
+    o.kb = aub * rhom;
     o.eb = etab;
     return o;
 }
@@ -365,6 +364,8 @@ struct RevArgs {
     int nx[3], act[3], per[3], nd, limiter, transport, source;
     int add_base;                 // the stage's base intensities are its input
     int out_f64;                  // !FUSE: Zout is FP64 whatever the storage type
+    int zg_f64;                   // Zg is FP64 whatever the storage type (read at own elements only:
+                                  // the transport-free launch takes the caller's cotangent as it is)
     int ub_dst_acc;               // FUSE: add to ub_dst instead of writing it
     double coef[3];               // dtk / dx_a
     double hl[3];                 // d tau / d alpha of one side of an a-face: abar len_a / 2
@@ -603,7 +604,8 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         } else {
 #pragma unroll
             for (int o = 0; o < NOWN; ++o) {
-                Ic[o] = ldI(own(o) + ie); Zc[o] = ldZ(own(o) + ie);
+                Ic[o] = ldI(own(o) + ie);
+                Zc[o] = A.zg_f64 ? LT::ld64((const double *)A.Zg + own(o) + ie) : ldZ(own(o) + ie);
                 acc[o] = zero; ab[o] = zero;
             }
         }
@@ -718,14 +720,16 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
             double abar = 0.0;
             for (int g = 0; g < NW; ++g) abar += (double)part[g][o][ii];
             const double Y = A.cc_Y[c], au = A.cc_au[c];
-            double t = A.ubA ? A.ubA[c] : 0.0, kbv = 0.0;
+            const double iY = Y > 0.0 ? rcp_nr(Y) : 0.0;
+            double t = A.ubA ? A.ubA[c] : 0.0, kbv = 0.0, rhom = -1.0;   // rho^m, formed on first use
             // alpha = kappa rho^m T^-p + alpha^s with T = u_g / Y
             if (A.transport && A.cc_on[c] && abar != 0.0) {
-                const double iY = Y > 0.0 ? rcp_nr(Y) : 0.0, Ta = A.ug_a[c] * iY;
+                const double Ta = A.ug_a[c] * iY;
                 if (Ta > 0.0) {
                     double tp, iTa;
                     tpow_inv(Ta, A.T_exp, tp, iTa);
-                    kbv = abar * rho_m(au, A.kap[c], A.rho[c], A.rho_exp) * tp;
+                    rhom = rho_m(au, A.kap[c], A.rho[c], A.rho_exp);
+                    kbv = abar * rhom * tp;
                     t += abar * au * (-A.T_exp) * tp * iTa * iY;
                 }
             }
@@ -734,15 +738,16 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
                 A.kb[c] += kbv;
             } else {
                 const double ugm = A.ugm[c], as = A.cc_as[c];
-                const double Tm = Y > 0.0 ? ugm * rcp_nr(Y) : 0.0;
+                const double Tm = ugm * iY;
                 double tmv = 0.0, iTmv = 0.0;
                 if (Tm > 0.0) tpow_inv(Tm, A.T_exp, tmv, iTmv);
                 const double am = (A.cc_on[c] && Tm > 0.0) ? au * tmv + as : 0.0;
                 const bool on = A.source && A.cc_on[c] && am > 0.0 && Y > 0.0 && ugm > 0.0;
+                if (on && rhom < 0.0) rhom = rho_m(au, A.kap[c], A.rho[c], A.rho_exp);
                 double P = 0.0, Q = 0.0;
                 for (int g = 0; g < NW; ++g) { P += (double)partP[g][lc]; Q += (double)part[g][NOWN + o][ii]; }
-                const SrcRev r = src_rev(on, Y, ugm, au, as, A.eta[c], A.kap[c], A.rho[c], on ? A.Em[c] : 0.0,
-                                         on ? A.X[c] : 0.0, P, Q, t, A.dts, A.sumw, A.T_exp, A.arad, A.rho_exp);
+                const SrcRev r = src_rev(on, iY, ugm, au, as, A.eta[c], tmv, iTmv, rhom, on ? A.Em[c] : 0.0,
+                                         on ? A.X[c] : 0.0, P, Q, t, A.dts, A.sumw, A.T_exp, A.arad);
                 A.ub_dst[c] = (A.ub_dst_acc ? A.ub_dst[c] : 0.0) + r.ugb;
                 A.kb[c] += kbv + r.kb;
                 A.eb[c] += r.eb;
@@ -929,7 +934,6 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
                              const double *dL_dug_out, double *dL_dI_in, double *dL_dug_in, double *dL_dkappa,
                              double *dL_deta) {
     const rt_config &f = c->cfg;
-    const size_t ni = (size_t)c->ncell * c->nd;
     const int order = f.order, ns = order == 2 ? 2 : 1, N = ar.N;
     const auto &In = ar.In, &Bs = ar.Bs;
     const auto &un = ar.un, &us = ar.us, &aln = ar.aln, &als = ar.als, &sE = ar.sE, &sX = ar.sX;
@@ -956,16 +960,11 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
         return A;
     };
     const bool f64 = f.precision == RT_FP64;
-    const void *Zin = dL_dI_out;
-    if (!f64) {
-        k_cvt<double, float><<<(unsigned)((ni + 255) / 256), 256, 0, c->stream>>>(dL_dI_out, (float *)Z[1], ni);
-        RT_CUDA_TRY(c, cudaGetLastError());
-        Zin = Z[1];
-    }
-    {   // the interaction that ends the last step, alone
+    {   // the interaction that ends the last step, alone (reading the caller's
+        // FP64 cotangent directly in both passes)
         RevArgs A = B;
         A.transport = 0; A.add_base = 1;
-        A.I = In[N]; A.Zg = Zin; A.ubA = dL_dug_out;
+        A.I = In[N]; A.Zg = dL_dI_out; A.zg_f64 = f64 ? 0 : 1; A.ubA = dL_dug_out;
         A.dts = dt; A.ugm = un[N - 1]; A.Em = sE[N * ns - 1]; A.X = sX[N * ns - 1];
         A.ub_dst = ubc; A.ub_dst_acc = 0; A.Zout = Z[0];
         if ((st = launch_rev(c, A, true)) != RT_OK) return st;

@@ -190,18 +190,25 @@ template <typename R> __device__ bool newton_E(const Teq<R> &q, R X, R &lo, R &h
 // pipe): an FP32 reciprocal refined by two Newton-Raphson steps
 // y <- y + y (1 - x y), each of which squares the relative error (1e-7 ->
 // 1e-14 -> rounding level); the exact division outside the FP32 range
+// |x| within [2^-99, 2^99) (nonzero, finite, well inside the FP32 range),
+// tested on the exponent bits with integer instructions: a comparison in
+// FP64 would occupy this part's slow FP64 pipe
+__device__ __forceinline__ bool in_fp32_range(double x) {
+    const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    return e - (1023u - 99u) < 198u;
+}
+// 1/x from the correctly rounded FP32 reciprocal (relative error <= 2^-24)
+// and one FP64 Newton step, which squares that error (~4e-15)
 __device__ __forceinline__ double rcp64(double x) {
-    const double ax = fabs(x);
-    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-    double y = (double)__frcp_rn((float)x);
-    y = fma(y, fma(-x, y, 1.0), y);
+    if (!in_fp32_range(x)) return 1.0 / x;
+    const double y = (double)__frcp_rn((float)x);
     return fma(y, fma(-x, y, 1.0), y);
 }
 
 // T^-p in FP64 for the mixed path: for p = 3.5 an FP32 reciprocal square
 // root refined by one FP64 Newton step for 1/sqrt (relative error ~1e-14)
 __device__ __forceinline__ double tneg_mixed(double T, double p) {
-    if (p == 3.5 && T > 1e-30 && T < 1e30) {
+    if (p == 3.5 && T > 0.0 && in_fp32_range(T)) {
         double y = (double)rsqrtf((float)T);
         y = y * (1.5 - 0.5 * T * y * y);
         double y2 = y * y;

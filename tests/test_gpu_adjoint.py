@@ -280,3 +280,4 @@ def test_recorded_reverse_matches_checkpoint_reverse(precision, order):
         a.step_adjoint_recorded(rid, dI, du, torch.empty_like(dI), torch.empty_like(du),
                                 torch.zeros_like(du), torch.zeros_like(du))
     assert e.value.status == 5     # RT_ESTATE
+
