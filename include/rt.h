@@ -72,6 +72,15 @@ typedef struct {
     int source;         /* 0 disables the radiation-gas interaction */
     double n0_cut;      /* intensities zeroed where |n_0| < n0_cut (section 3.5) */
     int precision;      /* rt_precision of the stored intensities */
+    int coupling;       /* temperature solve of section 3.5.2: 3 (or 0) the
+                           semi-implicit method 3 (eq. T_almost_fully_implicit);
+                           1 and 2 the explicit-opacity methods (eqs.
+                           semi_implicit_T, implicit_T), whose A1, A2 and total
+                           absorption use T_-, with the Planck absorption of the
+                           emission at T_- (1) or T_+ (2).  Methods 1 and 2 run
+                           on the general stage kernel and have no reverse mode;
+                           a cell whose equation has no positive temperature is
+                           left unchanged and counted as unconverged. */
 } rt_config;
 
 /* Geodesic angular grid, section 3.3: icosahedron, log2(n) edge bisections

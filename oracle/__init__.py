@@ -26,6 +26,7 @@ class _Cfg(C.Structure):
         ("rho_exp", C.c_double), ("T_exp", C.c_double), ("rho_floor", C.c_double),
         ("abar", C.c_double), ("tau_dt", C.c_int), ("order", C.c_int), ("limiter", C.c_int),
         ("ang_recon", C.c_int), ("transport", C.c_int), ("source", C.c_int), ("n0_cut", C.c_double),
+        ("coupling", C.c_int),
     ]
 
 
@@ -95,6 +96,7 @@ def make_cfg(cfg: dict) -> _Cfg:
     c.limiter = LIMITER[cfg.get("limiter", "mc")]; c.ang_recon = ANG[cfg.get("ang_recon", "mapr")]
     c.transport = int(bool(cfg.get("transport", True))); c.source = int(bool(cfg.get("source", True)))
     c.n0_cut = float(cfg.get("n0_cut", 0.1))
+    c.coupling = int(cfg.get("coupling", 3))
     return c
 
 

@@ -392,6 +392,38 @@ static int solve_E(const teq *q, double *X) {
     return 1;
 }
 
+/* Methods 1 and 2 of section 3.5.2 (eqs. semi_implicit_T and implicit_T):
+   the angular sums A1, A2 (eqs. A1, A2) with the explicit alpha_-, and
+   eq. energy_integral, E-bar_+ = A1 + A2 (alpha^a_P a T_+^4 + alpha^s E-bar_+),
+   with the Planck absorption alpha^a_P at T_- (method 1) or at T_+ (method 2)
+   and the emission multiplier eta.  Solved, like method 3, for
+   X = E-bar_+ with T_+ = T_- + (E-bar_- - X)/Y (eq. ideal_gas_difference):
+     h(X) = (1 - A2 alpha^s) X - A1 - A2 eta alpha^a_P a T(X)^4 = 0,
+   the paper's quartic (method 1) and its T^(4-p) form (method 2) rewritten
+   for X.  h increases strictly on [0, W), h(0) < 0, and h(W) = (1 - A2 alpha^s)
+   W - A1, which need not be positive: then no positive temperature solves the
+   equations (the instability the paper reports for these methods). */
+typedef struct { double A1, A2, W, Y, Tm, Em, au, as, eta, arad, p; int method; } meq;
+static double meq_T(const meq *q, double X) { return q->Tm + (q->Em - X) / q->Y; }
+static double meq_aaP(const meq *q, double T) { return q->au * pow(q->method == 1 ? q->Tm : T, -q->p); }
+static double meq_h(const meq *q, double X) {
+    double T = meq_T(q, X);
+    if (!(T >= 0.0)) return INFINITY;
+    return (1.0 - q->A2 * q->as) * X - q->A1 - q->A2 * q->eta * meq_aaP(q, T) * q->arad * T * T * T * T;
+}
+/* root by bisection to adjacent doubles; 0 if there is none in [0, W) */
+static int solve_meq(const meq *q, double *X) {
+    double lo = 0.0, hi = q->W;
+    if (!((1.0 - q->A2 * q->as) * q->W - q->A1 > 0.0)) return 0;
+    for (int n = 0; n < 2000; ++n) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (meq_h(q, mid) > 0.0) hi = mid; else lo = mid;
+    }
+    *X = fabs(meq_h(q, lo)) <= fabs(meq_h(q, hi)) ? lo : hi;
+    return 1;
+}
+
 /* the implicit interaction of section 3.5.2 for every cell:
    boost to the fluid frame (I-bar = D^4 I-hat, dOmega-bar = dOmega-hat / D^2,
    D = nbar^0 = u^0 - u.n in the tetrad frame), the angular sums of eqs.
@@ -425,7 +457,7 @@ long or_source_step(or_ctx *c, double *I, const double *ug_in, double *ug_out, d
                 const double *u = c->ucon + 4 * (size_t)ci;
                 double uh[4];
                 for (int a = 0; a < 4; ++a) { double s = 0.0; for (int m = 0; m < 4; ++m) s += g->ei[a][m] * u[m]; uh[a] = s; }
-                double Em = 0.0, B1 = 0.0, B2 = 0.0;
+                double Em = 0.0, B1 = 0.0, B2 = 0.0, A1 = 0.0, A2 = 0.0;
                 double *Dd = malloc(sizeof(double) * nd), *n0 = malloc(sizeof(double) * nd), *Iold = malloc(sizeof(double) * nd);
                 for (int s = 0; s < nd; ++s) {
                     const double *nh = c->G.dir + 3 * s;
@@ -440,13 +472,29 @@ long or_source_step(or_ctx *c, double *I, const double *ug_in, double *ug_out, d
                     Em += Ib * wb;
                     B1 += n0[s] * K * Ib * wb;
                     B2 += Dd[s] * K * wb;
+                    A1 += n0[s] / (n0[s] + Dd[s] * atm * dtk) * Ib * wb;
+                    A2 += Dd[s] / (n0[s] + Dd[s] * atm * dtk) * wb;
                 }
                 B2 *= dtk / fourpi;
-                teq q = {B1, B2, Em + Y * Tm, Y, Tm, Em, au, as, eta, c->c.arad, dtk, c->c.T_exp};
-                double Estar;
-                if (!solve_E(&q, &Estar)) ++fails;
-                double Tp = teq_T(&q, Estar);
-                double aap = au * pow(Tp, -c->c.T_exp), atp = aap + as;
+                A2 *= dtk / fourpi;
+                double Estar, Tp, aap, atp;
+                if (c->c.coupling == 1 || c->c.coupling == 2) {
+                    meq q = {A1, A2, Em + Y * Tm, Y, Tm, Em, au, as, eta, c->c.arad, c->c.T_exp, c->c.coupling};
+                    if (!solve_meq(&q, &Estar)) {   /* no positive temperature: the cell is left as it was */
+                        ++fails;
+                        free(Dd); free(n0); free(Iold);
+                        continue;
+                    }
+                    Tp = meq_T(&q, Estar);
+                    aap = meq_aaP(&q, Tp);
+                    atp = atm;                      /* the total absorption stays explicit */
+                } else {
+                    teq q = {B1, B2, Em + Y * Tm, Y, Tm, Em, au, as, eta, c->c.arad, dtk, c->c.T_exp};
+                    if (!solve_E(&q, &Estar)) ++fails;
+                    Tp = teq_T(&q, Estar);
+                    aap = au * pow(Tp, -c->c.T_exp);
+                    atp = aap + as;
+                }
                 double em = eta * aap * c->c.arad * Tp * Tp * Tp * Tp + as * Estar;
                 double Ep = 0.0, dR[4] = {0, 0, 0, 0};
                 for (int s = 0; s < nd; ++s) {

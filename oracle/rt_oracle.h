@@ -49,6 +49,7 @@ typedef struct {
     int transport;        /* 0 disables transport (source only) */
     int source;           /* 0 disables the interaction step */
     double n0_cut;        /* |n_0| below this: intensity zeroed */
+    int coupling;         /* temperature solve of section 3.5.2: 1, 2 or 3 (0 = 3) */
 } or_config;
 
 typedef struct or_ctx or_ctx;

@@ -40,6 +40,7 @@ class rt_config(C.Structure):
         ("T_exp", C.c_double), ("rho_floor", C.c_double), ("abar", C.c_double), ("tau_dt", C.c_int),
         ("order", C.c_int), ("limiter", C.c_int), ("ang_recon", C.c_int), ("transport", C.c_int),
         ("source", C.c_int), ("n0_cut", C.c_double), ("precision", C.c_int),
+        ("coupling", C.c_int),
     ]
 
 
@@ -148,6 +149,7 @@ def make_config(cfg: dict, precision="fp64") -> rt_config:
     c.limiter = LIMITER[cfg.get("limiter", "mc")]; c.ang_recon = ANG[cfg.get("ang_recon", "mapr")]
     c.transport = int(bool(cfg.get("transport", True))); c.source = int(bool(cfg.get("source", True)))
     c.n0_cut = float(cfg.get("n0_cut", 0.1)); c.precision = PRECISION[precision]
+    c.coupling = int(cfg.get("coupling", 3))
     return c
 
 

@@ -844,6 +844,7 @@ static rt_status adj_check(rt_ctx *c, const char *who) {
     if (c->metric != RT_MINKOWSKI_CART || !c->static_fluid)
         return adj_fail(c, RT_EINVAL, w + ": flat Cartesian geometry with the fluid at rest only");
     if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, w + ": FP64 or FP32 intensities only");
+    if (!rt_coupling3(c)) return adj_fail(c, RT_EINVAL, w + ": coupling method 3 only");
     if (c->nd > LaneD::NT || c->nd % 2) return adj_fail(c, RT_EINVAL, w + ": at most 192 directions");
     if ((double)c->ncell * c->nd >= 2147483647.0)
         return adj_fail(c, RT_EINVAL, w + ": n_cell * n_dir must be below 2^31");

@@ -53,8 +53,8 @@ extern "C" rt_status rt_create(const rt_grid *g, const rt_config *cfg, void *cud
         if (f.nx[a] > 1 && f.nx[a] < 2) { g_create_err = "active axes need at least 2 cells"; return RT_EINVAL; }
     }
     if (f.precision < 0 || f.precision > 2 || f.order < 1 || f.order > 2 || !(f.gam > 1.0) ||
-        f.T_exp < 0.0 || f.T_exp >= 4.0 || f.limiter < 0 || f.limiter > 2) {
-        g_create_err = "invalid precision, order, gamma, T_exp or limiter";
+        f.T_exp < 0.0 || f.T_exp >= 4.0 || f.limiter < 0 || f.limiter > 2 || f.coupling < 0 || f.coupling > 3) {
+        g_create_err = "invalid precision, order, gamma, T_exp, limiter or coupling method";
         return RT_EINVAL;
     }
     const bool halo = f.bc[2][0] == RT_BC_HALO || f.bc[2][1] == RT_BC_HALO;

@@ -518,6 +518,26 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             }
             B2 *= dt / qw;
             const double Y = A.cc_Y[cidx], ug = A.ug_in[cidx], Tm = ug / Y;
+            if (A.coupling != 3) {
+                // methods 1 and 2: A1 = B1 / (alpha_- dt), A2 = B2 / (alpha_- dt); the
+                // intensity update keeps the explicit alpha_-
+                const double iY = 1.0 / Y, au = A.cc_au[cidx], as = A.cc_as[cidx];
+                const M12 q{B1 / adt, B2 / adt, Em + ug, Y, iY, Tm, Em, au, as, A.eta[cidx], A.arad, A.T_exp,
+                            au * tpow_neg<double>(Tm, A.T_exp), A.coupling};
+                double X;
+                if (!solve_m12(q, &X)) {       // no positive temperature: the cell is left as it was
+                    atomicAdd(A.fail, 1ull);
+                    scOn[s] = 0;
+                } else {
+                    const double Tp = Tm + (Em - X) * iY;
+                    const double aap = A.coupling == 1 ? q.aam : au * tpow_neg<double>(Tp, A.T_exp);
+                    const double em = q.eta * aap * A.arad * Tp * Tp * Tp * Tp + as * X;
+                    if (A.sv_X) { A.sv_Em[cidx] = Em; A.sv_X[cidx] = X; }
+                    sc64[s] = Em;
+                    scEm[s] = (TM)(dt * em / qw);
+                    scA[s] = (TM)adt;
+                }
+            } else {
             Teq<double> q = make_teq<double>(B1, B2, Em + ug, Y, Tm, Em, A.cc_au[cidx], A.cc_as[cidx], A.eta[cidx], A.arad,
                                              dt, A.T_exp);
             double lo = 0.0, hi = q.W, X;
@@ -541,6 +561,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             sc64[s] = Em;
             scEm[s] = (TM)(dt * em / qw);
             scA[s] = (TM)(atp * dt);
+            }
         }
     }
     __syncthreads();
@@ -705,6 +726,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     A.gam = f.gam; A.arad = f.arad; A.T_exp = f.T_exp; A.abar = f.abar; A.sumw = c->sumw; A.sumwf = c->sumwf;
     A.tau_dt = f.tau_dt; A.limiter = f.limiter; A.ang_recon = f.ang_recon;
     A.transport = f.transport; A.source = f.source; A.dtk = dtk;
+    A.coupling = rt_coupling3(c) ? 3 : f.coupling;
     A.Isrc = Isrc; A.Ibase = Ibase; A.Iout = Iout; A.ug_in = ug_in; A.ug_out = ug_out;
     A.alpha_in = alpha_in; A.alpha_int = alpha_int; A.alpha_out = alpha_out;
     A.cc_au = c->cc_au; A.cc_as = c->cc_as; A.cc_Y = c->cc_Y; A.cc_on = c->cc_on;

@@ -27,6 +27,7 @@ struct StageArgs {
     // the packed kernel takes kb = 0 with pointers at the owned origin and
     // signed offsets
     int kb;
+    int coupling;              // temperature solve of section 3.5.2: 1, 2 or 3
     double dtk;
     const void *Isrc; const void *Ibase; void *Iout;
     const double *ug_in; double *ug_out;
@@ -217,6 +218,39 @@ __device__ __forceinline__ double tneg_mixed(double T, double p) {
     return tpow_neg<double>(T, p);
 }
 
+// Methods 1 and 2 of section 3.5.2 (eqs. semi_implicit_T, implicit_T) for the
+// post-interaction energy X = E-bar_+ with T = T_- + (E-bar_- - X)/Y:
+//   h(X) = (1 - A2 alpha^s) X - A1 - A2 eta alpha^a_P a T^4,
+// A1, A2 of eqs. A1, A2 (explicit alpha_-), alpha^a_P = kappa rho^m T_-^-p
+// (method 1) or kappa rho^m T^-p (method 2).  h increases strictly on [0, W);
+// without a sign change there (h(W) = (1 - A2 alpha^s) W - A1 <= 0) no
+// positive temperature solves the equations and the solve reports failure.
+struct M12 { double A1, A2, W, Y, iY, Tm, Em, au, as, eta, arad, p, aam; int method; };
+__device__ inline bool solve_m12(const M12 &q, double *Xout) {
+    const double lin = 1.0 - q.A2 * q.as;
+    if (!(lin * q.W - q.A1 > 0.0)) return false;
+    double lo = 0.0, hi = q.W, X = fmin(fmax(q.Em, 0.0), 0.5 * q.W);
+    const double pe = q.method == 1 ? 0.0 : q.p;
+    for (int it = 0; it < 200; ++it) {
+        const double T = q.Tm + (q.Em - X) * q.iY;
+        const double aa = q.method == 1 ? q.aam : q.au * tpow_neg<double>(T, q.p);
+        const double e4 = q.A2 * q.eta * aa * q.arad * T * T * T * T;
+        const double h = lin * X - q.A1 - e4;
+        if (h > 0.0) hi = X; else lo = X;
+        if (fabs(h) <= 4.0 * 2.220446049250313e-16 * (fabs(lin * X) + q.A1 + e4)) break;
+        const double dh = lin + (4.0 - pe) * e4 / T * q.iY;
+        double Xn = X - h / dh;
+        if (!(Xn > lo && Xn < hi)) Xn = 0.5 * (lo + hi);
+        if (fabs(Xn - X) <= 4.0 * 2.220446049250313e-16 * fabs(X) || hi - lo <= 4.0 * 2.220446049250313e-16 * hi) {
+            X = Xn;
+            break;
+        }
+        X = Xn;
+    }
+    *Xout = X;
+    return true;
+}
+
 // Temperature solve of the mixed (FP32-storage) path: FP32 Newton from E-bar_-,
 // then FP64 residual iterations X <- X - h_64(X) / h'_32(X) (the residual is
 // FP64, the slope FP32, so each iteration gains ~7 digits; one suffices after
@@ -253,4 +287,6 @@ __device__ inline bool solve_mixed(const Teq<double> &q, double *Xout) {
 // fast path of the stage (stage_flat.cu): flat Cartesian geometry, a fluid at
 // rest in every cell, MC limiter, fewer than 2^31 stored intensities
 bool rt_stage_fast_ok(const rt_ctx *c);
+// method 3 of section 3.5.2 (the fast paths and the reverse pass implement it only)
+inline bool rt_coupling3(const rt_ctx *c) { return c->cfg.coupling == 0 || c->cfg.coupling == 3; }
 rt_status rt_launch_stage_fs(rt_ctx *c, const rtk::StageArgs &A, int NT);

@@ -834,7 +834,7 @@ rt_status launch_fs_blk(rt_ctx *c, const StageArgs &A, int NT) {
 }  // namespace
 
 bool rt_stage_fast_ok(const rt_ctx *c) {
-    return c->metric == RT_MINKOWSKI_CART && c->static_fluid && c->cfg.limiter == RT_LIM_MC &&
+    return c->metric == RT_MINKOWSKI_CART && c->static_fluid && c->cfg.limiter == RT_LIM_MC && rt_coupling3(c) &&
            c->cfg.n_pole_zero == 0 && c->nd <= FS_NT && (double)(c->ncell + 2 * c->hcells) * c->nd < 2147483647.0;
 }
 
