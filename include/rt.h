@@ -40,7 +40,12 @@ typedef enum {
 } rt_status;
 
 typedef enum { RT_FP64 = 0, RT_FP32 = 1, RT_BF16 = 2 } rt_precision;
-typedef enum { RT_MINKOWSKI_CART = 0, RT_KERR_SCHILD = 1 } rt_metric_kind;
+/* RT_SNAKE: flat space in snake coordinates (w, y, z), w = x - A sin(k pi y)
+ * (App. A.1; params {A, k}); RT_CART_CYLTETRAD: flat space in Cartesian
+ * coordinates with the tetrad aligned with the cylindrical unit vectors
+ * (r-hat, phi-hat, z-hat), phi = atan2(y, x) (section 4.5; no params; the
+ * box must not contain the axis x = y = 0). */
+typedef enum { RT_MINKOWSKI_CART = 0, RT_KERR_SCHILD = 1, RT_SNAKE = 2, RT_CART_CYLTETRAD = 3 } rt_metric_kind;
 typedef enum { RT_BC_PERIODIC = 0, RT_BC_OUTFLOW = 1, RT_BC_POLE = 2, RT_BC_BEAM = 3, RT_BC_HALO = 4 } rt_bc;
 typedef enum { RT_LIM_MC = 0, RT_LIM_MINMOD = 1, RT_LIM_DONOR = 2 } rt_limiter;
 
@@ -105,7 +110,8 @@ void rt_destroy(rt_ctx *c);
 const char *rt_last_error(const rt_ctx *c);
 
 /* Metric and tetrad cache, sections 2.1 and App. A.2: kind = rt_metric_kind;
- * params = {M, a} for Kerr-Schild (ignored for Minkowski).  Computes, in FP64
+ * params = {M, a} for Kerr-Schild, {A, k} for snake coordinates (ignored
+ * otherwise).  Computes, in FP64
  * on the device, the metric, the normal-observer tetrad (eq.
  * tetrad_restriction), the Ricci rotation coefficients (eq.
  * ricci_rotation_coefficients) with exact derivatives, and the per-direction

@@ -12,7 +12,7 @@ import numpy as np
 from .build import build
 
 BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3, "halo": 4}
-COORDS = {"minkowski": 0, "kerr_schild": 1}
+COORDS = {"minkowski": 0, "kerr_schild": 1, "snake": 2, "cart_cyl_tetrad": 3}
 LIMITER = {"mc": 0, "minmod": 1, "donor": 2}
 ANG = {"mapr": 0, "donor": 1}
 
@@ -26,7 +26,7 @@ class _Cfg(C.Structure):
         ("rho_exp", C.c_double), ("T_exp", C.c_double), ("rho_floor", C.c_double),
         ("abar", C.c_double), ("tau_dt", C.c_int), ("order", C.c_int), ("limiter", C.c_int),
         ("ang_recon", C.c_int), ("transport", C.c_int), ("source", C.c_int), ("n0_cut", C.c_double),
-        ("coupling", C.c_int),
+        ("coupling", C.c_int), ("snake_A", C.c_double), ("snake_k", C.c_double),
     ]
 
 
@@ -97,6 +97,7 @@ def make_cfg(cfg: dict) -> _Cfg:
     c.transport = int(bool(cfg.get("transport", True))); c.source = int(bool(cfg.get("source", True)))
     c.n0_cut = float(cfg.get("n0_cut", 0.1))
     c.coupling = int(cfg.get("coupling", 3))
+    c.snake_A = float(cfg.get("snake_A", 0.0)); c.snake_k = float(cfg.get("snake_k", 0.0))
     return c
 
 

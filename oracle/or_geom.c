@@ -14,6 +14,14 @@
  *    forward-mode dual numbers, one run per coordinate direction.
  *  - Kerr-Schild metric in logical coordinates x1 = ln r, x2 = theta, x3 = phi
  *    (the textbook Kerr-Schild form with dr = r dx1).
+ *  - Snake coordinates (App. A.1): (w, y, z) with w = x - A sin(k pi y), the
+ *    metric of dx = dw + delta dy, delta = A k pi cos(k pi y); the tetrad is the
+ *    same Gram-Schmidt construction.  (The appendix prints a tetrad that is not
+ *    orthonormal under its own metric; this reading keeps eq. tetrad_def.)
+ *  - Flat space in Cartesian coordinates with the tetrad aligned with the
+ *    cylindrical unit vectors (section 4.5): e_1 = r-hat, e_2 = phi-hat,
+ *    e_3 = z-hat, phi = atan2(y, x).  (The printed matrix of
+ *    eq. cylindrical_alignment is garbled; this is the frame the text names.)
  */
 #include "or_internal.h"
 
@@ -32,8 +40,17 @@ static dn dexp(dn a) { double e = exp(a.v); dn o = {e, e * a.d}; return o; }
 /* g_{mu nu}(x) with derivative along coordinate wrt (1 or 2; 0 = none) */
 static void metric(const or_config *c, const double x[3], int wrt, dn g[4][4]) {
     for (int m = 0; m < 4; ++m) for (int n = 0; n < 4; ++n) g[m][n] = D(0.0);
-    if (c->coords == OR_MINKOWSKI_CART) {
+    if (c->coords == OR_MINKOWSKI_CART || c->coords == OR_CART_CYLTETRAD) {
         g[0][0] = D(-1.0); g[1][1] = D(1.0); g[2][2] = D(1.0); g[3][3] = D(1.0);
+        return;
+    }
+    if (c->coords == OR_SNAKE) {
+        dn y = {x[1], wrt == 2 ? 1.0 : 0.0};
+        dn kp = D(c->snake_k * M_PI);
+        dn del = dmul(D(c->snake_A), dmul(kp, dcos(dmul(kp, y))));
+        g[0][0] = D(-1.0); g[1][1] = D(1.0); g[3][3] = D(1.0);
+        g[1][2] = g[2][1] = del;
+        g[2][2] = dadd(D(1.0), dmul(del, del));
         return;
     }
     dn x1 = {x[0], wrt == 1 ? 1.0 : 0.0}, th = {x[1], wrt == 2 ? 1.0 : 0.0};
@@ -113,12 +130,25 @@ static void tetrad(dn g[4][4], dn gi[4][4], dn e[4][4]) {
     for (int m = 0; m < 4; ++m) e[1][m] = ddiv(v[m], n1);
 }
 
+/* tetrad (r-hat, phi-hat, z-hat) of Cartesian coordinates at (x, y) */
+static void tetrad_cyl(const double x[3], int wrt, dn e[4][4]) {
+    for (int a = 0; a < 4; ++a) for (int m = 0; m < 4; ++m) e[a][m] = D(0.0);
+    dn X = {x[0], wrt == 1 ? 1.0 : 0.0}, Y = {x[1], wrt == 2 ? 1.0 : 0.0};
+    dn r = dsqrt(dadd(dmul(X, X), dmul(Y, Y)));
+    dn c = ddiv(X, r), s = ddiv(Y, r);
+    e[0][0] = D(1.0);
+    e[1][1] = c; e[1][2] = s;
+    e[2][1] = dneg(s); e[2][2] = c;
+    e[3][3] = D(1.0);
+}
+
 void or_geometry(const or_config *c, const double x[3], int want_omega, or_geom *out) {
     dn g[3][4][4], gi[3][4][4], e[3][4][4];
     for (int w = 0; w < 3; ++w) {
         metric(c, x, w, g[w]);
         inverse4(g[w], gi[w]);
-        tetrad(g[w], gi[w], e[w]);
+        if (c->coords == OR_CART_CYLTETRAD) tetrad_cyl(x, w, e[w]);
+        else tetrad(g[w], gi[w], e[w]);
         if (!want_omega) break;
     }
     for (int m = 0; m < 4; ++m) for (int n = 0; n < 4; ++n) {

@@ -22,7 +22,11 @@ extern "C" {
 /* boundary kinds per logical face */
 enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_POLE = 2, OR_BC_BEAM = 3, OR_BC_HALO = 4 };
 /* coordinates */
-enum { OR_MINKOWSKI_CART = 0, OR_KERR_SCHILD = 1 };
+/* OR_SNAKE: flat space in snake coordinates (w, y, z), w = x - A sin(k pi y)
+   (App. A.1); OR_CART_CYLTETRAD: flat space in Cartesian coordinates with the
+   tetrad aligned with the cylindrical unit vectors (r-hat, phi-hat, z-hat)
+   (section 4.5, eq. cylindrical_alignment) */
+enum { OR_MINKOWSKI_CART = 0, OR_KERR_SCHILD = 1, OR_SNAKE = 2, OR_CART_CYLTETRAD = 3 };
 
 typedef struct {
     int n_geo;            /* icosahedron edge subdivisions n (1,2,4,...): 10n^2+2 directions */
@@ -50,6 +54,7 @@ typedef struct {
     int source;           /* 0 disables the interaction step */
     double n0_cut;        /* |n_0| below this: intensity zeroed */
     int coupling;         /* temperature solve of section 3.5.2: 1, 2 or 3 (0 = 3) */
+    double snake_A, snake_k;   /* OR_SNAKE: amplitude and wave number of the coordinate wiggle */
 } or_config;
 
 typedef struct or_ctx or_ctx;

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "librt_b300.so")
 RT_STATUS = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENOCONV", 5: "RT_ESTATE",
              6: "RT_ETIMEOUT"}
 BC = {"periodic": 0, "outflow": 1, "pole": 2, "beam": 3, "halo": 4}
-METRIC = {"minkowski": 0, "kerr_schild": 1}
+METRIC = {"minkowski": 0, "kerr_schild": 1, "snake": 2, "cart_cyl_tetrad": 3}
 LIMITER = {"mc": 0, "minmod": 1, "donor": 2}
 ANG = {"mapr": 0, "donor": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
@@ -174,8 +174,11 @@ class RadiationStep:
         self.rec_id = 0
         self.nd = grid.nd
         self.ncell = int(np.prod(cfg["nx"]))
-        self._check(lib().rt_set_metric(h, METRIC[cfg.get("coords", "minkowski")],
-                                        np.array([cfg.get("M", 1.0), cfg.get("a", 0.0)]).ctypes.data))
+        coords = cfg.get("coords", "minkowski")
+        params = ([cfg.get("snake_A", 0.0), cfg.get("snake_k", 0.0)] if coords == "snake"
+                  else [cfg.get("M", 1.0), cfg.get("a", 0.0)])
+        self._params = np.array(params, dtype=np.float64)
+        self._check(lib().rt_set_metric(h, METRIC[coords], self._params.ctypes.data))
 
     def _check(self, st):
         if st:

@@ -133,16 +133,33 @@ extern "C" const char *rt_last_error(const rt_ctx *c) { return c ? c->err.c_str(
 
 extern "C" rt_status rt_set_metric(rt_ctx *c, int kind, const double *params) {
     if (!c) return RT_EINVAL;
-    if (kind != RT_MINKOWSKI_CART && kind != RT_KERR_SCHILD) return fail(c, RT_EINVAL, "unknown metric kind");
+    if (kind < RT_MINKOWSKI_CART || kind > RT_CART_CYLTETRAD) return fail(c, RT_EINVAL, "unknown metric kind");
     if (c->metric >= 0) return fail(c, RT_ESTATE, "the metric is already set");
     if (rt_status d = rt_check_device(c)) return d;
-    c->metric = kind;
     if (kind == RT_KERR_SCHILD) {
         if (!params) return fail(c, RT_EINVAL, "Kerr-Schild needs {M, a}");
         c->M = params[0]; c->a = params[1];
         if (!(c->M >= 0.0) || !(std::fabs(c->a) <= c->M || c->M == 0.0)) return fail(c, RT_EINVAL, "need M >= 0, |a| <= M");
+        c->metric = kind;
         return rt_build_geometry(c);
     }
+    if (kind == RT_SNAKE) {
+        if (!params) return fail(c, RT_EINVAL, "snake coordinates need {A, k}");
+        c->M = params[0]; c->a = params[1];     // the geometry kernels take (A, k) in (M, a)
+        c->metric = kind;
+        return rt_build_geometry(c);
+    }
+    if (kind == RT_CART_CYLTETRAD) {
+        const rt_config &f = c->cfg;
+        // the cylindrical frame is undefined on the axis: no cell, ghost cell
+        // or face of the geometry table may reach it
+        auto spans0 = [&](int a) { return f.x0[a] - 2.0 * f.dx[a] <= 0.0 && f.x0[a] + (f.nx[a] + 2) * f.dx[a] >= 0.0; };
+        if (spans0(0) && spans0(1))
+            return fail(c, RT_EINVAL, "the cylindrical tetrad needs a box away from the axis x = y = 0");
+        c->metric = kind;
+        return rt_build_geometry(c);
+    }
+    c->metric = kind;
     c->gn[0] = c->cfg.nx[0] + (c->active[0] ? 4 : 0);
     c->gn[1] = c->cfg.nx[1] + (c->active[1] ? 4 : 0);
     return RT_OK;

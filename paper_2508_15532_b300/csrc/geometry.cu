@@ -33,11 +33,21 @@ struct GeoPoint {
     Dl det;
 };
 
+// (M, a) are Kerr-Schild's mass and spin, or (A, k) of snake coordinates
 __device__ void metric_ks(int kind, double M, double a, double x1, double x2, int wrt, Dl g[4][4]) {
     for (int m = 0; m < 4; ++m)
         for (int n = 0; n < 4; ++n) g[m][n] = mk(0.0);
-    if (kind == RT_MINKOWSKI_CART) {
+    if (kind == RT_MINKOWSKI_CART || kind == RT_CART_CYLTETRAD) {
         g[0][0] = mk(-1.0); g[1][1] = mk(1.0); g[2][2] = mk(1.0); g[3][3] = mk(1.0);
+        return;
+    }
+    if (kind == RT_SNAKE) {
+        // dx = dw + delta dy, delta = A k pi cos(k pi y), y = x2
+        const Dl y = mk(x2, wrt == 2 ? 1.0 : 0.0), kp = mk(a * 3.14159265358979323846);
+        const Dl del = mk(M) * kp * dl_cos(kp * y);
+        g[0][0] = mk(-1.0); g[1][1] = mk(1.0); g[3][3] = mk(1.0);
+        g[1][2] = g[2][1] = del;
+        g[2][2] = mk(1.0) + del * del;
         return;
     }
     Dl r = dl_exp(mk(x1, wrt == 1 ? 1.0 : 0.0));
@@ -89,6 +99,18 @@ __device__ void inverse_adj(const Dl a[4][4], Dl inv[4][4], Dl *det_out) {
 __device__ void build_point(int kind, double M, double a, double x1, double x2, int wrt, GeoPoint &P) {
     metric_ks(kind, M, a, x1, x2, wrt, P.g);
     inverse_adj(P.g, P.gi, &P.det);
+    if (kind == RT_CART_CYLTETRAD) {
+        // (r-hat, phi-hat, z-hat) of the Cartesian (x, y) = (x1, x2)
+        const Dl X = mk(x1, wrt == 1 ? 1.0 : 0.0), Y = mk(x2, wrt == 2 ? 1.0 : 0.0);
+        const Dl r = dl_sqrt(X * X + Y * Y), c = X / r, s = Y / r;
+        for (int b = 0; b < 4; ++b)
+            for (int m = 0; m < 4; ++m) P.e[b][m] = mk(0.0);
+        P.e[0][0] = mk(1.0);
+        P.e[1][1] = c; P.e[1][2] = s;
+        P.e[2][1] = -s; P.e[2][2] = c;
+        P.e[3][3] = mk(1.0);
+        return;
+    }
     Dl root = dl_sqrt(-P.gi[0][0]);
     for (int m = 0; m < 4; ++m) P.e[0][m] = -P.gi[0][m] / root;
     for (int b = 1; b < 4; ++b)
