@@ -44,8 +44,8 @@ FLUID_BYTES_PER_CELL_STEP = 224.0
 # of the torus recipe); traffic scales with the cells (each cell is read once
 # per source array and written once; the Kerr-Schild tables are per (r, theta)
 # point and are mostly served from L1/L2)
-NCU_TRAFFIC = {("a83e9d10b9b7", "fp32", "flat3d"): 9.97,
-               ("a83e9d10b9b7", "fp32", "kerr3d"): 13.07}   # {(sha1 of the stage sources, precision, workload): B}
+NCU_TRAFFIC = {("b3c065c082d8", "fp32", "flat3d"): 9.92,
+               ("b3c065c082d8", "fp32", "kerr3d"): 13.29}   # {(sha1 of the stage sources, precision, workload): B}
 STAGE_SOURCES = ("stage_common.cuh", "stage.cu", "stage_flat.cu")
 
 
@@ -75,6 +75,7 @@ class ClockSampler:
 
     def __init__(self, gpu_index=0):
         self.rows, self.proc, self.idx = [], None, gpu_index
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -89,7 +90,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([v.strip() for v in line.split(",")])
+            self.rows.append([v.strip() for v in line.split(",")] + [time.perf_counter()])
+
+    def wait_first(self, timeout=5.0):
+        """Block until the first sample has arrived (nvidia-smi takes a while
+        to start), so that the timed region that follows is sampled."""
+        end = time.perf_counter() + timeout
+        while self.proc and not self.rows and time.perf_counter() < end:
+            time.sleep(0.01)
+
+    def region(self, t0, t1):
+        self.t0, self.t1 = t0, t1
 
     def __exit__(self, *a):
         if self.proc:
@@ -100,17 +111,21 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        rows = self.rows
+        if self.t0 is not None:     # the samples taken while the timed region ran
+            inside = [r for r in rows if self.t0 <= r[-1] <= self.t1 + 0.025]
+            rows = inside or rows
+        sm = [float(r[1]) for r in rows if len(r) >= 10 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 10 and r[2].replace(".", "").isdigit()]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) >= 9:
+        for r in rows:
+            if len(r) >= 10:
                 for n, v in zip(names, r[5:9]):
                     if v.strip().lower() == "active":
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(sm), "interval_ms": 20}
 
 
 def cpu_oracle_rate(n_cells, n_geo, steps):
@@ -302,7 +317,7 @@ def adjoint_leg(dev, stream, grid, prec="fp64", nsteps=64, ckpt=8, N=64):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
@@ -401,12 +416,15 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st.set_timing(True)
     with ClockSampler(local) as clk:
+        clk.wait_first()
         torch.cuda.synchronize(dev)
+        t_start = time.perf_counter()
         ev0.record(stream)
         for _ in range(args.steps):
             st.step(dt, 1)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.region(t_start, time.perf_counter())
     ms = ev0.elapsed_time(ev1)
     stage_ms, launches = st.get_timing()
     st.set_timing(False)

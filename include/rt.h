@@ -124,7 +124,9 @@ rt_status rt_set_metric(rt_ctx *c, int kind, const double *params);
  * emission multiplier eta (NULL = 1).  Copied. */
 rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_gas, const double *ucon,
                        const double *kappa, const double *alpha_s_coef, const double *eta);
-/* Tetrad-frame intensities [n_cell*n_dir] in the configured storage type. */
+/* Tetrad-frame intensities [n_cell*n_dir] in the configured storage type.
+ * rt_set_intensity also sets the force on the gas (rt_moments' G) to zero:
+ * no interaction has acted on the new state. */
 rt_status rt_set_intensity(rt_ctx *c, const void *I);
 rt_status rt_get_intensity(rt_ctx *c, void *I);
 rt_status rt_set_ugas(rt_ctx *c, const double *u_gas);

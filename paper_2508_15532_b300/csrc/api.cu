@@ -209,8 +209,10 @@ extern "C" rt_status rt_set_fluid(rt_ctx *c, const double *rho, const double *u_
 extern "C" rt_status rt_set_intensity(rt_ctx *c, const void *I) {
     if (!c || !I) return RT_EINVAL;
     if (rt_status d = rt_check_device(c)) return d;
-    // a deferred G belongs to the state being replaced
-    if (c->g_lazy) if (rt_status st = rt_resolve_g(c)) return st;
+    // no interaction has acted on the new state yet: its force on the gas is
+    // zero (a deferred G of the replaced state is dropped, not computed)
+    c->g_lazy = false;
+    RT_CUDA_TRY(c, cudaMemsetAsync(c->G, 0, (size_t)c->ncell * 32, c->stream));
     RT_CUDA_TRY(c, cudaMemcpyAsync(c->I[0], I, (size_t)c->ncell * c->nd * c->esize, cudaMemcpyDefault, c->stream));
     c->have_I = true;
     return RT_OK;

@@ -11,7 +11,7 @@
 //   omega^a_{bc} = e^a_beta e^mu_b (d_mu e^beta_c + Gamma^beta_{mu nu} e^nu_c)
 //     (eq. ricci_rotation_coefficients) with d_mu from forward-mode duals.
 // Derived per (point, direction) and per (point, edge) tables feed the step.
-#include "rt_internal.cuh"
+#include "stage_common.cuh"
 #include <cmath>
 
 struct Dl {
@@ -351,9 +351,13 @@ __global__ void k_wbar(int ncell, int nd, const double *__restrict__ uhat, const
     if (cidx >= ncell) return;
     const double *u = uhat + 4 * (size_t)cidx;
     double sum = 0.0;
+    const bool rest = u[0] == 1.0 && u[1] == 0.0 && u[2] == 0.0 && u[3] == 0.0;   // D = 1
     for (int s = 0; s < nd; ++s) {
+        const double ws = wf ? (double)wf[s] : w[s];
+        if (rest) { sum += ws; continue; }
         const double D = u[0] - (u[1] * dir[3 * s] + u[2] * dir[3 * s + 1] + u[3] * dir[3 * s + 2]);
-        sum += (wf ? (double)wf[s] : w[s]) / (D * D);
+        const double r = rtk::rcp64(D);
+        sum += ws * r * r;
     }
     wbar[cidx] = sum;
 }
