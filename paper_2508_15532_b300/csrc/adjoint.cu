@@ -364,6 +364,7 @@ struct RevArgs {
     int nx[3], act[3], per[3], nd, limiter, transport, source;
     int add_base;                 // the stage's base intensities are its input
     int out_f64;                  // !FUSE: Zout is FP64 whatever the storage type
+    int rev_order;                // bricks in reverse launch order
     int zg_f64;                   // Zg is FP64 whatever the storage type (read at own elements only:
                                   // the transport-free launch takes the caller's cotangent as it is)
     int ub_dst_acc;               // FUSE: add to ub_dst instead of writing it
@@ -421,7 +422,10 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     const int d0 = act ? L * p : 0;        // idle lanes shadow direction 0; their results are dropped
     const int nx0 = A.nx[0], nx1 = A.nx[1], nx2 = A.nx[2];
     const int nseg = (nx0 + TXC - 1) / TXC;
-    const int seg = blockIdx.x % nseg, rest = blockIdx.x / nseg, nyb = nx1 / BY;
+    // every other launch walks the bricks in reverse: it starts where the launch
+    // before it ended, on the part of that launch's output still in L2
+    const int bid = A.rev_order ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int seg = bid % nseg, rest = bid / nseg, nyb = nx1 / BY;
     const int j0 = (rest % nyb) * BY, k0 = (rest / nyb) * BZ, i0 = seg * TXC;
     const int nc = min(TXC, nx0 - i0);
     auto mapq = [](int q, int n, int per) -> int {
@@ -931,6 +935,12 @@ static rt_status adj_forward(rt_ctx *c, const AdjArena &ar, double dt, double *G
 }
 
 // reverse sweep over the arena's N steps
+// the reverse sweep's launches alternate their brick order (see k_rev)
+static rt_status launch_rev_alt(rt_ctx *c, RevArgs &A, bool fuse, int &nlaunch) {
+    A.rev_order = nlaunch++ & 1;
+    return launch_rev(c, A, fuse);
+}
+
 static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const double *dL_dI_out,
                              const double *dL_dug_out, double *dL_dI_in, double *dL_dug_in, double *dL_dkappa,
                              double *dL_deta) {
@@ -941,6 +951,7 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
     void *const Z[2] = {ar.Z[0], ar.Z[1]};
     double *ubc = ar.ubc, *ubp = ar.ubp;
     rt_status st;
+    int nl = 0;
     RevArgs B{};
     for (int a = 0; a < 3; ++a) {
         B.nx[a] = f.nx[a]; B.act[a] = c->active[a]; B.per[a] = f.bc[a][0] == RT_BC_PERIODIC;
@@ -968,7 +979,7 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
         A.I = In[N]; A.Zg = dL_dI_out; A.zg_f64 = f64 ? 0 : 1; A.ubA = dL_dug_out;
         A.dts = dt; A.ugm = un[N - 1]; A.Em = sE[N * ns - 1]; A.X = sX[N * ns - 1];
         A.ub_dst = ubc; A.ub_dst_acc = 0; A.Zout = Z[0];
-        if ((st = launch_rev(c, A, true)) != RT_OK) return st;
+        if ((st = launch_rev_alt(c, A, true, nl)) != RT_OK) return st;
     }
     int zr = 0;   // Z[zr]: cotangent of the current stage's transported state
     for (int n = N - 1; n >= 0; --n) {
@@ -980,7 +991,7 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
             A.alpha = als[n]; A.ug_a = us[n]; A.ubA = nullptr;
             A.dts = 0.5 * dt; A.ugm = un[n]; A.Em = sE[2 * n]; A.X = sX[2 * n];
             A.ub_dst = ubc; A.ub_dst_acc = 1; A.Zout = Z[1];
-            if ((st = launch_rev(c, A, true)) != RT_OK) return st;
+            if ((st = launch_rev_alt(c, A, true, nl)) != RT_OK) return st;
             // predictor: fluxes of I^n, base I^n; the corrector's base cotangent Z[0] adds
             RevArgs P = stage_args(0.5 * dt);
             P.I = In[n]; P.Zg = Z[1]; P.Zown = Z[0]; P.add_base = 1;
@@ -988,11 +999,11 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
             if (n > 0) {
                 P.dts = dt; P.ugm = un[n - 1]; P.Em = sE[2 * n - 1]; P.X = sX[2 * n - 1];
                 P.ub_dst = ubp; P.ub_dst_acc = 0; P.Zout = Z[0];   // Z[0] is read at own elements only
-                if ((st = launch_rev(c, P, true)) != RT_OK) return st;
+                if ((st = launch_rev_alt(c, P, true, nl)) != RT_OK) return st;
                 std::swap(ubc, ubp);
             } else {
                 P.ubA_out = dL_dug_in; P.Zout = dL_dI_in; P.out_f64 = 1;
-                if ((st = launch_rev(c, P, false)) != RT_OK) return st;
+                if ((st = launch_rev_alt(c, P, false, nl)) != RT_OK) return st;
             }
         } else {
             RevArgs A = stage_args(dt);
@@ -1001,12 +1012,12 @@ static rt_status adj_reverse(rt_ctx *c, const AdjArena &ar, double dt, const dou
             if (n > 0) {
                 A.dts = dt; A.ugm = un[n - 1]; A.Em = sE[n - 1]; A.X = sX[n - 1];
                 A.ub_dst = ubp; A.ub_dst_acc = 0; A.Zout = Z[1 - zr];
-                if ((st = launch_rev(c, A, true)) != RT_OK) return st;
+                if ((st = launch_rev_alt(c, A, true, nl)) != RT_OK) return st;
                 zr ^= 1;
                 std::swap(ubc, ubp);
             } else {
                 A.ubA_out = dL_dug_in; A.Zout = dL_dI_in; A.out_f64 = 1;
-                if ((st = launch_rev(c, A, false)) != RT_OK) return st;
+                if ((st = launch_rev_alt(c, A, false, nl)) != RT_OK) return st;
             }
         }
     }
