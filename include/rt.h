@@ -160,7 +160,9 @@ rt_status rt_cfl_dt_noalloc(rt_ctx *c, double cfl, double *dt);
  * predictor transport over dt/2 + interaction over dt/2, corrector transport
  * over dt with the predictor fluxes + interaction over dt.  *n_fail (may be
  * NULL) receives the number of unconverged temperature solves (then
- * RT_ENOCONV).  Asynchronous unless n_fail is non-NULL. */
+ * RT_ENOCONV).  Asynchronous unless n_fail is non-NULL.  Grids of up to 1024
+ * directions step (n <= 8 of rt_create_geodesic_grid: 642 directions; n = 16
+ * and 32 return RT_EINVAL from the first stage). */
 rt_status rt_step(rt_ctx *c, double dt, int nsteps, double *dt_used, long long *n_fail);
 
 /* One stage of a step (section 3.6): stage 0 is the predictor (transport

@@ -33,10 +33,13 @@ namespace {
 using namespace rtk;
 
 // LK: the limiter kind fixed at compile time (RT_LIM_MC), or -1 to read it
-// from the arguments
-template <typename TS, typename TM, bool FLAT, int BY, int BZ, int LK>
-__global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
-    constexpr int TXC = NCELL / (BY * BZ);
+// from the arguments.  NC: cells per CTA (32; 16 or 8 where the directions'
+// shared-memory rows of 32 cells would not fit).  MAXT: the launch bound, 256
+// threads (up to 256 directions, one per thread) or 1024 (finer grids, at
+// most 64 registers per thread)
+template <typename TS, typename TM, bool FLAT, int BY, int BZ, int LK, int NC, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
+    constexpr int TXC = NC / (BY * BZ);
     constexpr int NOWN = BY * BZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nd = A.nd, ndp = nd + 1;
@@ -52,21 +55,21 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
     const int nc = min(TXC, A.nx0 - i0);
 
     // ---- shared layout
-    TM *It = (TM *)smem_raw;                                  // [NCELL][ndp]
-    TM *Ip = It + NCELL * ndp;                                // [NCELL][ndp]
-    TM *recX = Ip + NCELL * ndp;                              // [NOWN][TXC+1][5]
+    TM *It = (TM *)smem_raw;                                  // [NC][ndp]
+    TM *Ip = It + NC * ndp;                                   // [NC][ndp]
+    TM *recX = Ip + NC * ndp;                                 // [NOWN][TXC+1][5]
     TM *recY = recX + NOWN * (TXC + 1) * 5;                   // [BZ][BY+1][TXC][5]
     TM *recZ = recY + BZ * (BY + 1) * TXC * 5;                // [BY][BZ+1][TXC][5]
-    TM *scU = recZ + BY * (BZ + 1) * TXC * 5;                 // [NCELL][4] tetrad-frame fluid velocity
-    TM *scN0 = scU + 4 * NCELL, *scK = scN0 + NCELL, *scEm = scK + NCELL, *scA = scEm + NCELL;
-    TM *Icell = scA + NCELL;                                  // [NOWN][nd]   (curved only)
+    TM *scU = recZ + BY * (BZ + 1) * TXC * 5;                 // [NC][4] tetrad-frame fluid velocity
+    TM *scN0 = scU + 4 * NC, *scK = scN0 + NC, *scEm = scK + NC, *scA = scEm + NC;
+    TM *Icell = scA + NC;                                     // [NOWN][nd]   (curved only)
     TM *Arec = Icell + (FLAT ? 0 : NOWN * nd);                // [NOWN][nd][6] (curved only)
-    double *part = (double *)(((uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)) + 15) & ~(uintptr_t)15);  // [8][NCELL][6]
-    double *sc64 = part + 8 * NCELL * 6;                      // [NCELL]: E-bar_-
-    int *xmap = (int *)(sc64 + NCELL);                        // [TXC+4]
+    double *part = (double *)(((uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)) + 15) & ~(uintptr_t)15);  // [NT / NC][NC][6]
+    double *sc64 = part + NT * 6;                             // [NC]: E-bar_-
+    int *xmap = (int *)(sc64 + NC);                           // [TXC+4]
     int *rowY = xmap + TXC + 4;                               // [BZ][BY+4]
     int *rowZ = rowY + BZ * (BY + 4);                         // [BY][BZ+4]
-    int *scOn = rowZ + BY * (BZ + 4);                         // [NCELL]
+    int *scOn = rowZ + BY * (BZ + 4);                         // [NC]
 
     // ---- boundary descriptors
     for (int t = s; t < TXC + 4; t += NT) {
@@ -414,7 +417,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
         return ((size_t)k * A.nx1 + j) * A.nx0 + i0 + ii;
     };
     int all_static = 1;
-    if (s < NCELL) {
+    if (s < NC) {
         int ii, j;
         size_t cidx = gcell(s, ii, j);
         int on = 0;
@@ -444,9 +447,9 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
     // B1 and B2 are compensated too in FP32: with alpha^s dt >> 1 the solve's
     // coefficient alpha dt - B2 alpha^s cancels to ~1/(alpha dt) of its terms
     // and magnifies B2's rounding by as much
-    const int nchunk = NT / 32;
+    const int nchunk = NT / NC;
     {
-        const int c = s & 31, g = s >> 5;
+        const int c = s % NC, g = s / NC;
         TM Em = 0, cEm = 0, B1 = 0, B2 = 0, cB1 = 0, cB2 = 0;
         auto kadd = [](TM &sum, TM &comp, TM v) {
             if constexpr (sizeof(TM) == 4) {
@@ -489,18 +492,18 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 cEm = (tk - Em) - yk; Em = tk;
             }
         }
-        double *pp = part + (g * NCELL + c) * 6;
+        double *pp = part + (g * NC + c) * 6;
         pp[0] = (double)Em - (double)cEm; pp[1] = (double)B1 - (double)cB1; pp[2] = (double)B2 - (double)cB2;
     }
     __syncthreads();
     // one lane per cell: temperature solve and per-cell update constants
-    if (s < NCELL) {
+    if (s < NC) {
         int ii, j;
         size_t cidx = gcell(s, ii, j);
         if (ii < nc && scOn[s]) {
             double Em = 0, B1 = 0, B2 = 0;
             for (int g = 0; g < nchunk; ++g) {
-                const double *pp = part + (g * NCELL + s) * 6;
+                const double *pp = part + (g * NC + s) * 6;
                 Em += pp[0]; B1 += pp[1]; B2 += pp[2];
             }
             const double dt = A.dtk, adt = A.alpha_int[cidx] * dt;
@@ -568,7 +571,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
     // per-direction update (eq. fluid_interaction_discrete with alpha(T_+) and
     // emission at T_+), masks, store
     if (act) {
-        for (int lc = 0; lc < NCELL; ++lc) {
+        for (int lc = 0; lc < NC; ++lc) {
             int ii, j;
             size_t cidx = gcell(lc, ii, j);
             if (ii >= nc) continue;
@@ -590,7 +593,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
     __syncthreads();
     // exchange ledger: E-bar(I_+) and Delta R^{0 a} in direction chunks
     {
-        const int c = s & 31, g = s >> 5;
+        const int c = s % NC, g = s / NC;
         TM Ep = 0, cEp = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
         if ((c % TXC) < nc && scOn[c]) {
             const TM u0m = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
@@ -606,11 +609,11 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
                 r0 += dI; r1 += x * dI; r2 += y * dI; r3 += z * dI;
             }
         }
-        double *pp = part + (g * NCELL + c) * 6;
+        double *pp = part + (g * NC + c) * 6;
         pp[0] = (double)Ep - (double)cEp; pp[1] = r0; pp[2] = r1; pp[3] = r2; pp[4] = r3;
     }
     __syncthreads();
-    if (s < NCELL) {
+    if (s < NC) {
         int ii, j;
         size_t cidx = gcell(s, ii, j);
         if (ii < nc) {
@@ -618,7 +621,7 @@ __global__ void __launch_bounds__(MAXNT) k_stage(const StageArgs A) {
             if (scOn[s]) {
                 double Ep = 0, dR[4] = {0, 0, 0, 0};
                 for (int g = 0; g < nchunk; ++g) {
-                    const double *pp = part + (g * NCELL + s) * 6;
+                    const double *pp = part + (g * NC + s) * 6;
                     Ep += pp[0]; dR[0] += pp[1]; dR[1] += pp[2]; dR[2] += pp[3]; dR[3] += pp[4];
                 }
                 double ugp = ugm - (Ep - sc64[s]);
@@ -669,15 +672,26 @@ __global__ void k_cellconst(int ncell, double gam, double rho_exp, double rho_fl
     Y[c] = r / (gam - 1.0);
 }
 
-template <typename TS, typename TM, bool FLAT, int BY, int BZ>
+// shared memory of one CTA of k_stage: the brick's intensities before and
+// after the interaction, face records, per-cell constants, the curved
+// geometry's angular rows, the chunk partial sums, boundary descriptors
+template <typename TM, bool FLAT, int BY, int BZ, int NC>
+size_t stage_smem(int nd, int NT) {
+    constexpr int TXC = NC / (BY * BZ), NOWN = BY * BZ;
+    const size_t ndp = nd + 1;
+    size_t tm = 2 * NC * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NC;
+    if (!FLAT) tm += (size_t)NOWN * nd + 6 * (size_t)NOWN * nd;
+    return sizeof(TM) * tm + 16 + sizeof(double) * ((size_t)NT * 6 + NC) +
+           sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NC);
+}
+
+template <typename TS, typename TM, bool FLAT, int BY, int BZ, int NC, int MAXT>
 rt_status launch(rt_ctx *c, const StageArgs &A, int NT) {
-    constexpr int TXC = NCELL / (BY * BZ), NOWN = BY * BZ;
-    const int nd = A.nd, ndp = nd + 1;
-    size_t tm = 2 * NCELL * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NCELL;
-    if (!FLAT) tm += NOWN * nd + 6 * NOWN * nd;
-    size_t smem = sizeof(TM) * tm + 16 + sizeof(double) * (8 * NCELL * 6 + NCELL) +
-                  sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NCELL);
-    auto kern = A.limiter == RT_LIM_MC ? k_stage<TS, TM, FLAT, BY, BZ, RT_LIM_MC> : k_stage<TS, TM, FLAT, BY, BZ, -1>;
+    constexpr int TXC = NC / (BY * BZ);
+    const size_t smem = stage_smem<TM, FLAT, BY, BZ, NC>(A.nd, NT);
+    auto kern = k_stage<TS, TM, FLAT, BY, BZ, -1, NC, MAXT>;
+    if constexpr (MAXT == MAXNT)
+        if (A.limiter == RT_LIM_MC) kern = k_stage<TS, TM, FLAT, BY, BZ, RT_LIM_MC, NC, MAXT>;
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nseg = (A.nx0 + TXC - 1) / TXC;
     size_t nblk = (size_t)nseg * (A.nx1 / BY) * (A.nx2 / BZ);
@@ -688,10 +702,20 @@ rt_status launch(rt_ctx *c, const StageArgs &A, int NT) {
 
 template <typename TS, typename TM, bool FLAT>
 rt_status launch_blk(rt_ctx *c, const StageArgs &A, int NT) {
+    if (NT > MAXNT) {
+        // finer grids (more than 256 directions): one direction per thread,
+        // up to 1024 threads, 1 x 1 bricks of 32, 16 or 8 cells as shared
+        // memory allows
+        if (stage_smem<TM, FLAT, 1, 1, 32>(A.nd, NT) <= SMEM_MAX) return launch<TS, TM, FLAT, 1, 1, 32, MAXNT_BIG>(c, A, NT);
+        if (stage_smem<TM, FLAT, 1, 1, 16>(A.nd, NT) <= SMEM_MAX) return launch<TS, TM, FLAT, 1, 1, 16, MAXNT_BIG>(c, A, NT);
+        if (stage_smem<TM, FLAT, 1, 1, 8>(A.nd, NT) <= SMEM_MAX) return launch<TS, TM, FLAT, 1, 1, 8, MAXNT_BIG>(c, A, NT);
+        c->err = "the stage kernel's shared memory cannot hold this many directions";
+        return RT_EINVAL;
+    }
     bool by = A.act1 && A.nx1 % 2 == 0, bz = A.act2 && A.nx2 % 2 == 0;
-    if (by && bz) return launch<TS, TM, FLAT, 2, 2>(c, A, NT);
-    if (by) return launch<TS, TM, FLAT, 2, 1>(c, A, NT);
-    return launch<TS, TM, FLAT, 1, 1>(c, A, NT);
+    if (by && bz) return launch<TS, TM, FLAT, 2, 2, NCELL, MAXNT>(c, A, NT);
+    if (by) return launch<TS, TM, FLAT, 2, 1, NCELL, MAXNT>(c, A, NT);
+    return launch<TS, TM, FLAT, 1, 1, NCELL, MAXNT>(c, A, NT);
 }
 
 }  // namespace
@@ -762,7 +786,7 @@ rt_status rt_launch_stage(rt_ctx *c, const void *Isrc, const void *Ibase, void *
     }
     int NT = ((c->nd + 31) / 32) * 32;
     if (NT < 64) NT = 64;
-    if (NT > MAXNT) { c->err = "more than 256 directions per cell are not supported by the stage kernel"; return RT_EINVAL; }
+    if (NT > MAXNT_BIG) { c->err = "more than 1024 directions per cell are not supported by the stage kernel"; return RT_EINVAL; }
     if (rt_stage_fast_ok(c)) return rt_launch_stage_fs(c, A, NT);
     if (f.precision == RT_FP64)
         return flat ? launch_blk<double, double, true>(c, A, NT) : launch_blk<double, double, false>(c, A, NT);

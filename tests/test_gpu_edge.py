@@ -75,12 +75,12 @@ def test_errors_at_the_boundary():
         st.step(1e-3, 1)                                                      # no fluid, no intensity
     with pytest.raises(rt.RTError):
         rt.Grid(3)                                                            # n must be a power of two
-    g8 = rt.Grid(8)                                                           # 642 directions
-    st8 = rt.RadiationStep(g8, box((4, 4, 4), n_geo=8, index=83)[0], precision="fp32")
-    cfg8, f8 = box((4, 4, 4), n_geo=8, index=83)
+    g16 = rt.Grid(16)                                                         # 2562 directions
+    cfg16, f16 = box((4, 4, 4), n_geo=16, index=83)
+    st16 = rt.RadiationStep(g16, cfg16, precision="fp32")
     dev = torch.device("cuda")
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
-    st8.set_fluid(T(f8["rho"]), T(f8["ug"]), T(f8["ucon"]), T(f8["kappa"]), T(f8["alpha_s"]), T(f8["eta"]))
-    st8.set_intensity(T(f8["I"]).float())
-    with pytest.raises(rt.RTError, match="256 directions"):
-        st8.step(1e-3, 1)                                                     # beyond the stage kernel's limit
+    st16.set_fluid(T(f16["rho"]), T(f16["ug"]), T(f16["ucon"]), T(f16["kappa"]), T(f16["alpha_s"]), T(f16["eta"]))
+    st16.set_intensity(T(f16["I"]).float())
+    with pytest.raises(rt.RTError, match="1024 directions"):
+        st16.step(1e-3, 1)                                                    # beyond the stage kernel's limit

@@ -1,0 +1,115 @@
+"""The finer geodesic grid G3 of section 3.3 (n = 8: 642 directions, the grid
+of the section 4.1 expansion test) on the CUDA path.  Beyond 256 directions
+the general stage kernel runs one direction per thread in CTAs of up to 1024
+threads with 1 x 1 bricks of 32, 16 or 8 cells (whatever shared memory
+holds), so these cases cover that launch shape on every precision and
+geometry: flat static and moving fluids, the Kerr-Schild torus (minimum-angle
+reconstruction and angular fluxes over the finer rings) and the cylindrical
+tetrad.  Bars as in the 162-direction parity tests: FP64 within 1e-11 of the
+FP64 oracle per intensity (floor 1e-6 of the largest), FP32 storage within
+1e-4 (floor 1e-3)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import oracle
+import closed_form_cases as CF
+import curvilinear_cases as CC
+from paper_2508_15532_b300 import workloads as W
+from helpers import rel_err, run_gpu, run_oracle
+from test_gpu_parity import small_flat
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+
+
+def test_g3_flat_static_fp64_fp32_bf16():
+    cfg, f = small_flat(nx=(10, 6, 4), n_geo=8, index=91)
+    assert f["I"].shape[1] == 642
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 3)
+    out = run_gpu(cfg, f, dt, 3, "fp64")
+    assert out["fails"] == 0
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert rel_err(out["ug"], ref["ug"]).max() < 1e-11
+    assert rel_err(out["E"], ref["E"]).max() < 1e-11
+    o32 = run_gpu(cfg, f, dt, 3, "fp32")
+    assert rel_err(o32["I"], ref["I"], 1e-3).max() < 1e-4
+    # BF16 storage: the input and the output of each of the 6 stages round to
+    # 2^-9 relative; the limited transport at most doubles an error it carries
+    o16 = run_gpu(cfg, f, dt, 3, "bf16")
+    assert rel_err(o16["I"], ref["I"], 1e-3).max() < 2 * (1 + 2 * 3) * 2.0 ** -9
+
+
+def test_g3_flat_moving_fluid():
+    cfg, f = small_flat(nx=(9, 6, 4), n_geo=8, index=92)
+    rng = np.random.Generator(np.random.PCG64(W.SEED0 + 192))
+    v = rng.uniform(-0.3, 0.3, (len(f["rho"]), 3))
+    gam = 1.0 / np.sqrt(1.0 - (v * v).sum(1))
+    f["ucon"] = np.concatenate([gam[:, None], gam[:, None] * v], axis=1)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 2)
+    out = run_gpu(cfg, f, dt, 2, "fp64")
+    assert out["fails"] == 0
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert rel_err(out["ug"], ref["ug"]).max() < 1e-11
+    assert np.abs(out["G"] - ref["G"]).max() < 1e-9 * np.abs(ref["G"]).max()
+    o32 = run_gpu(cfg, f, dt, 2, "fp32")
+    assert rel_err(o32["I"], ref["I"], 1e-3).max() < 1e-4
+
+
+def test_g3_kerr_fp64():
+    """The torus workload's recipe on a 12 x 8 x 4 Kerr-Schild box with pole
+    boundaries: geometry tables, n_0 masks, the minimum-angle reconstruction
+    and the angular edge fluxes at 642 directions (rings of 5 and 6)."""
+    cfg, f = W.kerr(nr=12, nth=8, nph=4, n_geo=8, index=93)
+    dt = oracle.Oracle(cfg).cfl_dt(0.4)
+    ref = run_oracle(cfg, f, dt, 2)
+    out = run_gpu(cfg, f, dt, 2, "fp64")
+    assert out["fails"] == 0
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    assert rel_err(out["ug"], ref["ug"]).max() < 1e-11
+    assert rel_err(out["R"], ref["R"], 1e-6).max() < 1e-10
+
+
+def test_g3_cylindrical_tetrad_uniform_field():
+    """A uniform isotropic field under the cylindrical tetrad (section 4.5):
+    the CUDA path equals the oracle at 642 directions, and its one-step
+    departure from uniformity (angular truncation) is smaller than at 162."""
+    res = []
+    for n_geo in (4, 8):
+        cfg, f, dt, n, _ = CC.cylinder(N=(16, 16), n_geo=n_geo)
+        cfg = dict(cfg, order=1)
+        nd = 10 * n_geo * n_geo + 2
+        f = dict(f, I=np.ones((16 * 16, nd)))
+        dt1 = oracle.Oracle(cfg).cfl_dt(0.1)
+        out = run_gpu(cfg, f, dt1, 1, "fp64")
+        if n_geo == 8:
+            ref = run_oracle(cfg, f, dt1, 1)
+            assert rel_err(out["I"], ref["I"]).max() < 1e-11
+        R = np.abs(out["I"] - 1.0).reshape(16, 16, nd)[2:-2, 2:-2] / dt1
+        res.append(R.mean())
+    assert res[1] < res[0] < 6e-3
+
+
+def test_g3_spherical_front():
+    """Section 4.1 on its own grid G3: the oracle and the CUDA path agree on a
+    12^3 box, and on the 24^3 box the CUDA path's energy-weighted mean
+    radius is within half a cell of t = 0.6 (FP64 and FP32)."""
+    cfg, f, dt, n, x = CF.expansion(N=12, n_geo=8, t_end=0.3)
+    ref = run_oracle(cfg, f, dt, n)
+    out = run_gpu(cfg, f, dt, n, "fp64")
+    assert rel_err(out["I"], ref["I"]).max() < 1e-11
+    o32 = run_gpu(cfg, f, dt, n, "fp32")
+    assert rel_err(o32["I"], ref["I"], 1e-3).max() < 1e-4
+    cfg, f, dt, n, x = CF.expansion(N=24, n_geo=8, t_end=0.6)
+    w = oracle.Oracle(dict(cfg, nx=(2, 2, 2))).grid()["w"]
+    for prec in ("fp64", "fp32"):
+        out = run_gpu(cfg, f, dt, n, prec)
+        assert abs(CF.mean_radius(out["I"] @ w, x) - 0.6) < 0.5 * cfg["dx"][0], prec
+
