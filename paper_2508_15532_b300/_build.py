@@ -12,6 +12,12 @@ CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["grid.cu", "geometry.cu", "stage.cu", "stage_flat.cu", "moments.cu", "adjoint.cu", "api.cu"]
 LIB = os.path.join(HERE, "librt_b300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# stage.cu holds the general stage kernel, instantiated for several brick
+# shapes; the compiler's choice of which multiply-adds to fuse differs between
+# instances, so with contraction the results would depend on the brick shape
+# (and an x3 slab, whose brick may differ from the whole box's, would not
+# reproduce the whole box bit for bit).  Its fused multiply-adds are explicit.
+EXTRA = {"stage.cu": ["-fmad=false"]}
 
 
 def _deps():
@@ -38,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 and os.path.getmtime(o) >= max(os.path.getmtime(src), newest_header)):
             continue
         cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-rdc=false",
-               "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, s), "-o", o]
+               *EXTRA.get(s, []), "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, s), "-o", o]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT), s))

@@ -35,10 +35,11 @@ using namespace rtk;
 // LK: the limiter kind fixed at compile time (RT_LIM_MC), or -1 to read it
 // from the arguments.  NC: cells per CTA (32; 16 or 8 where the directions'
 // shared-memory rows of 32 cells would not fit).  MAXT: the launch bound, 256
-// threads (up to 256 directions, one per thread) or 1024 (finer grids, at
-// most 64 registers per thread)
-template <typename TS, typename TM, bool FLAT, int BY, int BZ, int LK, int NC, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
+// threads (up to 256 directions, one per thread), 192 (curved geometry: up
+// to 192 directions) or 1024 (finer grids, at most 64 registers per thread).
+// MINB: CTAs per SM the registers must allow
+template <typename TS, typename TM, bool FLAT, int BY, int BZ, int LK, int NC, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
     constexpr int TXC = NC / (BY * BZ);
     constexpr int NOWN = BY * BZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                 TM sm1 = limiter<TM>(LK >= 0 ? LK : A.limiter, I0 - Im1, Im1 - Im2);
                 TM s0 = limiter<TM>(LK >= 0 ? LK : A.limiter, I1 - I0, I0 - Im1);
                 const TM *rc = recX + (o * (TXC + 1)) * 5;
-                TM IL = Im1 + TM(0.5) * sm1, IR = I0 - TM(0.5) * s0;
+                TM IL = fma(TM(0.5), sm1, Im1), IR = fma(TM(-0.5), s0, I0);
                 TM phi;
                 if (FLAT) phi = face_phi<TM>(nh[0], rc, IL, IR, Im1, I0);
                 else {
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                         TM I2 = ld_x(rb, xmap[ii + 4], jr);
                         TM s1 = limiter<TM>(LK >= 0 ? LK : A.limiter, I2 - W1[o], W1[o] - W0[o]);
                         const TM *rc = recX + (o * (TXC + 1) + ii + 1) * 5;
-                        TM IL = W0[o] + TM(0.5) * S0[o], IR = W1[o] - TM(0.5) * s1;
+                        TM IL = fma(TM(0.5), S0[o], W0[o]), IR = fma(TM(-0.5), s1, W1[o]);
                         TM phi;
                         if (FLAT) phi = face_phi<TM>(nh[0], rc, IL, IR, W0[o], W1[o]);
                         else {
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                             geo_face(0, p1, p1 - 1, p1, n, P);
                             phi = P * face_phi<TM>(n, rc, IL, IR, W0[o], W1[o]);
                         }
-                        acc[o] += FLAT ? cdx[0] * (phi - Flo[o]) : (phi - Flo[o]);
+                        acc[o] = FLAT ? fma(cdx[0], phi - Flo[o], acc[o]) : acc[o] + (phi - Flo[o]);
                         Flo[o] = phi; W0[o] = W1[o]; W1[o] = I2; S0[o] = s1;
                     }
                 }
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
 #pragma unroll
                         for (int f = 0; f <= BY; ++f) {
                             const TM *rc = recY + ((r * (BY + 1) + f) * TXC + ii) * 5;
-                            TM IL = Y[f + 1] + TM(0.5) * sy[f + 1], IR = Y[f + 2] - TM(0.5) * sy[f + 2];
+                            TM IL = fma(TM(0.5), sy[f + 1], Y[f + 1]), IR = fma(TM(-0.5), sy[f + 2], Y[f + 2]);
                             if (FLAT) F[f] = face_phi<TM>(nh[1], rc, IL, IR, Y[f + 1], Y[f + 2]);
                             else {
                                 TM n, P;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                             }
                         }
 #pragma unroll
-                        for (int q = 0; q < BY; ++q) acc[r * BY + q] += FLAT ? cdx[1] * (F[q + 1] - F[q]) : (F[q + 1] - F[q]);
+                        for (int q = 0; q < BY; ++q) acc[r * BY + q] = FLAT ? fma(cdx[1], F[q + 1] - F[q], acc[r * BY + q]) : acc[r * BY + q] + (F[q + 1] - F[q]);
                     }
                 }
                 if (A.act2) {
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
 #pragma unroll
                         for (int f = 0; f <= BZ; ++f) {
                             const TM *rc = recZ + ((q * (BZ + 1) + f) * TXC + ii) * 5;
-                            TM IL = Z[f + 1] + TM(0.5) * sz[f + 1], IR = Z[f + 2] - TM(0.5) * sz[f + 2];
+                            TM IL = fma(TM(0.5), sz[f + 1], Z[f + 1]), IR = fma(TM(-0.5), sz[f + 2], Z[f + 2]);
                             if (FLAT) F[f] = face_phi<TM>(nh[2], rc, IL, IR, Z[f + 1], Z[f + 2]);
                             else {
                                 TM n, P;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                             }
                         }
 #pragma unroll
-                        for (int r = 0; r < BZ; ++r) acc[r * BY + q] += FLAT ? cdx[2] * (F[r + 1] - F[r]) : (F[r + 1] - F[r]);
+                        for (int r = 0; r < BZ; ++r) acc[r * BY + q] = FLAT ? fma(cdx[2], F[r + 1] - F[r], acc[r * BY + q]) : acc[r * BY + q] + (F[r + 1] - F[r]);
                     }
                 }
             }
@@ -327,9 +328,9 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
 #pragma unroll
                             for (int q = 0; q < RT_MAXNB; ++q) {
                                 const TM d1 = q + 1 < rg_kk ? dI[q + 1] : dI[0];
-                                al[q] = rg_g[3 * q] * dI[q] + rg_g[3 * q + 1] * d1;
-                                be[q] = rg_g[3 * q + 1] * dI[q] + rg_g[3 * q + 2] * d1;
-                                nr[q] = al[q] * dI[q] + be[q] * d1;
+                                al[q] = fma(rg_g[3 * q], dI[q], rg_g[3 * q + 1] * d1);
+                                be[q] = fma(rg_g[3 * q + 1], dI[q], rg_g[3 * q + 2] * d1);
+                                nr[q] = fma(al[q], dI[q], be[q] * d1);
                                 if (q < rg_kk && (q == 0 || nr[q] < mn)) mn = nr[q];
                             }
                             // near-equal norms tie (mirror-symmetric neighbourhoods); first in ring order wins
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                             const size_t od = (size_t)(6 * s + best) * 12;
 #pragma unroll
                             for (int q = 0; q < RT_MAXNB; ++q)
-                                rec[q] = Io0 + ab * ldT<TM>(A.mdT, od + 2 * q) + bb * ldT<TM>(A.mdT, od + 2 * q + 1);
+                                rec[q] = fma(bb, ldT<TM>(A.mdT, od + 2 * q + 1), fma(ab, ldT<TM>(A.mdT, od + 2 * q), Io0));
                         }
 #pragma unroll
                         for (int q = 0; q < RT_MAXNB; ++q)
@@ -355,6 +356,24 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                 }
                 __syncthreads();
                 if (act) {
+                    // eq. angular_fluxes: the flux through edge q is w_q times the
+                    // upwind reconstruction, the side given by the sign of v.u_e
+                    // (w = dlam n_0 v.u_e, eneg: u_e reversed).  With BY = 1 every
+                    // own row lies on the same (x1, x2) point, whose edge weights
+                    // and upwind sides are loaded once for all rows
+                    TM ewq[RT_MAXNB];
+                    unsigned upq = 0u;
+#pragma unroll
+                    for (int q = 0; q < RT_MAXNB; ++q) ewq[q] = TM(0);
+                    if constexpr (BY == 1) {
+                        const size_t pe0 = (size_t)((j0 + A.ng1) * A.gn0 + (i + A.ng0)) * A.ne;
+#pragma unroll
+                        for (int q = 0; q < RT_MAXNB; ++q)
+                            if (q < rg_kk) {
+                                ewq[q] = ldT<TM>(A.ew, pe0 + rg_e[q]);
+                                upq |= (unsigned)((ewq[q] > TM(0)) != (__ldg(A.eneg + pe0 + rg_e[q]) != 0)) << q;
+                            }
+                    }
 #pragma unroll 1
                     for (int o = 0; o < NOWN; ++o) {
                         const int pc = (j0 + o % BY + A.ng1) * A.gn0 + (i + A.ng0);
@@ -363,13 +382,19 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                         for (int q = 0; q < RT_MAXNB; ++q) {
                             if (q < rg_kk) {
                                 const bool own = (rg_own >> q) & 1u;
-                                const size_t pe = (size_t)pc * A.ne + rg_e[q];
-                                TM w = ldT<TM>(A.ew, pe);
+                                TM w;
+                                bool up;
+                                if constexpr (BY == 1) {
+                                    w = ewq[q];
+                                    up = (upq >> q) & 1u;
+                                } else {
+                                    const size_t pe = (size_t)pc * A.ne + rg_e[q];
+                                    w = ldT<TM>(A.ew, pe);
+                                    up = (w > TM(0)) != (__ldg(A.eneg + pe) != 0);
+                                }
                                 TM Io = Arec[(o * nd + s) * 6 + q], It2 = Arec[(o * nd + rg_nb[q]) * 6 + rg_bk[q]];
                                 TM IL = own ? Io : It2, IR = own ? It2 : Io;
-                                // eq. angular_fluxes: upwind by the sign of v.u_e (w = dlam n_0 v.u_e)
-                                TM F = w * (((w > TM(0)) != (__ldg(A.eneg + pe) != 0)) ? IL : IR);
-                                a += own ? F : -F;
+                                a = fma(own ? w : -w, up ? IL : IR, a);
                             }
                         }
 #pragma unroll
@@ -392,7 +417,7 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                         const int pc = (j + A.ng1) * A.gn0 + (i + A.ng0);
                         TM U = ldT<TM>(A.cenU, (size_t)pc * nd + s);
                         TM V = (TM)A.pt_V[pc];
-                        out = (U * Ib - dtk * (acc[o] / V + ang[o])) / U;
+                        out = fma(U, Ib, -dtk * (acc[o] / V + ang[o])) / U;
                         zero = zero || (A.mask[(size_t)pc * nd + s] & 1);
                     }
                     It[((r * BY + q) * TXC + ii) * ndp + s] = zero ? TM(0) : out;
@@ -469,8 +494,8 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                 TM t;
                 if (all_static) t = row[d] * w;
                 else {
-                    TM D = TM(1) + (u0m - (u1 * ldT<TM>(A.dirT, 3 * d) + u2 * ldT<TM>(A.dirT, 3 * d + 1) +
-                                           u3 * ldT<TM>(A.dirT, 3 * d + 2)));
+                    TM D = TM(1) + (u0m - fma(u1, ldT<TM>(A.dirT, 3 * d),
+                                              fma(u2, ldT<TM>(A.dirT, 3 * d + 1), u3 * ldT<TM>(A.dirT, 3 * d + 2))));
                     t = D * D * row[d] * w;
                     if constexpr (sizeof(TM) == 4) {
                         // rq = n^0 / (n^0 + D alpha dt), K = (alpha dt / n^0) rq; the
@@ -479,11 +504,11 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
                         // whose leading sum is per-cell FP64 (wbar): B2 then
                         // carries no FP32 rounding that the solve's cancellation
                         // alpha dt - B2 alpha^s would magnify
-                        const TM iD = dv<TM>(TM(1), D), rq = dv<TM>(n0, n0 + D * adt);
+                        const TM iD = dv<TM>(TM(1), D), rq = dv<TM>(n0, fma(D, adt, n0));
                         kadd(B1, cB1, n0 * (kn * rq) * t);
                         kadd(B2, cB2, w * iD * iD * rq);
                     } else {
-                        TM K = dv<TM>(adt, n0 + D * adt);
+                        TM K = dv<TM>(adt, fma(D, adt, n0));
                         kadd(B1, cB1, n0 * K * t);
                         kadd(B2, cB2, dv<TM>(K * w, D));
                     }
@@ -579,9 +604,9 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
             if (scOn[lc]) {
                 if (all_static) v = (v + scEm[lc]) / (TM(1) + scA[lc]);
                 else {
-                    TM D = TM(1) + (scU[4 * lc] - (scU[4 * lc + 1] * nh[0] + scU[4 * lc + 2] * nh[1] + scU[4 * lc + 3] * nh[2]));
+                    TM D = TM(1) + (scU[4 * lc] - fma(scU[4 * lc + 1], nh[0], fma(scU[4 * lc + 2], nh[1], scU[4 * lc + 3] * nh[2])));
                     TM n0 = scN0[lc];
-                    v = dv<TM>(n0 * v + dv<TM>(scEm[lc], D * D * D), n0 + D * scA[lc]);
+                    v = dv<TM>(fma(n0, v, dv<TM>(scEm[lc], D * D * D)), fma(D, scA[lc], n0));
                 }
                 bool zero = A.n_pole_zero > 0 && (j < A.n_pole_zero || j >= A.nx1 - A.n_pole_zero);
                 if (!FLAT) zero = zero || (A.mask[(size_t)((j + A.ng1) * A.gn0 + (i0 + ii + A.ng0)) * nd + s] & 1);
@@ -601,12 +626,12 @@ __global__ void __launch_bounds__(MAXT) k_stage(const StageArgs A) {
             for (int d = g; d < nd; d += nchunk) {
                 TM w = ldT<TM>(A.wT, d);
                 TM x = ldT<TM>(A.dirT, 3 * d), y = ldT<TM>(A.dirT, 3 * d + 1), z = ldT<TM>(A.dirT, 3 * d + 2);
-                TM D = all_static ? TM(1) : TM(1) + (u0m - (u1 * x + u2 * y + u3 * z));
+                TM D = all_static ? TM(1) : TM(1) + (u0m - fma(u1, x, fma(u2, y, u3 * z)));
                 TM t = D * D * rp[d] * w;
                 TM yk = t - cEp, tk = Ep + yk;
                 cEp = (tk - Ep) - yk; Ep = tk;
                 TM dI = (rp[d] - rt[d]) * w;
-                r0 += dI; r1 += x * dI; r2 += y * dI; r3 += z * dI;
+                r0 += dI; r1 = fma(x, dI, r1); r2 = fma(y, dI, r2); r3 = fma(z, dI, r3);
             }
         }
         double *pp = part + (g * NC + c) * 6;
@@ -685,13 +710,13 @@ size_t stage_smem(int nd, int NT) {
            sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NC);
 }
 
-template <typename TS, typename TM, bool FLAT, int BY, int BZ, int NC, int MAXT>
+template <typename TS, typename TM, bool FLAT, int BY, int BZ, int NC, int MAXT, int MINB = 1>
 rt_status launch(rt_ctx *c, const StageArgs &A, int NT) {
     constexpr int TXC = NC / (BY * BZ);
     const size_t smem = stage_smem<TM, FLAT, BY, BZ, NC>(A.nd, NT);
-    auto kern = k_stage<TS, TM, FLAT, BY, BZ, -1, NC, MAXT>;
-    if constexpr (MAXT == MAXNT)
-        if (A.limiter == RT_LIM_MC) kern = k_stage<TS, TM, FLAT, BY, BZ, RT_LIM_MC, NC, MAXT>;
+    auto kern = k_stage<TS, TM, FLAT, BY, BZ, -1, NC, MAXT, MINB>;
+    if constexpr (MAXT <= MAXNT)
+        if (A.limiter == RT_LIM_MC) kern = k_stage<TS, TM, FLAT, BY, BZ, RT_LIM_MC, NC, MAXT, MINB>;
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nseg = (A.nx0 + TXC - 1) / TXC;
     size_t nblk = (size_t)nseg * (A.nx1 / BY) * (A.nx2 / BZ);
@@ -713,6 +738,20 @@ rt_status launch_blk(rt_ctx *c, const StageArgs &A, int NT) {
         return RT_EINVAL;
     }
     bool by = A.act1 && A.nx1 % 2 == 0, bz = A.act2 && A.nx2 % 2 == 0;
+    if constexpr (!FLAT) {
+        // curved geometry: the tables do not depend on x3 (phi), so 8 x 1 x 4
+        // bricks, whose four rows share every table entry, beat 8 x 2 x 2
+        // bricks (measured 96.0 against 110.9 ms per 256 x 128 x 128 torus
+        // step); the kernel is latency-bound, and three CTAs of 192 threads
+        // per SM (96 registers) take it to 83.8 ms
+        constexpr int MB = sizeof(TM) == 4 ? CURV_MINB : 1;   // FP64: shared memory allows one CTA
+        if (NT <= CURV_NT) {
+            if (A.act2 && A.nx2 % 4 == 0) return launch<TS, TM, FLAT, 1, 4, NCELL, CURV_NT, MB>(c, A, NT);
+            if (by && bz) return launch<TS, TM, FLAT, 2, 2, NCELL, CURV_NT, MB>(c, A, NT);
+            if (by) return launch<TS, TM, FLAT, 2, 1, NCELL, CURV_NT, MB>(c, A, NT);
+            return launch<TS, TM, FLAT, 1, 1, NCELL, CURV_NT, MB>(c, A, NT);
+        }
+    }
     if (by && bz) return launch<TS, TM, FLAT, 2, 2, NCELL, MAXNT>(c, A, NT);
     if (by) return launch<TS, TM, FLAT, 2, 1, NCELL, MAXNT>(c, A, NT);
     return launch<TS, TM, FLAT, 1, 1, NCELL, MAXNT>(c, A, NT);

@@ -8,6 +8,7 @@ namespace rtk {
 constexpr int NCELL = 32;    // cells per CTA
 constexpr int MAXNT = 256;
 constexpr int MAXNT_BIG = 1024;     // general stage kernel on finer grids: one direction per thread
+constexpr int CURV_NT = 192, CURV_MINB = 3;   // general stage kernel, curved geometry, up to 192 directions
 constexpr size_t SMEM_MAX = 227 * 1024;   // shared memory of one CTA (opt-in maximum)
 constexpr double FOURPI = 12.566370614359172953850573533118;
 constexpr int F_MIR = 1 << 29, F_FIX = 1 << 30, F_MASK = (1 << 29) - 1;
@@ -95,7 +96,10 @@ template <typename TM>
 __device__ __forceinline__ TM face_phi(TM n, const TM *rec, TM IL, TM IR, TM Il, TM Ir) {
     TM cL = n > TM(0) ? rec[0] : rec[1];
     TM cR = n > TM(0) ? rec[1] : rec[0];
-    return n * (cL * IL + cR * IR) - fabs(n) * rec[2] * (Ir - Il) + rec[3] * IL + rec[4] * IR;
+    // explicit multiply-adds: the general kernel's file is compiled without
+    // contraction, so that every brick shape rounds alike
+    const TM a = fma(cL, IL, cR * IR), b = fma(rec[3], IL, rec[4] * IR);
+    return fma(n, a, fma(-fabs(n) * rec[2], Ir - Il, b));
 }
 
 // boundary resolution of one index along one axis (setup only)

@@ -78,13 +78,15 @@ def test_tangential_beam_straight():
     assert cerr(outs["fp64"]["I"]) < 0.15
 
 
-def test_photon_orbit_bump_turns():
+@pytest.mark.parametrize("n_geo", [4, 8])
+def test_photon_orbit_bump_turns(n_geo):
     """Section 4.7: the tangential photon's direction bump turns inward just
-    inside the prograde photon orbit of a = 0.5 and outward just outside it."""
+    inside the prograde photon orbit of a = 0.5 and outward just outside it
+    (162 directions, and the section's own 642)."""
     r1 = AC.photon_orbit_radius(0.5)
     turn = {}
     for fr in (0.95, 1.0, 1.05):
-        cfg, f, dt, n, vr = AC.orbit_bump(fr * r1)
+        cfg, f, dt, n, vr = AC.orbit_bump(fr * r1, n_geo=n_geo)
         ref, outs = both(cfg, f, dt, n, ("fp64", "fp32"))
         w = oracle.Oracle(cfg).grid()["w"]
         turn[fr] = AC.mean_vr(outs["fp64"]["I"], w, vr) - AC.mean_vr(f["I"], w, vr)
