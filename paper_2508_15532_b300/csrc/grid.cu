@@ -130,8 +130,9 @@ __global__ void k_mapr_dots(int nd, const int *__restrict__ nnb, const double *_
         d0 = x0[0] * xm[0] + x0[1] * xm[1] + x0[2] * xm[2];
         d1 = x1[0] * xm[0] + x1[1] * xm[1] + x1[2] * xm[2];
     }
-    md[2 * (size_t)t] = d0;
-    md[2 * (size_t)t + 1] = d1;
+    const size_t o = ((size_t)(b * 6 + q) * nd + s) * 2;
+    md[o] = d0;
+    md[o + 1] = d1;
 }
 
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, size_t n) {

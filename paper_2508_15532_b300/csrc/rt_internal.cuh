@@ -31,9 +31,10 @@ struct rt_grid {
     double *mx = nullptr;        // [nd*6*3] gnomonic image of neighbour q in the tangent plane of s
     double *mg = nullptr;        // [nd*6*3] inverse Gram matrix (a, b, c) of the pair (q, q+1)
     double *mm = nullptr;        // [nd*6*3] gnomonic image of the midpoint of edge q
-    // md[((s*6 + b)*6 + q)*2 + {0,1}] = mx(s, b).mm(s, q), mx(s, b+1).mm(s, q):
-    // the reconstruction weights of edge midpoint q for the plane of pair b
-    double *md = nullptr;        // [nd*6*6*2]
+    // md[((b*6 + q)*nd + s)*2 + {0,1}] = mx(s, b).mm(s, q), mx(s, b+1).mm(s, q):
+    // the reconstruction weights of edge midpoint q for the plane of pair b;
+    // direction-fastest, so that a warp's lookups for one plane coalesce
+    double *md = nullptr;        // [6*6*nd*2]
     float *dirf = nullptr, *wf = nullptr, *mxf = nullptr, *mgf = nullptr, *mmf = nullptr, *mdf = nullptr;
 };
 

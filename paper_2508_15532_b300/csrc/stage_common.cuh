@@ -76,6 +76,15 @@ template <> struct IO<__nv_bfloat16, float> {
 };
 
 template <typename TM> __device__ __forceinline__ TM ldT(const void *p, size_t i) { return __ldg((const TM *)p + i); }
+// elements 2i and 2i + 1 in one load
+__device__ __forceinline__ void ldT2(const void *p, size_t i, float &a, float &b) {
+    const float2 v = __ldg((const float2 *)p + i);
+    a = v.x; b = v.y;
+}
+__device__ __forceinline__ void ldT2(const void *p, size_t i, double &a, double &b) {
+    const double2 v = __ldg((const double2 *)p + i);
+    a = v.x; b = v.y;
+}
 
 template <typename TM> __device__ __forceinline__ TM dv(TM a, TM b);
 template <> __device__ __forceinline__ float dv<float>(float a, float b) { return __fdividef(a, b); }
