@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
     TM *scU = recZ + BY * (BZ + 1) * TXC * 5;                 // [NC][4] tetrad-frame fluid velocity
     TM *scN0 = scU + 4 * NC, *scK = scN0 + NC, *scEm = scK + NC, *scA = scEm + NC;
     TM *Icell = scA + NC;                                     // [NOWN][nd]   (curved only)
-    TM *Arec = Icell + (FLAT ? 0 : NOWN * nd);                // [NOWN][nd][6] (curved only)
+    TM *Arec = Icell + (FLAT ? 0 : NOWN * nd);                // [NOWN][6][nd] (curved only; slot-major: own slots conflict-free)
     double *part = (double *)(((uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)) + 15) & ~(uintptr_t)15);  // [NT / NC][NC][6]
     double *sc64 = part + NT * 6;                             // [NC]: E-bar_-
     int *xmap = (int *)(sc64 + NC);                           // [TXC+4]
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                         }
 #pragma unroll
                         for (int q = 0; q < RT_MAXNB; ++q)
-                            if (q < rg_kk) Arec[(o * nd + s) * 6 + q] = rec[q];
+                            if (q < rg_kk) Arec[(o * 6 + q) * nd + s] = rec[q];
                     }
                 }
                 __syncthreads();
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                                     w = ldT<TM>(A.ew, pe);
                                     up = (w > TM(0)) != (__ldg(A.eneg + pe) != 0);
                                 }
-                                TM Io = Arec[(o * nd + s) * 6 + q], It2 = Arec[(o * nd + rg_nb[q]) * 6 + rg_bk[q]];
+                                TM Io = Arec[(o * 6 + q) * nd + s], It2 = Arec[(o * 6 + rg_bk[q]) * nd + rg_nb[q]];
                                 TM IL = own ? Io : It2, IR = own ? It2 : Io;
                                 a = fma(own ? w : -w, up ? IL : IR, a);
                             }
