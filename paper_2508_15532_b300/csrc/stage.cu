@@ -212,6 +212,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                     for (int m = 0; m < 3; ++m) rg_g[3 * q + m] = ldT<TM>(A.mgT, (size_t)(6 * s + q) * 3 + m);
                 }
             }
+            if (rg_kk == 5) {
+                // a pentagon's ring is padded to six: neighbour 5 repeats
+                // neighbour 0 (so plane 4 pairs neighbours 4 and 0 like the
+                // others pair q and q + 1), and plane 5, which would pair 0 with
+                // itself, gets a NaN Gram inverse: its norm is NaN, never below
+                // the threshold, and drops out of the minimum (fmin ignores NaN)
+                rg_nb[5] = rg_nb[0];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) rg_g[15 + m] = qnan<TM>();
+            }
         }
         for (int ii = 0; ii < nc; ++ii) {
             const int i = i0 + ii;
@@ -323,26 +333,24 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                         } else {
                             TM dI[RT_MAXNB], al[RT_MAXNB], be[RT_MAXNB], nr[RT_MAXNB];
 #pragma unroll
-                            for (int q = 0; q < RT_MAXNB; ++q) dI[q] = q < rg_kk ? Icell[o * nd + rg_nb[q]] - Io0 : TM(0);
-                            TM mn = TM(0);
+                            for (int q = 0; q < RT_MAXNB; ++q) dI[q] = Icell[o * nd + rg_nb[q]] - Io0;
 #pragma unroll
                             for (int q = 0; q < RT_MAXNB; ++q) {
-                                const TM d1 = q + 1 < rg_kk ? dI[q + 1] : dI[0];
+                                const TM d1 = dI[q + 1 < RT_MAXNB ? q + 1 : 0];
                                 al[q] = fma(rg_g[3 * q], dI[q], rg_g[3 * q + 1] * d1);
                                 be[q] = fma(rg_g[3 * q + 1], dI[q], rg_g[3 * q + 2] * d1);
                                 nr[q] = fma(al[q], dI[q], be[q] * d1);
-                                if (q < rg_kk && (q == 0 || nr[q] < mn)) mn = nr[q];
                             }
+                            TM mn = nr[0];
+#pragma unroll
+                            for (int q = 1; q < RT_MAXNB; ++q) mn = fmin(mn, nr[q]);
                             // near-equal norms tie (mirror-symmetric neighbourhoods); first in ring order wins
                             const TM thr = mn + TM(1e-6) * fabs(mn);
-                            int best = rg_kk - 1;
-#pragma unroll
-                            for (int q = RT_MAXNB - 1; q >= 0; --q)
-                                if (q < rg_kk && nr[q] <= thr) best = q;
+                            int best = 0;
                             TM ab = TM(0), bb = TM(0);
 #pragma unroll
-                            for (int q = 0; q < RT_MAXNB; ++q)
-                                if (q == best) { ab = al[q]; bb = be[q]; }
+                            for (int q = RT_MAXNB - 1; q >= 0; --q)
+                                if (nr[q] <= thr) { best = q; ab = al[q]; bb = be[q]; }
                             // precomputed dot products of the plane's dual basis with the
                             // edge midpoints (plane-major, direction-fastest: coalesced;
                             // measured 82.6 -> 76.2 ms per 256 x 128 x 128 torus step)
@@ -355,8 +363,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                             }
                         }
 #pragma unroll
-                        for (int q = 0; q < RT_MAXNB; ++q)
-                            if (q < rg_kk) Arec[(o * 6 + q) * nd + s] = rec[q];
+                        for (int q = 0; q < RT_MAXNB; ++q) Arec[(o * 6 + q) * nd + s] = rec[q];
                     }
                 }
                 __syncthreads();
@@ -371,12 +378,18 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
 #pragma unroll
                     for (int q = 0; q < RT_MAXNB; ++q) ewq[q] = TM(0);
                     if constexpr (BY == 1) {
+                        // folded per ring slot: the signed weight (+w on the edge's
+                        // own side) and whether the upwind value is s's own; a
+                        // pentagon's padding slot keeps weight 0
                         const size_t pe0 = (size_t)((j0 + A.ng1) * A.gn0 + (i + A.ng0)) * A.ne;
 #pragma unroll
                         for (int q = 0; q < RT_MAXNB; ++q)
                             if (q < rg_kk) {
-                                ewq[q] = ldT<TM>(A.ew, pe0 + rg_e[q]);
-                                upq |= (unsigned)((ewq[q] > TM(0)) != (__ldg(A.eneg + pe0 + rg_e[q]) != 0)) << q;
+                                const TM w = ldT<TM>(A.ew, pe0 + rg_e[q]);
+                                const bool own = (rg_own >> q) & 1u;
+                                const bool up = (w > TM(0)) != (__ldg(A.eneg + pe0 + rg_e[q]) != 0);
+                                ewq[q] = own ? w : -w;
+                                upq |= (unsigned)(own == up) << q;
                             }
                     }
 #pragma unroll 1
@@ -385,21 +398,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                         TM a = TM(0);
 #pragma unroll
                         for (int q = 0; q < RT_MAXNB; ++q) {
-                            if (q < rg_kk) {
-                                const bool own = (rg_own >> q) & 1u;
-                                TM w;
-                                bool up;
+                            // with BY = 1 a pentagon's padding slot has weight 0 and
+                            // reads valid slots (neighbour 0's slot 0)
+                            if (BY == 1 || q < rg_kk) {
+                                const TM Io = Arec[(o * 6 + q) * nd + s], It2 = Arec[(o * 6 + rg_bk[q]) * nd + rg_nb[q]];
                                 if constexpr (BY == 1) {
-                                    w = ewq[q];
-                                    up = (upq >> q) & 1u;
+                                    a = fma(ewq[q], ((upq >> q) & 1u) ? Io : It2, a);
                                 } else {
+                                    const bool own = (rg_own >> q) & 1u;
                                     const size_t pe = (size_t)pc * A.ne + rg_e[q];
-                                    w = ldT<TM>(A.ew, pe);
-                                    up = (w > TM(0)) != (__ldg(A.eneg + pe) != 0);
+                                    const TM w = ldT<TM>(A.ew, pe);
+                                    const bool up = (w > TM(0)) != (__ldg(A.eneg + pe) != 0);
+                                    TM IL = own ? Io : It2, IR = own ? It2 : Io;
+                                    a = fma(own ? w : -w, up ? IL : IR, a);
                                 }
-                                TM Io = Arec[(o * 6 + q) * nd + s], It2 = Arec[(o * 6 + rg_bk[q]) * nd + rg_nb[q]];
-                                TM IL = own ? Io : It2, IR = own ? It2 : Io;
-                                a = fma(own ? w : -w, up ? IL : IR, a);
                             }
                         }
 #pragma unroll

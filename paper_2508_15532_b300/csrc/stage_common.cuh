@@ -76,6 +76,9 @@ template <> struct IO<__nv_bfloat16, float> {
 };
 
 template <typename TM> __device__ __forceinline__ TM ldT(const void *p, size_t i) { return __ldg((const TM *)p + i); }
+template <typename TM> __device__ __forceinline__ TM qnan();
+template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
 // elements 2i and 2i + 1 in one load
 __device__ __forceinline__ void ldT2(const void *p, size_t i, float &a, float &b) {
     const float2 v = __ldg((const float2 *)p + i);
