@@ -432,9 +432,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                     if (FLAT) out = Ib - acc[o];
                     else {
                         const int pc = (j + A.ng1) * A.gn0 + (i + A.ng0);
-                        TM U = ldT<TM>(A.cenU, (size_t)pc * nd + s);
-                        TM V = (TM)A.pt_V[pc];
-                        out = fma(U, Ib, -dtk * (acc[o] / V + ang[o])) / U;
+                        // (U Ib - dt (acc / V + ang)) / U with the reciprocals of the
+                        // point's U = n^0 n_0 and volume V, which the own rows on one
+                        // (x1, x2) point share (evaluated once per point)
+                        const TM iU = TM(1) / ldT<TM>(A.cenU, (size_t)pc * nd + s);
+                        const TM iV = TM(1) / (TM)A.pt_V[pc];
+                        out = Ib - dtk * fma(acc[o], iV, ang[o]) * iU;
                         zero = zero || (A.mask[(size_t)pc * nd + s] & 1);
                     }
                     It[((r * BY + q) * TXC + ii) * ndp + s] = zero ? TM(0) : out;

