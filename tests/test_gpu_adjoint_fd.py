@@ -17,10 +17,18 @@ h = 1e-4 has 100 times less noise and a truncation error of ~h^2 = 1e-8, so
 the 1e-5 bar is held there, on all 32 samples; h = 1e-6 is run on the first
 8 samples and held to 1e-3.
 
+The quotient's noise is absolute, not relative to the component: over the
+32 eta samples the spread between the quotients at h = 1e-4, 3e-5 and 1e-5
+puts it at 1.1e-8 (median) to 4.5e-8 (largest) at h = 1e-4, about 2e-7 of
+the largest gradient, and the gradients' absolute errors measure the same
+(median 1.7e-8, largest 3.8e-8).  Against a component of 1% of the largest
+that noise alone is 2e-5 relative.  So components are compared relative to
+max(|quotient|, 3e-2 of the largest component), where the largest noise
+stays below 1e-5 at h = 1e-4 and below 1e-3 at h = 1e-6.
+
 Bars: FP64 gradients within 1e-5 of the quotient (h = 1e-4); the mixed
 gradients (FP32 per-element reverse arithmetic, FP64 per-cell sums) within
-1e-3.  Components below 1e-3 of the largest one are compared on that scale.
-RT_REPORT_DIR, when set, receives the measured errors as JSON."""
+1e-3.  RT_REPORT_DIR, when set, receives the measured errors as JSON."""
 import json
 import os
 
@@ -102,7 +110,7 @@ def test_adjoint_workload_32_cells_central_differences():
                 rows.append((fd, float(grads["fp64"][which][idx]), float(grads["fp32"][which][idx])))
             rows = np.array(rows)
             scale = max(float(grads["fp64"][which].abs().max()), 1e-300)
-            den = np.maximum(np.abs(rows[:, 0]), 1e-3 * scale)
+            den = np.maximum(np.abs(rows[:, 0]), 3e-2 * scale)
             e64 = np.abs(rows[:, 1] - rows[:, 0]) / den
             e32 = np.abs(rows[:, 2] - rows[:, 0]) / den
             e6432 = np.abs(rows[:, 2] - rows[:, 1]) / den
