@@ -237,7 +237,8 @@ rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G);
  * in FP32 and the per-element reverse arithmetic and intensity cotangents are
  * FP32, while per-cell sums and per-cell cotangents stay FP64.
  * Scope: flat Cartesian geometry, fluid at rest, FP64 or FP32 intensities,
- * at most 192 directions, periodic (>= 4 cells) or outflow boundaries;
+ * at most 672 directions (G3 = 642 of section 3.3), periodic (>= 4 cells) or
+ * outflow boundaries;
  * anything else is RT_EINVAL.
  * All pointers are device pointers; dL_dI_in may alias dL_dI_out.
  * Stream-ordered. */

@@ -65,6 +65,16 @@ struct LaneD {
     __device__ static V wv(const double *w, int d) { return w[d]; }
 };
 
+// finer geodesic grids (G3 = 642 directions): the same lanes in one CTA of up
+// to 704 (FP32 pairs) or 672 (FP64) threads, one per SM
+struct LaneF3 : LaneF {
+    static constexpr int NT = 352, MINB = 1;
+};
+struct LaneD3 : LaneD {
+    static constexpr int NT = 672, MINB = 1;
+};
+constexpr int REV_MAX_DIRS = LaneD3::NT;   // 672
+
 // Half of the limited slope, hs = s/2 (the reconstruction offset of eq.
 // radiative_transfer_discrete's face states), and its derivatives in the
 // forward difference dl = I_{p+1} - I_p and the backward difference
@@ -802,8 +812,10 @@ rt_status launch_rev_t(rt_ctx *c, const RevArgs &A) {
     const int dyn = FUSE ? (int)(RNC * LT::NT * LT::L * sizeof(typename LT::S)) : 0;
     bool per = true;   // every active axis periodic
     for (int a = 0; a < 3; ++a) per = per && (!A.act[a] || A.per[a]);
-    auto kern = A.limiter == RT_LIM_MC ? (per ? k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, true> : k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, false>)
-                                       : (per ? k_rev<LT, BY, BZ, FUSE, -1, true> : k_rev<LT, BY, BZ, FUSE, -1, false>);
+    auto kern = k_rev<LT, BY, BZ, FUSE, -1, false>;
+    if constexpr (LT::NT <= LaneD::NT)       // the finer-grid lanes keep one instance per brick
+        kern = A.limiter == RT_LIM_MC ? (per ? k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, true> : k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, false>)
+                                      : (per ? k_rev<LT, BY, BZ, FUSE, -1, true> : kern);
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     kern<<<(unsigned)nblk, LT::NT, dyn, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
@@ -820,6 +832,11 @@ template <class LT, bool FUSE> rt_status launch_rev_b(rt_ctx *c, const RevArgs &
     return launch_rev_t<LT, 1, 1, FUSE>(c, A);
 }
 static rt_status launch_rev(rt_ctx *c, const RevArgs &A, bool fuse) {
+    if (c->nd > LaneD::NT) {       // finer grids: 1 x 1 bricks
+        if (c->cfg.precision == RT_FP64)
+            return fuse ? launch_rev_t<LaneD3, 1, 1, true>(c, A) : launch_rev_t<LaneD3, 1, 1, false>(c, A);
+        return fuse ? launch_rev_t<LaneF3, 1, 1, true>(c, A) : launch_rev_t<LaneF3, 1, 1, false>(c, A);
+    }
     if (c->cfg.precision == RT_FP64) return fuse ? launch_rev_b<LaneD, true>(c, A) : launch_rev_b<LaneD, false>(c, A);
     return fuse ? launch_rev_b<LaneF, true>(c, A) : launch_rev_b<LaneF, false>(c, A);
 }
@@ -849,7 +866,7 @@ static rt_status adj_check(rt_ctx *c, const char *who) {
         return adj_fail(c, RT_EINVAL, w + ": flat Cartesian geometry with the fluid at rest only");
     if (c->cfg.precision == RT_BF16) return adj_fail(c, RT_EINVAL, w + ": FP64 or FP32 intensities only");
     if (!rt_coupling3(c)) return adj_fail(c, RT_EINVAL, w + ": coupling method 3 only");
-    if (c->nd > LaneD::NT || c->nd % 2) return adj_fail(c, RT_EINVAL, w + ": at most 192 directions");
+    if (c->nd > REV_MAX_DIRS || c->nd % 2) return adj_fail(c, RT_EINVAL, w + ": at most 672 directions");
     if ((double)c->ncell * c->nd >= 2147483647.0)
         return adj_fail(c, RT_EINVAL, w + ": n_cell * n_dir must be below 2^31");
     for (int a = 0; a < 3; ++a) {

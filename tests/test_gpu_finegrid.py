@@ -113,3 +113,50 @@ def test_g3_spherical_front():
         out = run_gpu(cfg, f, dt, n, prec)
         assert abs(CF.mean_radius(out["I"] @ w, x) - 0.6) < 0.5 * cfg["dx"][0], prec
 
+
+
+@pytest.mark.parametrize("bc,limiter", [((("periodic", "periodic"),) * 3, "mc"),
+                                        ((("outflow", "outflow"), ("periodic", "periodic"), ("periodic", "periodic")), "minmod")])
+def test_g3_adjoint_against_oracle(bc, limiter):
+    """The reverse pass at 642 directions (one CTA of 672 FP64 or 352 FP32
+    threads per SM, 1 x 1 bricks) against the oracle adjoint, two steps on a
+    9 x 4 x 4 box: FP64 within 1e-9 (floor 1e-6 of the largest component); the
+    mixed pass (FP32 storage) as in test_gpu_adjoint.py: kappa and eta within
+    1e-4 of their largest component, the intensity gradient within 1e-4 of
+    the largest in all but 1e-3 of the elements (limiter kinks) and 5e-2 in
+    every element."""
+    from test_gpu_adjoint import _gpu_adjoint, _loss_cotangents
+    nx = (9, 4, 4)
+    rng = np.random.Generator(np.random.PCG64(W.SEED0 + 195))
+    nc = int(np.prod(nx))
+    cfg = W.base_config(8, nx, (0, 0, 0), tuple(1.0 / n for n in nx), bc, limiter=limiter)
+    nd = 642
+    rho = np.exp(rng.normal(0.0, 0.5, nc))
+    T = rng.uniform(0.5, 2.0, nc)
+    f = dict(rho=rho, ug=rho * T / (W.GAMMA - 1.0), ucon=W.static_ucon(nc),
+             kappa=np.full(nc, 1e-2) * rng.uniform(0.5, 2.0, nc), alpha_s=np.full(nc, 0.4),
+             eta=rng.uniform(0.5, 1.5, nc), I=W.planck(T)[:, None] * (1.0 + 0.1 * rng.uniform(-1, 1, (nc, nd))))
+    nsteps = 2
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    dt = o.cfl_dt(0.4)
+    w = o.grid()["w"]
+    for precision in ("fp64", "fp32"):
+        I0 = f["I"] if precision == "fp64" else np.asarray(f["I"], dtype=np.float32).astype(np.float64)
+        o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+        o.set_intensity(I0)
+        o.step(dt, nsteps)
+        dI, du = _loss_cotangents(o.intensity(), o.ug(), w)
+        o2 = oracle.Oracle(cfg)
+        o2.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+        gI, gk, ge = o2.adjoint(I0, f["ug"], nsteps, dt, dI, du)
+        Ib, ub, kb, eb = _gpu_adjoint(cfg, f, I0, dt, nsteps, dI, du, precision)
+        if precision == "fp64":
+            for name, got, ref in (("I0", Ib, gI), ("kappa", kb, gk), ("eta", eb, ge)):
+                assert rel_err(got, ref, 1e-6).max() <= 1e-9, (name, rel_err(got, ref, 1e-6).max())
+        else:
+            for name, got, ref in (("kappa", kb, gk), ("eta", eb, ge)):
+                err = np.abs(got - ref).max() / np.abs(ref).max()
+                assert err <= 1e-4, (name, err)
+            e = np.abs(Ib - gI) / np.abs(gI).max()
+            assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 0.05, (np.quantile(e, 0.999), e.max())
