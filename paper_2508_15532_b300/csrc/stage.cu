@@ -57,8 +57,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
 
     // ---- shared layout
     TM *It = (TM *)smem_raw;                                  // [NC][ndp]
-    TM *Ip = It + NC * ndp;                                   // [NC][ndp]
-    TM *recX = Ip + NC * ndp;                                 // [NOWN][TXC+1][5]
+    // It holds the transported intensities I*, then (after the update) the
+    // interaction's change I_+ - I* of every element, which is all the
+    // exchange ledger needs
+    TM *recX = It + NC * ndp;                                 // [NOWN][TXC+1][5]
     TM *recY = recX + NOWN * (TXC + 1) * 5;                   // [BZ][BY+1][TXC][5]
     TM *recZ = recY + BZ * (BY + 1) * TXC * 5;                // [BY][BZ+1][TXC][5]
     TM *scU = recZ + BY * (BZ + 1) * TXC * 5;                 // [NC][4] tetrad-frame fluid velocity
@@ -66,8 +68,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
     TM *Icell = scA + NC;                                     // [NOWN][nd]   (curved only)
     TM *Arec = Icell + (FLAT ? 0 : NOWN * nd);                // [NOWN][6][nd] (curved only; slot-major: own slots conflict-free)
     double *part = (double *)(((uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)) + 15) & ~(uintptr_t)15);  // [NT / NC][NC][6]
-    double *sc64 = part + NT * 6;                             // [NC]: E-bar_-
-    int *xmap = (int *)(sc64 + NC);                           // [TXC+4]
+    int *xmap = (int *)(part + NT * 6);                       // [TXC+4]
     int *rowY = xmap + TXC + 4;                               // [BZ][BY+4]
     int *rowZ = rowY + BZ * (BY + 4);                         // [BY][BZ+4]
     int *scOn = rowZ + BY * (BZ + 4);                         // [NC]
@@ -581,7 +582,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                     const double aap = A.coupling == 1 ? q.aam : au * tpow_neg<double>(Tp, A.T_exp);
                     const double em = q.eta * aap * A.arad * Tp * Tp * Tp * Tp + as * X;
                     if (A.sv_X) { A.sv_Em[cidx] = Em; A.sv_X[cidx] = X; }
-                    sc64[s] = Em;
                     scEm[s] = (TM)(dt * em / qw);
                     scA[s] = (TM)adt;
                 }
@@ -606,7 +606,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
             const double Tp = Tm + (Em - X) / Y;
             const double aap = A.cc_au[cidx] * tpow_neg<double>(Tp, A.T_exp), atp = aap + A.cc_as[cidx];
             const double em = A.eta[cidx] * aap * A.arad * Tp * Tp * Tp * Tp + A.cc_as[cidx] * X;
-            sc64[s] = Em;
             scEm[s] = (TM)(dt * em / qw);
             scA[s] = (TM)(atp * dt);
             }
@@ -621,6 +620,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
             size_t cidx = gcell(lc, ii, j);
             if (ii >= nc) continue;
             TM v = It[lc * ndp + s];
+            const TM v0 = v;
             if (scOn[lc]) {
                 if (all_static) v = (v + scEm[lc]) / (TM(1) + scA[lc]);
                 else {
@@ -632,25 +632,26 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                 if (!FLAT) zero = zero || (A.mask[(size_t)((j + A.ng1) * A.gn0 + (i0 + ii + A.ng0)) * nd + s] & 1);
                 if (zero) v = TM(0);
             }
-            Ip[lc * ndp + s] = IO<TS, TM>::st(A.Iout, cidx * nd + s, v);
+            It[lc * ndp + s] = IO<TS, TM>::st(A.Iout, cidx * nd + s, v) - v0;   // the stored I_+ minus I*
         }
     }
     __syncthreads();
-    // exchange ledger: E-bar(I_+) and Delta R^{0 a} in direction chunks
+    // exchange ledger: E-bar(I_+) - E-bar(I*) and Delta R^{0 a} in direction
+    // chunks, summed from the per-element changes (no cancellation)
     {
         const int c = s % NC, g = s / NC;
         TM Ep = 0, cEp = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
         if ((c % TXC) < nc && scOn[c]) {
             const TM u0m = scU[4 * c], u1 = scU[4 * c + 1], u2 = scU[4 * c + 2], u3 = scU[4 * c + 3];
-            const TM *rp = Ip + c * ndp, *rt = It + c * ndp;
+            const TM *rd = It + c * ndp;
             for (int d = g; d < nd; d += nchunk) {
                 TM w = ldT<TM>(A.wT, d);
                 TM x = ldT<TM>(A.dirT, 3 * d), y = ldT<TM>(A.dirT, 3 * d + 1), z = ldT<TM>(A.dirT, 3 * d + 2);
                 TM D = all_static ? TM(1) : TM(1) + (u0m - fma(u1, x, fma(u2, y, u3 * z)));
-                TM t = D * D * rp[d] * w;
+                TM t = D * D * rd[d] * w;
                 TM yk = t - cEp, tk = Ep + yk;
                 cEp = (tk - Ep) - yk; Ep = tk;
-                TM dI = (rp[d] - rt[d]) * w;
+                TM dI = rd[d] * w;
                 r0 += dI; r1 = fma(x, dI, r1); r2 = fma(y, dI, r2); r3 = fma(z, dI, r3);
             }
         }
@@ -669,7 +670,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
                     const double *pp = part + (g * NC + s) * 6;
                     Ep += pp[0]; dR[0] += pp[1]; dR[1] += pp[2]; dR[2] += pp[3]; dR[3] += pp[4];
                 }
-                double ugp = ugm - (Ep - sc64[s]);
+                double ugp = ugm - Ep;          // Ep: E-bar(I_+) - E-bar(I*)
                 A.ug_out[cidx] = ugp;
                 double T = ugp / A.cc_Y[cidx];
                 A.alpha_out[cidx] = T > 0.0 ? A.cc_au[cidx] * tpow_neg<double>(T, A.T_exp) + A.cc_as[cidx] : 0.0;
@@ -724,9 +725,9 @@ template <typename TM, bool FLAT, int BY, int BZ, int NC>
 size_t stage_smem(int nd, int NT) {
     constexpr int TXC = NC / (BY * BZ), NOWN = BY * BZ;
     const size_t ndp = nd + 1;
-    size_t tm = 2 * NC * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NC;
+    size_t tm = NC * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NC;
     if (!FLAT) tm += (size_t)NOWN * nd + 6 * (size_t)NOWN * nd;
-    return sizeof(TM) * tm + 16 + sizeof(double) * ((size_t)NT * 6 + NC) +
+    return sizeof(TM) * tm + 16 + sizeof(double) * ((size_t)NT * 6) +
            sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NC);
 }
 
@@ -762,8 +763,9 @@ rt_status launch_blk(rt_ctx *c, const StageArgs &A, int NT) {
         // curved geometry: the tables do not depend on x3 (phi), so 8 x 1 x 4
         // bricks, whose four rows share every table entry, beat 8 x 2 x 2
         // bricks (measured 96.0 against 110.9 ms per 256 x 128 x 128 torus
-        // step); the kernel is latency-bound, and three CTAs of 192 threads
-        // per SM (96 registers) take it to 83.8 ms
+        // step); the kernel is latency-bound: three CTAs of 192 threads per
+        // SM (96 registers) took it to 83.8 ms, and with the brick's single
+        // intensity tile four (80 registers) run it in 63.2 ms
         constexpr int MB = sizeof(TM) == 4 ? CURV_MINB : 1;   // FP64: shared memory allows one CTA
         if (NT <= CURV_NT) {
             if (A.act2 && A.nx2 % 4 == 0) return launch<TS, TM, FLAT, 1, 4, NCELL, CURV_NT, MB>(c, A, NT);

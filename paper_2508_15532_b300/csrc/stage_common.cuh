@@ -8,7 +8,7 @@ namespace rtk {
 constexpr int NCELL = 32;    // cells per CTA
 constexpr int MAXNT = 256;
 constexpr int MAXNT_BIG = 1024;     // general stage kernel on finer grids: one direction per thread
-constexpr int CURV_NT = 192, CURV_MINB = 3;   // general stage kernel, curved geometry, up to 192 directions
+constexpr int CURV_NT = 192, CURV_MINB = 4;   // general stage kernel, curved geometry, up to 192 directions
 constexpr size_t SMEM_MAX = 227 * 1024;   // shared memory of one CTA (opt-in maximum)
 constexpr double FOURPI = 12.566370614359172953850573533118;
 constexpr int F_MIR = 1 << 29, F_FIX = 1 << 30, F_MASK = (1 << 29) - 1;
