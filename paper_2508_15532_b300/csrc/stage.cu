@@ -67,8 +67,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_stage(const StageArgs A) {
     TM *scN0 = scU + 4 * NC, *scK = scN0 + NC, *scEm = scK + NC, *scA = scEm + NC;
     TM *Icell = scA + NC;                                     // [NOWN][nd]   (curved only)
     TM *Arec = Icell + (FLAT ? 0 : NOWN * nd);                // [NOWN][6][nd] (curved only; slot-major: own slots conflict-free)
-    double *part = (double *)(((uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)) + 15) & ~(uintptr_t)15);  // [NT / NC][NC][6]
-    int *xmap = (int *)(part + NT * 6);                       // [TXC+4]
+    // the interaction's chunk sums, used only after the transport, share the
+    // angular rows' space (less shared memory leaves more L1 to the tables)
+    double *part = (double *)(((uintptr_t)Icell + 15) & ~(uintptr_t)15);   // [NT / NC][NC][6]
+    const uintptr_t end_ang = (uintptr_t)(Arec + (FLAT ? 0 : 6 * NOWN * nd)), end_part = (uintptr_t)(part + NT * 6);
+    int *xmap = (int *)(end_ang > end_part ? end_ang : end_part);   // [TXC+4]
     int *rowY = xmap + TXC + 4;                               // [BZ][BY+4]
     int *rowZ = rowY + BZ * (BY + 4);                         // [BY][BZ+4]
     int *scOn = rowZ + BY * (BZ + 4);                         // [NC]
@@ -718,17 +721,18 @@ __global__ void k_cellconst(int ncell, double gam, double rho_exp, double rho_fl
     Y[c] = r / (gam - 1.0);
 }
 
-// shared memory of one CTA of k_stage: the brick's intensities before and
-// after the interaction, face records, per-cell constants, the curved
-// geometry's angular rows, the chunk partial sums, boundary descriptors
+// shared memory of one CTA of k_stage: the brick's intensities (I*, then the
+// interaction's changes), face records, per-cell constants, the curved
+// geometry's angular rows and (in the same space) the chunk partial sums,
+// boundary descriptors
 template <typename TM, bool FLAT, int BY, int BZ, int NC>
 size_t stage_smem(int nd, int NT) {
     constexpr int TXC = NC / (BY * BZ), NOWN = BY * BZ;
     const size_t ndp = nd + 1;
-    size_t tm = NC * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NC;
-    if (!FLAT) tm += (size_t)NOWN * nd + 6 * (size_t)NOWN * nd;
-    return sizeof(TM) * tm + 16 + sizeof(double) * ((size_t)NT * 6) +
-           sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NC);
+    const size_t tm = NC * ndp + NOWN * (TXC + 1) * 5 + BZ * (BY + 1) * TXC * 5 + BY * (BZ + 1) * TXC * 5 + 8 * NC;
+    const size_t ang = FLAT ? 0 : sizeof(TM) * 7 * (size_t)NOWN * nd;   // angular rows
+    const size_t prt = 16 + sizeof(double) * (size_t)NT * 6;           // chunk sums (same space)
+    return sizeof(TM) * tm + (ang > prt ? ang : prt) + sizeof(int) * (TXC + 4 + BZ * (BY + 4) + BY * (BZ + 4) + NC);
 }
 
 template <typename TS, typename TM, bool FLAT, int BY, int BZ, int NC, int MAXT, int MINB = 1>
