@@ -16,6 +16,11 @@ from paper_2508_15532_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-9
+# mixed pass (FP32 storage and per-element arithmetic), away from limiter
+# kinks: a few hundred FP32 roundings (2^-24 = 6e-8) per gradient element over
+# these short rollouts; measured 1.1e-7 to 2.4e-7 of the largest component on
+# every case here
+MIXED_TOL = 1e-5
 
 
 def _torch():
@@ -108,11 +113,14 @@ def test_checkpointed_rollout_matches_oracle():
 
 def test_mixed_adjoint_fp32_storage_against_oracle():
     """FP32 intensities: the recompute is stored in FP32 and the per-element
-    reverse arithmetic is FP32 (per-cell sums and cotangents FP64).  The
-    forward FP32 bar is 1e-4 per intensity; the gradients in kappa and eta
-    (sums over directions and faces) meet 1e-4 of their largest component,
-    and the intensity gradient does so in all but a few elements, where the
-    FP32 state can fall on the other side of a limiter kink."""
+    reverse arithmetic is FP32 (per-cell sums and cotangents FP64).  Every
+    gradient component (I0, kappa, eta) meets MIXED_TOL of the largest
+    component of its gradient.  A cell where the FP32 forward state took
+    another branch of the MC limiter than the FP64 one (a kink) would differ
+    by more; these seeded inputs have none (the predictor's output is not
+    readable on the CUDA side, so kinks of second-order steps are not located
+    here: test_mixed_adjoint_outliers_sit_at_limiter_kinks locates them on
+    first-order steps)."""
     torch = _torch()
     import paper_2508_15532_b300 as rt
     cfg, f = _case(2, None, False, N=8, index=62)
@@ -137,11 +145,124 @@ def test_mixed_adjoint_fp32_storage_against_oracle():
     eb = torch.zeros_like(ub_in)
     st.step_adjoint(T(I0).float(), T(f["ug"]), dt, nsteps, T(dI), T(du), Ib_in, ub_in, kb, eb)
     torch.cuda.synchronize()
-    for name, got, ref in (("kappa", kb, gk), ("eta", eb, ge)):
+    for name, got, ref in (("I0", Ib_in, gI), ("kappa", kb, gk), ("eta", eb, ge)):
         err = np.abs(got.cpu().numpy() - ref).max() / np.abs(ref).max()
-        assert err <= 1e-4, (name, err)
-    e = np.abs(Ib_in.cpu().numpy() - gI) / np.abs(gI).max()
-    assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 0.05, (np.quantile(e, 0.999), e.max())
+        assert err <= MIXED_TOL, (name, err)
+
+
+def _mc_branch(S, nx, bc, dtype):
+    """Branch of the MC half slope hs = min(|dl|, |dr|, |dl + dr|/4) sign(dl)
+    (section 3.4) at every (cell, direction) along every active axis, computed
+    in `dtype` from the state S [n_cell, n_dir] (cells x1-fastest): 0 where
+    dl dr <= 0, 1 for |dl|, 2 for |dr| strictly smaller, 3 for the quarter
+    sum strictly below both.  Ghosts: periodic wrap, outflow copy of the edge
+    cell.  Returns one array [nx2, nx1, nx0, n_dir] per active axis."""
+    A = np.asarray(S, dtype=dtype).reshape(nx[2], nx[1], nx[0], -1)
+    out = []
+    for a in range(3):
+        if nx[a] < 2:
+            continue
+        ax = 2 - a
+        pad = [(0, 0)] * 4
+        pad[ax] = (1, 1)
+        P = np.pad(A, pad, mode="wrap" if bc[a][0] == "periodic" else "edge")
+        n = nx[a]
+        lo, mid, hi = (np.take(P, np.arange(k, k + n), axis=ax) for k in (0, 1, 2))
+        dl, dr = hi - mid, mid - lo
+        al, ar, q = np.abs(dl), np.abs(dr), np.abs(dtype(0.25) * (dl + dr))
+        w1 = ar < al
+        m1 = np.where(w1, ar, al)
+        w2 = q < m1
+        out.append(np.where(dl * dr > 0, np.where(w2, 3, np.where(w1, 2, 1)), 0))
+    return out
+
+
+KINK_CASES = [
+    # periodic flat3d-like box
+    ("flat3d", (12, 12, 12), None),
+    # outflow on every axis (the ghost folding of the x1 pipeline and of the columns)
+    ("box", (12, 10, 6), (("outflow", "outflow"),) * 3),
+]
+
+
+@pytest.mark.parametrize("kind,nx,bc", KINK_CASES)
+def test_mixed_adjoint_outliers_sit_at_limiter_kinks(kind, nx, bc):
+    """The mixed pass (FP32 recompute and per-element arithmetic) against the
+    oracle adjoint, element by element: its intensity gradient meets
+    MIXED_TOL of the largest component everywhere except next to a limiter kink, a cell
+    where the FP32 forward state and the FP64 one take different branches of
+    the MC limiter (the derivative of the half slope jumps there, so the two
+    gradients legitimately differ).  First-order steps, so that every stage's
+    input is a step's end state on both sides; two steps, so that only the
+    second stage can hold a kink (the first starts from the same FP32-rounded
+    intensities).  A kink in stage s at cell c' changes the cotangent of that
+    stage's input at c' and its two neighbours along the kink's axis; each
+    earlier stage's transport reaches two cells further on each axis, so the
+    initial-intensity gradient may differ only within 1 + 2 s cells of c'.
+    The interaction couples the directions of a cell, so a kink in any
+    direction marks its whole cell."""
+    from scipy.ndimage import maximum_filter1d
+    if kind == "flat3d":
+        cfg, f = _case(1, None, False, N=nx[0], index=65)
+    else:
+        cfg, f = _box_case(nx, bc, "mc", 1, index=66)
+    bcs = [b[0] for b in cfg["bc"]]
+    bcs = [(b, b) for b in bcs]
+    nsteps = 2
+    o = oracle.Oracle(cfg)
+    o.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    dt = o.cfl_dt(0.4)
+    w = o.grid()["w"]
+    I0 = np.asarray(f["I"], dtype=np.float32).astype(np.float64)
+    o.set_intensity(I0)
+    S64 = [o.intensity()]
+    for _ in range(nsteps):
+        o.step(dt, 1)
+        S64.append(o.intensity())
+    dI, du = _loss_cotangents(S64[-1], o.ug(), w)
+    o2 = oracle.Oracle(cfg)
+    o2.set_fluid(f["rho"], f["ug"], f["ucon"], f["kappa"], f["alpha_s"], f["eta"])
+    gI, gk, ge = o2.adjoint(I0, f["ug"], nsteps, dt, dI, du)
+
+    torch = _torch()
+    import paper_2508_15532_b300 as rt
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    st = rt.RadiationStep(rt.Grid(cfg["n_geo"]), cfg, precision="fp32")
+    st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+    I0t = T(I0).float()
+    st.set_intensity(I0t)
+    S32 = [I0t.cpu().numpy()]
+    buf = torch.empty_like(I0t)
+    for _ in range(nsteps):
+        st.step(dt, 1)
+        st.get_intensity(buf)
+        torch.cuda.synchronize()
+        S32.append(buf.cpu().numpy())
+    Ib, ub, kb, eb = _gpu_adjoint(cfg, f, I0, dt, nsteps, dI, du, "fp32")
+
+    # cells within reach of a kink
+    near = np.zeros((nx[2], nx[1], nx[0]), dtype=bool)
+    nkink = []
+    for s in range(nsteps):
+        kink = np.zeros_like(near)
+        for c32, c64 in zip(_mc_branch(S32[s], nx, bcs, np.float32), _mc_branch(S64[s], nx, bcs, np.float64)):
+            kink |= (c32 != c64).any(axis=-1)
+        nkink.append(int(kink.sum()))
+        r = 1 + 2 * s
+        for a in range(3):
+            if nx[a] > 1 and kink.any():
+                kink = maximum_filter1d(kink, size=2 * r + 1, axis=2 - a,
+                                        mode="wrap" if bcs[a][0] == "periodic" else "constant")
+        near |= kink
+    assert nkink[0] == 0, nkink          # the first stage starts from the same intensities
+    for name, got, ref in (("kappa", kb, gk), ("eta", eb, ge)):
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= MIXED_TOL, (name, err)
+    e = (np.abs(Ib - gI) / np.abs(gI).max()).reshape(nx[2], nx[1], nx[0], -1).max(axis=-1)
+    far = e[~near]
+    assert far.size > 0.5 * e.size, (nkink, int(near.sum()))
+    assert far.max() <= MIXED_TOL, (nkink, int(near.sum()), far.max(), np.argwhere((e > MIXED_TOL) & ~near)[:5])
 
 
 def _box_case(nx, bc, limiter="mc", order=2, index=63):
@@ -193,8 +314,9 @@ def test_step_adjoint_boxes_fp64_and_mixed(nx, bc, limiter, order):
     """Every brick shape of the reverse kernel (1 x 1, 2 x 1, 2 x 2), outflow
     folding along the x1 pipeline and along the columns, minmod, first-order
     steps and an inactive x1 axis, in both passes, against the oracle adjoint:
-    FP64 within 1e-9 of the largest component; the mixed pass as in
-    test_mixed_adjoint_fp32_storage_against_oracle."""
+    FP64 within 1e-9 of the largest component, the mixed pass within
+    MIXED_TOL (these seeded inputs put no limiter kink between the FP32 and
+    the FP64 forward states)."""
     cfg, f = _box_case(nx, bc, limiter, order, index=64 + sum(nx))
     nsteps = 3
     o = oracle.Oracle(cfg)
@@ -216,11 +338,9 @@ def test_step_adjoint_boxes_fp64_and_mixed(nx, bc, limiter, order):
                 err = rel_err(got, ref, 1e-6).max()
                 assert err <= TOL, (precision, name, err)
         else:
-            for name, got, ref in (("kappa", kb, gk), ("eta", eb, ge)):
+            for name, got, ref in (("I0", Ib, gI), ("kappa", kb, gk), ("eta", eb, ge)):
                 err = np.abs(got - ref).max() / np.abs(ref).max()
-                assert err <= 1e-4, (precision, name, err)
-            e = np.abs(Ib - gI) / np.abs(gI).max()
-            assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 0.05, (precision, np.quantile(e, 0.999), e.max())
+                assert err <= MIXED_TOL, (precision, name, err)
 
 
 @pytest.mark.parametrize("precision,order", [("fp64", 2), ("fp32", 2), ("fp64", 1)])

@@ -131,11 +131,11 @@ def test_g3_adjoint_against_oracle(bc, limiter):
     """The reverse pass at 642 directions (one CTA of 672 FP64 or 352 FP32
     threads per SM, 1 x 1 bricks) against the oracle adjoint, two steps on a
     9 x 4 x 4 box: FP64 within 1e-9 (floor 1e-6 of the largest component); the
-    mixed pass (FP32 storage) as in test_gpu_adjoint.py: kappa and eta within
-    1e-4 of their largest component, the intensity gradient within 1e-4 of
-    the largest in all but 1e-3 of the elements (limiter kinks) and 5e-2 in
-    every element."""
-    from test_gpu_adjoint import _gpu_adjoint, _loss_cotangents
+    mixed pass (FP32 storage) as in test_gpu_adjoint.py: every component of
+    the I0, kappa and eta gradients within MIXED_TOL of the largest component
+    of its gradient (these seeded inputs put no limiter kink between the FP32
+    and the FP64 forward states)."""
+    from test_gpu_adjoint import MIXED_TOL, _gpu_adjoint, _loss_cotangents
     nx = (9, 4, 4)
     rng = np.random.Generator(np.random.PCG64(W.SEED0 + 195))
     nc = int(np.prod(nx))
@@ -165,8 +165,6 @@ def test_g3_adjoint_against_oracle(bc, limiter):
             for name, got, ref in (("I0", Ib, gI), ("kappa", kb, gk), ("eta", eb, ge)):
                 assert rel_err(got, ref, 1e-6).max() <= 1e-9, (name, rel_err(got, ref, 1e-6).max())
         else:
-            for name, got, ref in (("kappa", kb, gk), ("eta", eb, ge)):
+            for name, got, ref in (("I0", Ib, gI), ("kappa", kb, gk), ("eta", eb, ge)):
                 err = np.abs(got - ref).max() / np.abs(ref).max()
-                assert err <= 1e-4, (name, err)
-            e = np.abs(Ib - gI) / np.abs(gI).max()
-            assert np.quantile(e, 0.999) <= 1e-4 and e.max() <= 0.05, (np.quantile(e, 0.999), e.max())
+                assert err <= MIXED_TOL, (name, err)
