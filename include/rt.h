@@ -240,7 +240,10 @@ rt_status rt_moments(rt_ctx *c, double *R, double *Ebar, double *G);
  * at most 672 directions (G3 = 642 of section 3.3), periodic (>= 4 cells) or
  * outflow boundaries;
  * anything else is RT_EINVAL.
- * All pointers are device pointers; dL_dI_in may alias dL_dI_out.
+ * All pointers are device pointers; dL_dI_in may alias dL_dI_out.  The
+ * recompute reads I_ckpt in place (a 256-byte aligned checkpoint that does
+ * not overlap dL_dI_in; otherwise it is first copied into the arena), so it
+ * must not change until the call's work on the stream is done.
  * Stream-ordered. */
 rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double *ug_ckpt, double dt, int nsteps,
                           const double *dL_dI_out, const double *dL_dug_out, double *dL_dI_in,

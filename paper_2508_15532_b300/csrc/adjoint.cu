@@ -16,6 +16,7 @@
 //     output I_+ = (I_* + c)/(1 + a), so I_* is never stored, and its root
 //     enters through the implicit function theorem.
 #include <atomic>
+#include <cstdint>
 #include "stage_common.cuh"
 #include "f32x2.cuh"
 #include <algorithm>
@@ -402,7 +403,10 @@ struct RevArgs {
 // workload here), or -1 to read it from the arguments.  PER: every active axis
 // is periodic, so no stencil row lies beyond an outflow boundary and the ghost
 // folding drops out at compile time
-template <class LT, int BY, int BZ, bool FUSE, int LK, bool PER>
+// NOTR: an instance for launches without transport, whose x1 loop is only
+// loads and a reduction (kept apart, so that the transport instances compile
+// as they would without it)
+template <class LT, int BY, int BZ, bool FUSE, int LK, bool PER, bool NOTR = false>
 __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     using S = typename LT::S;
     using V = typename LT::V;
@@ -573,6 +577,36 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
     if constexpr (PFX) {
         if (xon) { pf_issue(0); cp_commit(); }
     }
+    // without transport (the launch that reverses the interaction ending a
+    // reversed run, or a source-only configuration) a position's work is two
+    // loads and a reduction: unrolled, so that several positions' loads are in
+    // flight at once (rolled, the launch waits on one DRAM round trip per
+    // position)
+    if constexpr (NOTR) {
+#pragma unroll 4
+        for (int ii = 0; ii < nc; ++ii) {
+            const int ie = (i0 + ii) * nd;
+            S red[NRED];
+#pragma unroll
+            for (int o = 0; o < NOWN; ++o) {
+                const V Ic = ldI(own(o) + ie);
+                const V Zc = A.zg_f64 ? LT::ld64((const double *)A.Zg + own(o) + ie) : ldZ(own(o) + ie);
+                V ib = zero;
+                if (A.add_base) ib = ib + Zc;
+                if (Zo) ib = ib + LT::ld(Zo + own(o) + ie);
+                red[o] = act ? LT::hsum(zero) : S(0);
+                if constexpr (FUSE) {
+                    if (act) LT::st(sIt + (o * TXC + ii) * (NT * L) + d0, ib);
+                    red[NOWN + o] = act ? LT::hsum(ib * Ic) : S(0);
+                } else if (act) {
+                    if (A.out_f64) LT::st64((double *)A.Zout + own(o) + ie, ib);
+                    else LT::st((S *)A.Zout + own(o) + ie, ib);
+                }
+            }
+            const S rs = tsum_n<NRED, S>(red, lane);
+            if (lane < NRED) part[warp][lane][ii] = rs;
+        }
+    } else {
 #pragma unroll 1
     for (int ii = 0; ii < nc; ++ii) {
         const int i = i0 + ii, ie = i * nd;
@@ -705,6 +739,7 @@ __global__ void __launch_bounds__(LT::NT, LT::MINB) k_rev(const RevArgs A) {
         const S rs = tsum_n<NRED, S>(red, lane);
         if (lane < NRED) part[warp][lane][ii] = rs;
     }
+    }
     __syncthreads();
     if constexpr (FUSE) {
         // P = sum over directions of the cotangent of I_+, per own cell
@@ -816,6 +851,7 @@ rt_status launch_rev_t(rt_ctx *c, const RevArgs &A) {
     if constexpr (LT::NT <= LaneD::NT)       // the finer-grid lanes keep one instance per brick
         kern = A.limiter == RT_LIM_MC ? (per ? k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, true> : k_rev<LT, BY, BZ, FUSE, RT_LIM_MC, false>)
                                       : (per ? k_rev<LT, BY, BZ, FUSE, -1, true> : kern);
+    if (!A.transport) kern = k_rev<LT, BY, BZ, FUSE, -1, false, true>;   // neither limiter nor boundaries enter
     RT_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     kern<<<(unsigned)nblk, LT::NT, dyn, c->stream>>>(A);
     RT_CUDA_TRY(c, cudaGetLastError());
@@ -1057,8 +1093,16 @@ extern "C" rt_status rt_step_adjoint(rt_ctx *c, const void *I_ckpt, const double
     AdjArena ar;
     if ((st = adj_layout(c, nsteps, ar)) != RT_OK) return st;
     const size_t nc = (size_t)c->ncell, ni = nc * c->nd;
-    // 1. forward recompute from the checkpoint with the stage kernels
-    RT_CUDA_TRY(c, cudaMemcpyAsync(ar.In[0], I_ckpt, ni * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+    // 1. forward recompute from the checkpoint with the stage kernels; the
+    // stages only read their first input, so the checkpoint serves in place;
+    // it is copied into the arena first where it overlaps the gradient this
+    // call writes, or is not aligned as the arena's buffers (the stage kernels
+    // load intensities in pairs, 8 bytes at a time)
+    const char *ck = (const char *)I_ckpt, *gi = (const char *)dL_dI_in;
+    if ((ck < gi + ni * sizeof(double) && gi < ck + ni * c->esize) || ((uintptr_t)ck & 255u) != 0)
+        RT_CUDA_TRY(c, cudaMemcpyAsync(ar.In[0], I_ckpt, ni * c->esize, cudaMemcpyDeviceToDevice, c->stream));
+    else
+        ar.In[0] = const_cast<void *>(I_ckpt);
     RT_CUDA_TRY(c, cudaMemcpyAsync(ar.un[0], ug_ckpt, nc * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if ((st = adj_forward(c, ar, dt, nullptr)) != RT_OK) return st;
     // 2. reverse sweep
