@@ -155,6 +155,21 @@ static void transport_adj(or_ctx *c, const double *Isrc, const double *ug_src, d
     free(Ig); free(Gb); free(alg); free(abar_g); free(gmap); free(gmir); free(gfix); free(ginterior);
 }
 
+/* a stage of section 3.6 with the transport switched off (a source-only
+   configuration) leaves its base unchanged: Iout = Ibase, whose reverse adds
+   Ib_out to the base's cotangent */
+static void stage_fwd(or_ctx *c, const double *Isrc, const double *ug_src, const double *Ibase, double dtk,
+                      double *Iout) {
+    if (c->c.transport) or_transport_stage(c, Isrc, ug_src, Ibase, dtk, Iout);
+    else memcpy(Iout, Ibase, sizeof(double) * (size_t)c->ncell * c->G.nd);
+}
+static void stage_adj(or_ctx *c, const double *Isrc, const double *ug_src, double dtk, const double *Ib_out,
+                      double *Ib_src, double *Ib_base, double *ub_src, double *kb) {
+    if (c->c.transport) { transport_adj(c, Isrc, ug_src, dtk, Ib_out, Ib_src, Ib_base, ub_src, kb); return; }
+    const size_t ni = (size_t)c->ncell * c->G.nd;
+    for (size_t e = 0; e < ni; ++e) Ib_base[e] += Ib_out[e];
+}
+
 /* reverse of one interaction step (fluid at rest): Iin = transported
    intensities, ugin = gas energy entering; Ib_out, ub_out = cotangents of the
    outputs -> accumulate Ib_in, ub_in, kb, eb */
@@ -259,12 +274,12 @@ int or_adjoint(or_ctx *c, const double *I0, const double *ug0, int nsteps, doubl
         const double *I = In + ni * st, *u = un + n * st;
         double *Inext = In + ni * (st + 1), *unext = un + n * (st + 1);
         if (c->c.order == 1) {
-            or_transport_stage(c, I, u, I, dt, Inext);
+            stage_fwd(c, I, u, I, dt, Inext);
             or_source_step(c, Inext, u, unext, dt, NULL);
         } else {
-            or_transport_stage(c, I, u, I, 0.5 * dt, Ist);
+            stage_fwd(c, I, u, I, 0.5 * dt, Ist);
             or_source_step(c, Ist, u, us, 0.5 * dt, NULL);
-            or_transport_stage(c, Ist, us, I, dt, Inext);
+            stage_fwd(c, Ist, us, I, dt, Inext);
             or_source_step(c, Inext, u, unext, dt, NULL);
         }
     }
@@ -279,25 +294,25 @@ int or_adjoint(or_ctx *c, const double *I0, const double *ug0, int nsteps, doubl
         const double *I = In + ni * st, *u = un + n * st;
         memset(Ibn, 0, sizeof(double) * ni); memset(ubn, 0, sizeof(double) * n);
         if (c->c.order == 1) {
-            or_transport_stage(c, I, u, I, dt, I2);
+            stage_fwd(c, I, u, I, dt, I2);
             memset(Ib2, 0, sizeof(double) * ni);
             source_adj(c, I2, u, dt, Ib, ub, Ib2, ubn, dL_dkappa, dL_deta);
-            transport_adj(c, I, u, dt, Ib2, Ibn, Ibn, ubn, dL_dkappa);
+            stage_adj(c, I, u, dt, Ib2, Ibn, Ibn, ubn, dL_dkappa);
         } else {
             /* recompute the stage intermediates */
-            or_transport_stage(c, I, u, I, 0.5 * dt, Is);
+            stage_fwd(c, I, u, I, 0.5 * dt, Is);
             memcpy(Ist, Is, sizeof(double) * ni);
             or_source_step(c, Ist, u, us, 0.5 * dt, NULL);
-            or_transport_stage(c, Ist, us, I, dt, I2);
+            stage_fwd(c, Ist, us, I, dt, I2);
             /* corrector interaction and transport */
             memset(Ib2, 0, sizeof(double) * ni);
             source_adj(c, I2, u, dt, Ib, ub, Ib2, ubn, dL_dkappa, dL_deta);
             memset(Ibs, 0, sizeof(double) * ni); memset(ubs, 0, sizeof(double) * n);
-            transport_adj(c, Ist, us, dt, Ib2, Ibs, Ibn, ubs, dL_dkappa);
+            stage_adj(c, Ist, us, dt, Ib2, Ibs, Ibn, ubs, dL_dkappa);
             /* predictor interaction and transport */
             memset(Ib2, 0, sizeof(double) * ni);
             source_adj(c, Is, u, 0.5 * dt, Ibs, ubs, Ib2, ubn, dL_dkappa, dL_deta);
-            transport_adj(c, I, u, 0.5 * dt, Ib2, Ibn, Ibn, ubn, dL_dkappa);
+            stage_adj(c, I, u, 0.5 * dt, Ib2, Ibn, Ibn, ubn, dL_dkappa);
         }
         memcpy(Ib, Ibn, sizeof(double) * ni);
         memcpy(ub, ubn, sizeof(double) * n);

@@ -17,10 +17,11 @@ HREL = 1e-4
 TOL = 1e-5
 
 
-def _setup(order=2, limiter=None, index=50, N=6):
+def _setup(order=2, limiter=None, index=50, N=6, transport=True):
     cfg, f = W.flat3d(N=N, n_geo=2, index=index)
     cfg = dict(cfg)
     cfg["order"] = order
+    cfg["transport"] = transport
     if limiter is not None:
         cfg["limiter"] = limiter
     o = oracle.Oracle(cfg)
@@ -39,9 +40,12 @@ def _loss(cfg, f, dt, nsteps, w, kappa, eta, I0, ug0):
     return float((E ** 2).sum() + 3.0 * (ug * E).sum()), o.intensity(), E, ug
 
 
-@pytest.mark.parametrize("order,limiter", [(2, None), (1, None), (2, "minmod")])
-def test_adjoint_matches_finite_differences(order, limiter):
-    cfg, f, o = _setup(order=order, limiter=limiter)
+@pytest.mark.parametrize("order,limiter,transport", [(2, None, True), (1, None, True), (2, "minmod", True),
+                                                     (2, None, False), (1, None, False)])
+def test_adjoint_matches_finite_differences(order, limiter, transport):
+    """transport False: a source-only configuration, where each stage of
+    section 3.6 leaves its base unchanged and only the interaction acts"""
+    cfg, f, o = _setup(order=order, limiter=limiter, transport=transport)
     nsteps = 3
     dt = o.cfl_dt(0.4)
     w = o.grid()["w"]
