@@ -113,6 +113,48 @@ def test_source_only_adjoint_fp64_and_mixed(order):
                 assert err <= 1e-4, (precision, name, err)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_read_in_place_or_copied(precision):
+    """rt_step_adjoint reads a 256-byte aligned checkpoint that does not
+    overlap dL_dI_in in place, and copies it into its arena otherwise: an
+    unaligned checkpoint (one element into a buffer) and, in FP64, a
+    checkpoint that is also the dL_dI_in buffer give the same gradients, bit
+    for bit, as the aligned one."""
+    torch = _torch()
+    import paper_2508_15532_b300 as rt
+    cfg, f = _case(2, None, False, N=8, index=68)
+    nsteps = 2
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    st = rt.RadiationStep(rt.Grid(cfg["n_geo"]), cfg, precision=precision)
+    st.set_fluid(T(f["rho"]), T(f["ug"]), T(f["ucon"]), T(f["kappa"]), T(f["alpha_s"]), T(f["eta"]))
+    dt = st.cfl_dt(0.4)
+    w = T(rt.Grid(cfg["n_geo"]).query()[1])
+    I0 = T(f["I"]) if precision == "fp64" else T(f["I"]).float()
+    dI = (2.0 * (T(f["I"]) @ w))[:, None] * w[None, :]
+    du = T(f["ug"])
+
+    def run(ck, out=None):
+        Ib_in = torch.empty_like(dI) if out is None else out
+        ub_in = torch.empty_like(du)
+        kb, eb = torch.zeros_like(du), torch.zeros_like(du)
+        st.step_adjoint(ck, T(f["ug"]), dt, nsteps, dI.clone(), du.clone(), Ib_in, ub_in, kb, eb)
+        torch.cuda.synchronize()
+        return [x.cpu().numpy() for x in (Ib_in, ub_in, kb, eb)]
+
+    ref = run(I0.clone())
+    buf = torch.empty(I0.numel() + 1, dtype=I0.dtype, device=dev)
+    ck = buf[1:].view_as(I0)
+    ck.copy_(I0)
+    assert ck.data_ptr() % 256 != 0
+    for a, b in zip(run(ck), ref):
+        assert np.array_equal(a, b)
+    if precision == "fp64":
+        shared = I0.clone()        # the checkpoint is also the buffer that receives dL/dI_in
+        for a, b in zip(run(shared, out=shared), ref):
+            assert np.array_equal(a, b)
+
+
 def test_checkpointed_rollout_matches_oracle():
     torch = _torch()
     import paper_2508_15532_b300 as rt
